@@ -1,0 +1,84 @@
+"""The five benchmark workloads and small stand-ins of the same structure.
+
+Each workload is a graph plus the arrays that define one of the paper's graph
+LPs (Sec. 3): the LP kind, an optional objective vector and optional row
+bounds.  Inputs only; no solver arithmetic lives here.
+
+  bmatch-2k        bipartite matching LP, 2,000 + 2,000 vertices, 20,000 uniform edges (seed 1)
+  densest-rmat18   densest subgraph (Charikar dual, Sec. 3) on R-MAT scale 18, edge factor 16 (seed 2)
+  domset-rmat20    weighted dominating set, explicit CSR of I + A, weights U[1,10) (seed 3)
+  bmatching-256    256 bipartite b-matching LPs, edges log-uniform in [1e3, 2e5], b in 1..5 (seed 4)
+  vcover-rmat24    vertex cover on R-MAT scale 24 (seed 5)
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Optional
+
+import torch
+
+from . import Graph, bipartite_uniform, capacities, instance_seed, loguniform_sizes, rmat, symmetric_csr, vertex_weights
+
+
+@dataclass
+class Workload:
+    name: str
+    lp: str                      # bmatch | bmatching | densest | domset | vcover
+    graph: Graph
+    eps: float = 0.1
+    objective: Optional[torch.Tensor] = None   # float32 [n] (vertex weights for domset)
+    bounds: Optional[torch.Tensor] = None      # float32 [n_vertices] (b-matching capacities)
+    csr: Optional[tuple] = None                # (rowptr, colidx) of I + A for domset
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def edges(self) -> torch.Tensor:
+        return self.graph.edge_pairs()
+
+    @property
+    def n_edges(self) -> int:
+        return self.graph.m
+
+
+def bmatch(n_left=2000, n_right=2000, m=20000, seed=1, device="cpu") -> Workload:
+    g = bipartite_uniform(n_left, n_right, m, seed=seed, device=device)
+    return Workload(f"bmatch-{n_left}+{n_right}-{m}", "bmatch", g)
+
+
+def densest(scale=18, seed=2, device="cpu") -> Workload:
+    g = rmat(scale, seed=seed, device=device)
+    return Workload(f"densest-rmat{scale}", "densest", g)
+
+
+def domset(scale=20, seed=3, device="cpu") -> Workload:
+    g = rmat(scale, seed=seed, device=device)
+    c = vertex_weights(g.n, seed=seed, device=device)
+    rowptr, col = symmetric_csr(g, with_self=True)
+    return Workload(f"domset-rmat{scale}", "domset", g, objective=c, csr=(rowptr, col))
+
+
+def vcover(scale=24, seed=5, device="cpu") -> Workload:
+    g = rmat(scale, seed=seed, device=device)
+    return Workload(f"vcover-rmat{scale}", "vcover", g)
+
+
+def bmatching_instance(m, seed, device="cpu") -> Workload:
+    side = max(2, int(math.ceil(m / 10)))
+    m = min(m, side * side)
+    g = bipartite_uniform(side, side, m, seed=seed, device=device)
+    b = capacities(g.n, seed=seed, device=device)
+    return Workload(f"bmatching-{m}", "bmatching", g, bounds=b)
+
+
+def bmatching_batch(count=256, seed=4, lo=1e3, hi=2e5, device="cpu") -> list:
+    sizes = loguniform_sizes(count, seed, lo, hi)
+    return [bmatching_instance(m, instance_seed(seed, k), device=device) for k, m in enumerate(sizes)]
+
+
+WORKLOADS = {
+    "bmatch-2k": lambda device="cpu": bmatch(device=device),
+    "densest-rmat18": lambda device="cpu": densest(18, 2, device=device),
+    "domset-rmat20": lambda device="cpu": domset(20, 3, device=device),
+    "vcover-rmat24": lambda device="cpu": vcover(24, 5, device=device),
+}

@@ -1,0 +1,272 @@
+/*
+ * mwu.h -- C ABI of a GB300 (sm_103a) solver for positive linear programs by the
+ * multiplicative-weight-update (MWU) method with step-size search of
+ * arXiv 2307.03307 ("Efficient Parallel Implementation of the Multiplicative
+ * Weight Update Method for Graph-based Linear Programs").
+ *
+ * Problem statement (Sec. 2.2, Eq. NormFeasibleLP): find x >= 0 with
+ *     P x <= 1  (packing rows, P in R_+^{m_P x n})  and  C x >= 1  (covering rows),
+ * to a (1+eps)-relative approximation.  Pure packing (max c^T x, P x <= 1) and
+ * pure covering (min c^T x, C x >= 1) embed the objective as one extra row
+ * (1/M) c^T x >= 1 or <= 1 and search on M (Sec. 2.2); densest subgraph fixes D
+ * in W z >= 1, O z <= D (Sec. 3, Eq. densest_linalg) and searches on D.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an int status (mwu_status); nothing aborts or throws
+ *     across this boundary.  Negative values are errors; mwu_last_error(ctx)
+ *     gives a one-line message.
+ *   - Input pointers may be host or device memory (the library copies with
+ *     cudaMemcpyDefault during mwu_create and never keeps a caller pointer).
+ *   - All device work of a context is issued on opt.stream (NULL = a stream
+ *     the context creates).  A context is not thread safe.
+ *   - Indices are int32; sizes int64.  Vectors of the FP32 form are float32,
+ *     of the FP64 form float64.
+ */
+#ifndef MWU_H_
+#define MWU_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+    MWU_OK = 0,
+    MWU_FEASIBLE = 0,       /* probe ended with max(Px) <= (1+eps) min(Cx), min(Cx) >= 1 (Theorem 4.1) */
+    MWU_INFEASIBLE = 1,     /* d = 0, alpha < 1 (Alg. 2), or packing rows past 1+eps          */
+    MWU_MAX_ITER = 2,       /* iteration cap reached (5000 in Sec. 6)                           */
+    MWU_RUNNING = 3,        /* mwu_iterate returned before the probe ended                      */
+    MWU_ERR_INVALID = -1,   /* bad argument or malformed matrix                                 */
+    MWU_ERR_CUDA = -2,      /* a CUDA call failed                                               */
+    MWU_ERR_OOM = -3,       /* device allocation failed                                         */
+    MWU_ERR_NUMERIC = -4,   /* NaN/Inf met in a reduction                                       */
+    MWU_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                                    */
+    MWU_ERR_STATE = -6      /* call out of order (e.g. candidates before a direction)           */
+} mwu_status;
+
+/* Infeasibility reasons reported in mwu_iter_stats.reason. */
+enum { MWU_REASON_NONE = 0, MWU_REASON_COVERED = 1, MWU_REASON_PACKING = 2,
+       MWU_REASON_D_ZERO = 3, MWU_REASON_ALPHA = 4, MWU_REASON_MAX_ITER = 5 };
+
+/* ------------------------------------------------------------ problem kind */
+typedef enum {
+    MWU_PACKING = 0,   /* max c^T x s.t. P x <= 1 ; C is the objective row (1/M) c^T        */
+    MWU_COVERING = 1,  /* min c^T x s.t. C x >= 1 ; P is the objective row (1/M) c^T        */
+    MWU_MIXED = 2,     /* feasibility: P x <= 1, C x >= 1 (no objective, no target)          */
+    MWU_DENSEST = 3    /* min D s.t. W z >= 1, O z <= D ; P = O/D, C = W, built from a graph */
+} mwu_kind;
+
+/* --------------------------------------------------------- matrix kinds */
+/* Sec. 3 matrices and their implicit forms (Sec. 5.1.2).  Edge lists are
+ * int32 pairs (u_e, v_e) interleaved, u_e != v_e, each undirected edge once. */
+typedef enum {
+    MWU_MAT_CSR = 0,          /* explicit CSR rows x cols (rowptr, colidx, val or NULL = ones)   */
+    MWU_MAT_INCIDENCE = 1,    /* M, n_vertices x n_edges: M[w,e] = 1 iff w in e (Eq. incidence)  */
+    MWU_MAT_INCIDENCE_T = 2,  /* M^T, n_edges x n_vertices (vertex cover, Sec. 3)                */
+    MWU_MAT_PAIR = 3,         /* O, n_vertices x 2 n_edges: O[w, 2e+b] = 1 iff w is endpoint b   */
+    MWU_MAT_INTERWEAVE = 4,   /* W, n_edges x 2 n_edges: W[e,2e] = W[e,2e+1] = 1 (Eq. interweaved)*/
+    MWU_MAT_NONE = 5          /* side given by the objective row                                 */
+} mwu_mat_kind;
+
+typedef struct {
+    int32_t kind;              /* mwu_mat_kind                                               */
+    int32_t rows, cols;        /* CSR only (implicit kinds derive them)                      */
+    int64_t nnz;               /* CSR only                                                   */
+    const int32_t *rowptr;     /* CSR: rows+1 entries, rowptr[0] = 0, non-decreasing         */
+    const int32_t *colidx;     /* CSR: nnz column indices in [0, cols)                       */
+    const float *val;          /* CSR: nnz values >= 0, finite; NULL = all ones              */
+    const int32_t *edges;      /* implicit kinds: 2*n_edges int32 (u0,v0,u1,v1,...)          */
+    int32_t n_vertices;        /* implicit kinds                                             */
+    int64_t n_edges;           /* implicit kinds                                             */
+    const float *row_bound;    /* optional, rows entries > 0: row j reads (A x)_j <= b_j
+                                  (packing) or >= b_j (covering), i.e. diag(1/b) A
+                                  (Appendix A.1 bounds); NULL = all ones                   */
+} mwu_matrix;
+
+/* --------------------------------------------------------------- options */
+enum { MWU_STEP_KARY = 0,      /* K candidates per pass (Alg. 3 generalised; K = 1 is Alg. 3) */
+       MWU_STEP_BINARY = 1,    /* Alg. 3 as printed: one candidate per pass                  */
+       MWU_STEP_STANDARD = 2 };/* alpha = 1 (Alg. 1)                                         */
+enum { MWU_PREC_F32_R64 = 0,   /* FP32 vectors and per-element math, FP64 reductions         */
+       MWU_PREC_FP64 = 1 };    /* everything FP64, one candidate per pass, host-driven search*/
+
+typedef struct {
+    double eps;                /* (0,1); default 0.1                                          */
+    int32_t max_iter;          /* MWU iterations per probe; default 5000 (Sec. 6)             */
+    double eta_factor;         /* eta = eta_factor ln(m_P+m_C)/eps; default 10 (Alg. 1)      */
+    int32_t step;              /* MWU_STEP_*; default KARY                                    */
+    int32_t K;                 /* candidates per pass, 1..8; default 8 (FP64 form forces 1)  */
+    int32_t max_passes;        /* candidate passes per iteration; default 6 (F32), 64 (FP64) */
+    int32_t warm_start;        /* start the exponential phase at floor(log2 alpha_prev)      */
+    int32_t double_single;     /* c_d = 1/eta when one side is a single row (Sec. 2.2)       */
+    int32_t precision;         /* MWU_PREC_*; default F32_R64                                 */
+    double outer_tol;          /* bisection stops when hi <= (1+outer_tol) lo; default eps   */
+    int32_t max_probes;        /* default 64                                                  */
+    int32_t use_graph;         /* capture one iteration in a CUDA graph (F32 form); default 1 */
+    int32_t check_every;       /* iterations between host reads of the status; default 8     */
+    int32_t group;             /* lanes per CSR row, 0 = automatic; else 1,2,4,8,16,32       */
+    int32_t timing;            /* record CUDA events around each kernel class of every
+                                  iteration (read with mwu_get_timing); default 0           */
+    void *stream;              /* cudaStream_t; NULL = a non-blocking stream the context
+                                  creates and owns                                           */
+} mwu_options;
+
+/* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
+int mwu_default_options(mwu_options *opt);
+
+/* ------------------------------------------------------------ statistics */
+typedef struct {
+    int32_t status;            /* mwu_status of the probe (RUNNING if not ended)             */
+    int32_t reason;            /* MWU_REASON_*                                                */
+    int32_t iters;             /* MWU iterations of the current probe                        */
+    int32_t last_passes;       /* candidate passes of the last iteration                     */
+    int64_t evals;             /* f(alpha) evaluations of the current probe                  */
+    int64_t passes;            /* candidate passes of the current probe                      */
+    double alpha;              /* last accepted step size                                    */
+    double ymax, zmin;         /* max(Px), min(Cx) at the current x                          */
+} mwu_iter_stats;
+
+typedef struct {
+    int32_t status;            /* MWU_OK, or an error                                        */
+    double objective;          /* best certified objective (c^T x / max(Px), c^T x / min(Cx),
+                                  or max(Oz)/min(Wz)) over all probes                        */
+    double lo, hi;             /* final bracket of the search on M or D                      */
+    int32_t probes;            /* feasibility probes run                                     */
+    int64_t iters;             /* MWU iterations over all probes                             */
+    int64_t evals;             /* f(alpha) evaluations over all probes                       */
+    int64_t passes;            /* candidate passes over all probes                           */
+    double seconds;            /* wall time of the solve                                     */
+    int64_t launches;          /* kernels launched by the solve (graph nodes counted)        */
+} mwu_result;
+
+/* Per-kernel-class device time of the iterations run with opt.timing = 1,
+ * from CUDA events recorded on the context's stream inside the captured
+ * iteration (FP32 form) or around the launches (FP64 form). */
+typedef struct {
+    double dir_ms;             /* gradient + direction kernel (with the deferred x update)   */
+    double cand_first_ms;      /* first candidate pass (forward SpMV dy = Pd, dz = Cd)       */
+    double cand_rest_ms;       /* further candidate passes (exit at once when done)          */
+    double update_ms;          /* y, z update with the next iteration's reductions           */
+    int64_t iters;             /* iterations timed                                           */
+    int64_t cand_passes;       /* candidate passes that evaluated candidates                 */
+} mwu_timing;
+
+typedef struct {
+    double eta, c_d, eps, target;
+    double s_p, S_p, s_c, S_c; /* LSE shifts (max y, min z) and shifted sums                  */
+    double ymax, zmin;
+    double alpha;              /* last accepted (or searched) alpha                          */
+    int64_t n_positive;        /* |{i : d_i > 0}| of the last direction                      */
+    int64_t n, m_P, m_C;       /* variables, packing rows, covering rows (objective row incl.)*/
+    int32_t K, iters;
+} mwu_scalars;
+
+/* Vectors readable with mwu_get_vector. */
+enum { MWU_VEC_X = 0, MWU_VEC_Y = 1, MWU_VEC_Z = 2, MWU_VEC_D = 3, MWU_VEC_DY = 4,
+       MWU_VEC_DZ = 5, MWU_VEC_G = 6, MWU_VEC_H = 7 };
+
+typedef struct mwu_ctx mwu_ctx;
+
+/* ------------------------------------------------------------ lifecycle */
+/* Build a solver context.  Matrices follow the paper's normalisation (Sec. 2.2):
+ *   PACKING : P = the constraint matrix (CSR, INCIDENCE, ...), C kind NONE;
+ *             objective_c (n floats, NULL = ones) becomes the covering row.
+ *   COVERING: C = the constraint matrix, P kind NONE; objective_c becomes the packing row.
+ *   MIXED   : both P and C given, objective_c ignored.
+ *   DENSEST : P must be MWU_MAT_PAIR and C MWU_MAT_INTERWEAVE over the same edge list.
+ * Input arrays are validated on the device (monotone rowptr, indices in range,
+ * values finite and >= 0, bounds > 0, covering rows non-empty); a violation
+ * returns MWU_ERR_INVALID.  The context owns every device buffer it allocates;
+ * release it with mwu_destroy.  *out is NULL on failure. */
+int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C,
+               const float *objective_c, const mwu_options *opt, mwu_ctx **out);
+
+/* Release a context and its device memory.  NULL is ignored. */
+void mwu_destroy(mwu_ctx *ctx);
+
+/* Message of the last error of ctx (or of the last failed mwu_create when ctx is NULL). */
+const char *mwu_last_error(const mwu_ctx *ctx);
+
+/* -------------------------------------------------------- one probe (Alg. 2) */
+/* Fix the probe target (M for PACKING/COVERING, D for DENSEST; ignored for
+ * MIXED) and reset the probe: eta = eta_factor ln(m_P+m_C)/eps, x_i = eps/(n
+ * ||P_{:,i}||_inf), y = Px, z = Cx and their LSE reductions (Alg. 2 init). */
+int mwu_set_target(mwu_ctx *ctx, double target);
+
+/* Replace x (n entries, host or device, float32 or float64 per x_is_fp64) and
+ * recompute y = Px, z = Cx and their reductions.  Keeps eta and the target. */
+int mwu_set_x(mwu_ctx *ctx, const void *x, int32_t x_is_fp64);
+
+/* Run up to n_iters iterations of Alg. 2 (gradients, direction, d = 0 test,
+ * dy = Pd, dz = Cd, step-size search, update, stopping test).  Returns the
+ * probe status: FEASIBLE, INFEASIBLE, MAX_ITER or RUNNING; or an error.
+ * stats may be NULL. */
+int mwu_iterate(mwu_ctx *ctx, int32_t n_iters, mwu_iter_stats *stats);
+
+/* Stage hooks of one iteration, for checking each step against a reference:
+ * mwu_direction computes g, h, d (Alg. 2, gradient and direction lines) and
+ * dy = Pd, dz = Cd at the current x without taking a step; it returns
+ * MWU_INFEASIBLE when d = 0.  *n_positive may be NULL. */
+int mwu_direction(mwu_ctx *ctx, int64_t *n_positive);
+
+/* Evaluate K <= 8 step candidates on the stored y, dy, z, dz of the last
+ * mwu_direction (Sec. 4.1): psi[k] = smax(y + a_k dy) - smax(y),
+ * phi[k] = smin(z + a_k dz) - smin(z), zmin[k] = min(z + a_k dz).
+ * Host arrays of K doubles; any output may be NULL. */
+int mwu_eval_candidates(mwu_ctx *ctx, const double *alphas, int32_t K,
+                        double *psi, double *phi, double *zmin);
+
+/* Run the configured step-size search (Alg. 3 / K-candidate form) on the
+ * last direction without updating x.  *alpha < 1 means INFEASIBLE. */
+int mwu_search(mwu_ctx *ctx, double *alpha, int64_t *evals);
+
+/* ------------------------------------------------------- the whole solve */
+/* Bisect on M (or D) between lo and hi (<= 0: the automatic bracket of Sec.
+ * 2.2 / Sec. 3) until hi <= (1+outer_tol) lo, one probe per midpoint, and
+ * report the best certified objective.  MIXED runs a single probe. */
+int mwu_solve(mwu_ctx *ctx, double lo, double hi, mwu_result *res);
+
+/* --------------------------------------------------------- read back */
+/* Copy vector `which` (MWU_VEC_*) into dst (host or device), n entries, as
+ * float64 when as_fp64 else float32.  n must equal the vector's length.
+ * MWU_VEC_X after mwu_solve is the best probe's x. */
+int mwu_get_vector(mwu_ctx *ctx, int32_t which, void *dst, int64_t n, int32_t as_fp64);
+
+/* Copy the current scalars. */
+int mwu_get_scalars(mwu_ctx *ctx, mwu_scalars *out);
+
+/* Accumulated per-kernel-class times (see mwu_timing); reset != 0 clears them. */
+int mwu_get_timing(mwu_ctx *ctx, mwu_timing *out, int32_t reset);
+
+/* --------------------------------------- smoothed potential (autograd) */
+/* pot = smax_eta(P x) - smin_eta(C x) at the given x (device, n float32) with
+ * the context's eta (set by mwu_set_target), and its gradients (device
+ * float32 outputs, each may be NULL):
+ *   grad_x[i]      = (P^T nabla smax(Px) - C^T nabla smin(Cx))_i   (= g - h)
+ *   grad_obj[i]    = d pot / d c_i for the objective row (1/M) c^T
+ *                    (+w x_i/M on the packing side, -w x_i/M on the covering side)
+ *   grad_vals[k]   = d pot / d val[k] for the k-th stored value of the
+ *                    explicit CSR matrix (sign +w_j x_i for P, -w_j x_i for C).
+ * Sec. 4.1 defines the potential (its 1/eta factor is left out here). */
+int mwu_potential(mwu_ctx *ctx, const float *x, double *pot,
+                  float *grad_x, float *grad_obj, float *grad_vals);
+
+/* ------------------------------------------------------------- batched */
+/* Many independent instances in one context (one launch per phase over all
+ * instances, captured in a CUDA graph).  Supported: PACKING over INCIDENCE
+ * matrices with optional row_bound (b-matching, Appendix A.1 with lb = 0).
+ * P[k] is instance k's matrix; objective rows are ones. */
+int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
+                     mwu_ctx **out);
+
+/* Solve every instance of a batch context: per-instance bisection on M, all
+ * probes of all instances advanced together.  objective/iters may be NULL;
+ * otherwise host arrays of `count` entries. */
+int mwu_solve_batch(mwu_ctx *ctx, double *objective, int64_t *iters, mwu_result *total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MWU_H_ */

@@ -1,0 +1,1069 @@
+// C ABI of libmwu (include/mwu.h): context lifecycle, the probe driver of
+// Alg. 2, the bisection on M or D (Sec. 2.2, Sec. 3), read-back, the smoothed
+// potential for autograd, and the batched front end.
+//
+// Two execution forms share the kernels of mwu_kernels.cu:
+//   F32_R64 : FP32 vectors, K candidates per pass, one iteration captured once
+//             in a CUDA graph (gradient+direction, first candidate pass with
+//             the forward SpMV, max_passes-1 further passes that exit at once
+//             when the search is done, update); the host reads the status
+//             every `check_every` iterations.
+//   FP64    : the plain form: FP64 vectors, one candidate per pass (Alg. 3),
+//             the host reads the search state after every pass.
+#include "mwu.h"
+#include "mwu_setup.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace mwu;
+
+static thread_local std::string g_create_error;
+
+struct mwu_ctx {
+    int32_t kind = 0;
+    mwu_options opt{};
+    bool fp64 = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Arena ar;
+    std::string err;
+    int64_t n = 0, mP = 0, mC = 0;
+    Problem<float> pf{};
+    Problem<double> pd{};
+    DevState *st_dev = nullptr;
+    DevState *st_host = nullptr;
+    const float *objective = nullptr;
+    cudaGraphExec_t gexec_chunk = nullptr;   // check_every iterations
+    cudaGraphExec_t gexec_one = nullptr;     // one iteration
+    std::vector<cudaEvent_t> ev;             // 4 per iteration of the chunk graph (timing)
+    std::vector<cudaEvent_t> ev_one;         // 4 for the one-iteration graph
+    mwu_timing tim{};
+    int64_t launches = 0;
+    void *x_best = nullptr;
+    int n_sms = 0;
+    double target = 1.0;
+    bool have_direction = false;
+    // batch front end
+    std::vector<mwu_ctx *> batch;
+};
+
+// ------------------------------------------------------------ helpers
+#define TRY_CUDA(ctx, expr)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) return fail_cuda((ctx), e_, #expr);                             \
+    } while (0)
+
+static int fail(mwu_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+static int fail_cuda(mwu_ctx *c, cudaError_t e, const char *what) {
+    std::string m = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? MWU_ERR_OOM : MWU_ERR_CUDA, m);
+}
+
+template <class F> static cudaError_t with_prob(mwu_ctx *c, F f) {
+    if (c->fp64) return f(c->pd);
+    return f(c->pf);
+}
+
+static int pow2_floor(double v) {
+    int g = 1;
+    while (g * 2 <= v && g < 32) g *= 2;
+    return g;
+}
+
+static int choose_G(double avg, int forced) {
+    if (forced > 0) return forced;
+    int g = pow2_floor(avg) / 2;
+    return std::max(1, std::min(32, g));
+}
+
+static int heavy_len_for(int G) { return std::max(256, 32 * G); }
+
+int mwu_default_options(mwu_options *o) {
+    if (!o) return MWU_ERR_INVALID;
+    std::memset(o, 0, sizeof(*o));
+    o->eps = 0.1;
+    o->max_iter = 5000;
+    o->eta_factor = 10.0;
+    o->step = MWU_STEP_KARY;
+    o->K = 8;
+    o->max_passes = 0;   // 0 -> form default
+    o->warm_start = 0;
+    o->double_single = 1;
+    o->precision = MWU_PREC_F32_R64;
+    o->outer_tol = 0.0;  // 0 -> eps
+    o->max_probes = 64;
+    o->use_graph = 1;
+    o->check_every = 8;
+    o->group = 0;
+    o->stream = nullptr;
+    return MWU_OK;
+}
+
+const char *mwu_last_error(const mwu_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+// ------------------------------------------------------------ views
+struct SideBuild {
+    RowView rv{};
+    ColView cv{};
+    int64_t m = 0;       // rows
+    int64_t nvar = -1;   // variables implied by this matrix (-1: any)
+    int32_t sign = 1;
+    bool dense = false;
+};
+
+static const int32_t *copy_in_i(mwu_ctx *c, const int32_t *src, int64_t n) {
+    int32_t *d = c->ar.alloc<int32_t>(n);
+    if (!d) return nullptr;
+    if (n > 0 && cudaMemcpyAsync(d, src, sizeof(int32_t) * (size_t)n, cudaMemcpyDefault, c->stream) != cudaSuccess)
+        return nullptr;
+    return d;
+}
+static const float *copy_in_f(mwu_ctx *c, const float *src, int64_t n) {
+    float *d = c->ar.alloc<float>(n);
+    if (!d) return nullptr;
+    if (n > 0 && cudaMemcpyAsync(d, src, sizeof(float) * (size_t)n, cudaMemcpyDefault, c->stream) != cudaSuccess)
+        return nullptr;
+    return d;
+}
+
+static int check_err_flag(mwu_ctx *c, int *d_err) {
+    int h = 0;
+    TRY_CUDA(c, cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h != 0) return fail(c, MWU_ERR_INVALID, validation_message(h));
+    return MWU_OK;
+}
+
+static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &sb, int *d_err) {
+    sb.sign = sign;
+    cudaStream_t s = c->stream;
+    const int forced_G = c->opt.group;
+    if (!A) return fail(c, MWU_ERR_INVALID, "missing matrix");
+    const float *rdiv = nullptr;
+    auto load_bounds = [&](int64_t rows) -> int {
+        if (!A->row_bound) return MWU_OK;
+        rdiv = copy_in_f(c, A->row_bound, rows);
+        if (!rdiv) return fail(c, MWU_ERR_OOM, "allocating row bounds");
+        TRY_CUDA(c, validate_positive(rdiv, rows, 7, d_err, s));
+        return MWU_OK;
+    };
+    int rc;
+    switch (A->kind) {
+    case MWU_MAT_CSR: {
+        if (A->rows <= 0 || A->cols <= 0 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && !A->colidx))
+            return fail(c, MWU_ERR_INVALID, "CSR: bad shape or null arrays");
+        if (A->nnz >= (int64_t)INT32_MAX) return fail(c, MWU_ERR_INVALID, "CSR: nnz exceeds int32 indexing");
+        const int32_t *ptr = copy_in_i(c, A->rowptr, A->rows + 1);
+        const int32_t *idx = copy_in_i(c, A->colidx, A->nnz);
+        const float *val = A->val ? copy_in_f(c, A->val, A->nnz) : nullptr;
+        if (!ptr || !idx || (A->val && !val)) return fail(c, MWU_ERR_OOM, "copying CSR");
+        TRY_CUDA(c, validate_csr(ptr, idx, val, A->rows, A->cols, A->nnz, sign < 0, d_err, s));
+        if ((rc = check_err_flag(c, d_err)) != MWU_OK) return rc;
+        if ((rc = load_bounds(A->rows)) != MWU_OK) return rc;
+        int32_t *tp, *ti;
+        float *tv;
+        TRY_CUDA(c, csr_transpose(c->ar, ptr, idx, val, A->rows, A->cols, A->nnz, &tp, &ti, &tv, s));
+        double avg_r = (double)A->nnz / (double)A->rows, avg_c = (double)A->nnz / (double)A->cols;
+        sb.rv = RowView{RK_CSR, choose_G(avg_r, forced_G), A->rows, A->nnz, ptr, idx, val, rdiv, 0, 0, nullptr};
+        sb.cv = ColView{CK_CSR, choose_G(avg_c, forced_G), tp, ti, tv, rdiv, nullptr, 0, 0, nullptr};
+        sb.m = A->rows;
+        sb.nvar = A->cols;
+        break;
+    }
+    case MWU_MAT_INCIDENCE:
+    case MWU_MAT_INCIDENCE_T:
+    case MWU_MAT_PAIR:
+    case MWU_MAT_INTERWEAVE: {
+        int64_t E = A->n_edges;
+        int32_t nv = A->n_vertices;
+        if (E <= 0 || !A->edges) return fail(c, MWU_ERR_INVALID, "implicit matrix: missing edge list");
+        if (A->kind != MWU_MAT_INTERWEAVE && nv <= 0) return fail(c, MWU_ERR_INVALID, "implicit matrix: n_vertices <= 0");
+        if (2 * E >= (int64_t)INT32_MAX) return fail(c, MWU_ERR_INVALID, "edge list exceeds int32 slot indexing");
+        const int32_t *edges = copy_in_i(c, A->edges, 2 * E);
+        if (!edges) return fail(c, MWU_ERR_OOM, "copying edge list");
+        if (A->kind != MWU_MAT_INTERWEAVE) {
+            TRY_CUDA(c, validate_edges(edges, E, nv, d_err, s));
+            if ((rc = check_err_flag(c, d_err)) != MWU_OK) return rc;
+        }
+        int32_t *vptr = nullptr, *slots = nullptr, *eids = nullptr;
+        if (A->kind != MWU_MAT_INTERWEAVE) {
+            TRY_CUDA(c, build_vertex_slots(c->ar, edges, E, nv, &vptr, &slots, s));
+            if (A->kind != MWU_MAT_PAIR) TRY_CUDA(c, slots_to_edges(c->ar, slots, 2 * E, &eids, s));
+        }
+        double avg = nv > 0 ? 2.0 * (double)E / (double)nv : 1.0;
+        if (A->kind == MWU_MAT_INCIDENCE) {
+            if (sign < 0) {   // covering vertex rows must be non-empty
+                TRY_CUDA(c, validate_csr(vptr, eids, nullptr, nv, E, 2 * E, 1, d_err, s));
+                if ((rc = check_err_flag(c, d_err)) != MWU_OK) return rc;
+            }
+            if ((rc = load_bounds(nv)) != MWU_OK) return rc;
+            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, eids, nullptr, rdiv, 0, 0, nullptr};
+            sb.cv = ColView{CK_FIXED2, 1, nullptr, edges, nullptr, rdiv, nullptr, 0, 0, nullptr};
+            sb.m = nv;
+            sb.nvar = E;
+        } else if (A->kind == MWU_MAT_INCIDENCE_T) {
+            if ((rc = load_bounds(E)) != MWU_OK) return rc;
+            sb.rv = RowView{RK_FIXED2, 1, E, 2 * E, nullptr, edges, nullptr, rdiv, 0, 0, nullptr};
+            sb.cv = ColView{CK_CSR, choose_G(avg, forced_G), vptr, eids, nullptr, rdiv, nullptr, 0, 0, nullptr};
+            sb.m = E;
+            sb.nvar = nv;
+        } else if (A->kind == MWU_MAT_PAIR) {
+            if ((rc = load_bounds(nv)) != MWU_OK) return rc;
+            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, slots, nullptr, rdiv, 0, 0, nullptr};
+            sb.cv = ColView{CK_FIXED1, 1, nullptr, edges, nullptr, rdiv, nullptr, 0, 0, nullptr};
+            sb.m = nv;
+            sb.nvar = 2 * E;
+        } else {
+            if ((rc = load_bounds(E)) != MWU_OK) return rc;
+            sb.rv = RowView{RK_PAIRSUM, 1, E, 2 * E, nullptr, nullptr, nullptr, rdiv, 0, 0, nullptr};
+            sb.cv = ColView{CK_HALF1, 1, nullptr, nullptr, nullptr, rdiv, nullptr, 0, 0, nullptr};
+            sb.m = E;
+            sb.nvar = 2 * E;
+        }
+        break;
+    }
+    default:
+        return fail(c, MWU_ERR_INVALID, "unsupported matrix kind");
+    }
+    // heavy rows of CSR row views
+    if (sb.rv.kind == RK_CSR) {
+        sb.rv.heavy_len = heavy_len_for(sb.rv.G);
+        int32_t *list = nullptr, cnt = 0;
+        TRY_CUDA(c, heavy_list(c->ar, sb.rv.ptr, sb.rv.rows, sb.rv.heavy_len, &list, &cnt, s));
+        sb.rv.heavy = list;
+        sb.rv.n_heavy = cnt;
+    }
+    if (sb.cv.kind == CK_CSR) sb.cv.heavy_len = heavy_len_for(sb.cv.G);
+    return MWU_OK;
+}
+
+static void dense_side(SideBuild &sb, const float *c, int32_t sign) {
+    sb.sign = sign;
+    sb.dense = true;
+    sb.rv = RowView{RK_DENSE1, 1, 1, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr};
+    sb.cv = ColView{CK_DENSE1, 1, nullptr, nullptr, nullptr, nullptr, c, 0, 0, nullptr};
+    sb.m = 1;
+    sb.nvar = -1;
+}
+
+template <class T>
+static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32_t *heavy_var, int32_t n_heavy_var,
+                         int G_var, int var_bps, int row_bps) {
+    p.n = c->n;
+    p.x = c->ar.alloc<T>(c->n);
+    p.d = c->ar.alloc<T>(c->n);
+    p.g = c->ar.alloc<T>(c->n);
+    p.h = c->ar.alloc<T>(c->n);
+    if (!p.x || !p.d || !p.g || !p.h) return fail(c, MWU_ERR_OOM, "allocating variable vectors");
+    for (int s = 0; s < 2; ++s) {
+        Side<T> &sd = p.side[s];
+        sd.rv = sb[s].rv;
+        sd.cv = sb[s].cv;
+        sd.sign = sb[s].sign;
+        sd.m = sb[s].m;
+        if (!sb[s].dense) {
+            sd.v = c->ar.alloc<T>(sd.m);
+            sd.dv = c->ar.alloc<T>(sd.m);
+            if (!sd.v || !sd.dv) return fail(c, MWU_ERR_OOM, "allocating constraint vectors");
+        } else {
+            sd.v = sd.dv = nullptr;
+        }
+    }
+    p.st = c->st_dev;
+    p.grid_var = std::max(1, c->n_sms * var_bps);
+    p.grid_row = std::max(2, c->n_sms * row_bps);
+    size_t recs = (size_t)std::max(p.grid_var, p.grid_row) + 8;
+    p.part_var = c->ar.alloc<double>((int64_t)(recs * REC));
+    p.part_row = c->ar.alloc<double>((int64_t)(recs * REC));
+    if (!p.part_var || !p.part_row) return fail(c, MWU_ERR_OOM, "allocating partial buffers");
+    p.G_var = G_var;
+    p.heavy_var = heavy_var;
+    p.n_heavy_var = n_heavy_var;
+    p.heavy_var_len = 0;
+    return MWU_OK;
+}
+
+int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const float *objective_c,
+               const mwu_options *opt, mwu_ctx **out) {
+    if (!out) return fail(nullptr, MWU_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    mwu_options o;
+    if (opt) o = *opt;
+    else mwu_default_options(&o);
+    if (!(o.eps > 0.0 && o.eps < 1.0)) return fail(nullptr, MWU_ERR_INVALID, "eps must lie in (0,1)");
+    if (o.max_iter < 0 || o.K < 1 || o.K > KMAX) return fail(nullptr, MWU_ERR_INVALID, "max_iter < 0 or K not in 1..8");
+    if (!(o.eta_factor > 0.0)) return fail(nullptr, MWU_ERR_INVALID, "eta_factor must be > 0");
+    if (o.group != 0 && (o.group < 1 || o.group > 32 || (o.group & (o.group - 1))))
+        return fail(nullptr, MWU_ERR_INVALID, "group must be 0 or a power of two <= 32");
+    if (kind < MWU_PACKING || kind > MWU_DENSEST) return fail(nullptr, MWU_ERR_INVALID, "unknown problem kind");
+    if (o.precision != MWU_PREC_F32_R64 && o.precision != MWU_PREC_FP64)
+        return fail(nullptr, MWU_ERR_INVALID, "unknown precision");
+    if (o.step < MWU_STEP_KARY || o.step > MWU_STEP_STANDARD) return fail(nullptr, MWU_ERR_INVALID, "unknown step mode");
+
+    mwu_ctx *c = new mwu_ctx();
+    c->kind = kind;
+    c->fp64 = o.precision == MWU_PREC_FP64;
+    if (c->fp64 || o.step == MWU_STEP_BINARY) o.K = 1;
+    if (o.max_passes <= 0) o.max_passes = (c->fp64 || o.K == 1) ? 64 : 6;
+    if (o.outer_tol <= 0.0) o.outer_tol = o.eps;
+    if (o.max_probes <= 0) o.max_probes = 64;
+    if (o.check_every <= 0) o.check_every = 8;
+    c->opt = o;
+    auto bail = [&](int rc) {
+        g_create_error = c->err;
+        delete c;   // destructor frees the arena
+        return rc;
+    };
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            c->err = "cannot create a CUDA stream (no device?)";
+            return bail(MWU_ERR_CUDA);
+        }
+        c->own_stream = true;
+    }
+    c->ar.set_stream(c->stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "no CUDA device";
+        return bail(MWU_ERR_CUDA);
+    }
+    int *d_err = c->ar.alloc<int>(4);
+    if (!d_err || cudaMemsetAsync(d_err, 0, 4 * sizeof(int), c->stream) != cudaSuccess) {
+        c->err = "allocating error flag";
+        return bail(MWU_ERR_OOM);
+    }
+    SideBuild sb[2];
+    int rc = MWU_OK;
+    switch (kind) {
+    case MWU_PACKING:
+        if ((rc = build_side(c, P, +1, sb[0], d_err)) != MWU_OK) return bail(rc);
+        c->n = sb[0].nvar;
+        break;
+    case MWU_COVERING:
+        if ((rc = build_side(c, C, -1, sb[1], d_err)) != MWU_OK) return bail(rc);
+        c->n = sb[1].nvar;
+        break;
+    case MWU_MIXED:
+        if ((rc = build_side(c, P, +1, sb[0], d_err)) != MWU_OK) return bail(rc);
+        if ((rc = build_side(c, C, -1, sb[1], d_err)) != MWU_OK) return bail(rc);
+        if (sb[0].nvar != sb[1].nvar) { c->err = "P and C disagree on the number of variables"; return bail(MWU_ERR_INVALID); }
+        c->n = sb[0].nvar;
+        break;
+    case MWU_DENSEST:
+        if (!P || !C || P->kind != MWU_MAT_PAIR || C->kind != MWU_MAT_INTERWEAVE) {
+            c->err = "DENSEST needs P = MWU_MAT_PAIR and C = MWU_MAT_INTERWEAVE";
+            return bail(MWU_ERR_INVALID);
+        }
+        if (P->n_edges != C->n_edges) { c->err = "P and C edge counts differ"; return bail(MWU_ERR_INVALID); }
+        if ((rc = build_side(c, P, +1, sb[0], d_err)) != MWU_OK) return bail(rc);
+        if ((rc = build_side(c, C, -1, sb[1], d_err)) != MWU_OK) return bail(rc);
+        c->n = sb[0].nvar;
+        break;
+    }
+    if (c->n <= 0) { c->err = "no variables"; return bail(MWU_ERR_INVALID); }
+    if (c->n >= (int64_t)INT32_MAX) { c->err = "variable count exceeds int32 indexing"; return bail(MWU_ERR_INVALID); }
+    if (kind == MWU_PACKING || kind == MWU_COVERING) {
+        const float *cd = nullptr;
+        if (objective_c) {
+            cd = copy_in_f(c, objective_c, c->n);
+            if (!cd) { c->err = "copying objective"; return bail(MWU_ERR_OOM); }
+            if (validate_nonneg(cd, c->n, 8, d_err, c->stream) != cudaSuccess) { c->err = "validate objective"; return bail(MWU_ERR_CUDA); }
+            if ((rc = check_err_flag(c, d_err)) != MWU_OK) return bail(rc);
+        }
+        c->objective = cd;
+        if (kind == MWU_PACKING) dense_side(sb[1], cd, -1);
+        else dense_side(sb[0], cd, +1);
+    }
+    c->mP = sb[0].m;
+    c->mC = sb[1].m;
+    // heavy variables (long CSR columns on either side)
+    int G_var = 1;
+    for (int s = 0; s < 2; ++s)
+        if (sb[s].cv.kind == CK_CSR) G_var = std::max(G_var, sb[s].cv.G);
+    for (int s = 0; s < 2; ++s)
+        if (sb[s].cv.kind == CK_CSR) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = heavy_len_for(G_var); }
+    int32_t *hv = nullptr, nhv = 0;
+    if (sb[0].cv.kind == CK_CSR || sb[1].cv.kind == CK_CSR) {
+        cudaError_t e = heavy_list2(c->ar, sb[0].cv.kind == CK_CSR ? sb[0].cv.ptr : nullptr, sb[0].cv.heavy_len,
+                                    sb[1].cv.kind == CK_CSR ? sb[1].cv.ptr : nullptr, sb[1].cv.heavy_len, c->n, &hv,
+                                    &nhv, c->stream);
+        if (e != cudaSuccess) { fail_cuda(c, e, "heavy variable list"); return bail(MWU_ERR_CUDA); }
+    }
+    // device state
+    c->st_dev = c->ar.alloc<DevState>(1);
+    if (!c->st_dev || cudaMallocHost((void **)&c->st_host, sizeof(DevState)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "allocating state";
+        return bail(MWU_ERR_OOM);
+    }
+    std::memset(c->st_host, 0, sizeof(DevState));
+    if (cudaMemsetAsync(c->st_dev, 0, sizeof(DevState), c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "clearing state";
+        return bail(MWU_ERR_CUDA);
+    }
+    int vb = 1, rb = 1;
+    if (c->fp64) { sweep_blocks_per_sm<double>(&vb, &rb); rc = alloc_problem(c, c->pd, sb, hv, nhv, G_var, vb, rb); }
+    else { sweep_blocks_per_sm<float>(&vb, &rb); rc = alloc_problem(c, c->pf, sb, hv, nhv, G_var, vb, rb); }
+    if (rc != MWU_OK) return bail(rc);
+    c->x_best = c->ar.raw((size_t)c->n * (c->fp64 ? sizeof(double) : sizeof(float)));
+    if (!c->x_best) { c->err = "allocating best x"; return bail(MWU_ERR_OOM); }
+    c->ar.release_tmp();
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        fail_cuda(c, cudaGetLastError(), "mwu_create");
+        return bail(MWU_ERR_CUDA);
+    }
+    // initial target: 1 (MIXED) or the automatic upper end
+    rc = mwu_set_target(c, 1.0);
+    if (rc < 0) return bail(rc);
+    *out = c;
+    return MWU_OK;
+}
+
+void mwu_destroy(mwu_ctx *c) {
+    if (!c) return;
+    for (mwu_ctx *b : c->batch) mwu_destroy(b);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec_chunk) cudaGraphExecDestroy(c->gexec_chunk);
+    if (c->gexec_one) cudaGraphExecDestroy(c->gexec_one);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_one) cudaEventDestroy(e);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    c->ar.free_all();
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// ------------------------------------------------------------ state I/O
+static int pull_state(mwu_ctx *c) {
+    TRY_CUDA(c, cudaMemcpyAsync(c->st_host, c->st_dev, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MWU_OK;
+}
+static int push_state(mwu_ctx *c) {
+    TRY_CUDA(c, cudaMemcpyAsync(c->st_dev, c->st_host, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+    return MWU_OK;
+}
+
+static void reset_probe_fields(DevState &h) {
+    h.status = ST_RUNNING;
+    h.reason = RS_NONE;
+    h.iter = 0;
+    h.numeric_bad = 0;
+    h.pending = 0;
+    h.alpha_acc = 0.0;
+    h.alpha_prev = 0.0;
+    h.phase = PH_DONE;
+    h.passes = 0;
+    h.last_passes = 0;
+    h.evals = 0;
+    h.total_passes = 0;
+    h.n_pos = 0;
+    for (int k = 0; k < 8; ++k) h.counter[k] = 0;
+}
+
+static int probe_status(const DevState &h) {
+    switch (h.status) {
+    case ST_FEASIBLE: return MWU_FEASIBLE;
+    case ST_INFEASIBLE: return MWU_INFEASIBLE;
+    case ST_MAX_ITER: return MWU_MAX_ITER;
+    case ST_RUNNING: return MWU_RUNNING;
+    default: return MWU_ERR_NUMERIC;
+    }
+}
+
+int mwu_set_target(mwu_ctx *c, double target) {
+    if (!c) return MWU_ERR_INVALID;
+    if (!(target > 0.0) || !std::isfinite(target)) return fail(c, MWU_ERR_INVALID, "target must be positive and finite");
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    DevState &h = *c->st_host;
+    const mwu_options &o = c->opt;
+    c->target = target;
+    h.eps = o.eps;
+    h.eta = o.eta_factor * std::log((double)(c->mP + c->mC)) / o.eps;
+    h.c_d = (o.double_single && (c->mP == 1 || c->mC == 1)) ? 1.0 / h.eta : 1.0 / (2.0 * h.eta);
+    h.target = target;
+    h.scale[0] = h.scale[1] = 1.0;
+    if (c->kind == MWU_PACKING) h.scale[1] = 1.0 / target;
+    else if (c->kind == MWU_COVERING || c->kind == MWU_DENSEST) h.scale[0] = 1.0 / target;
+    h.max_iter = o.max_iter;
+    h.K = o.K;
+    h.max_passes = o.max_passes;
+    h.warm_start = o.warm_start;
+    h.step_mode = o.step == MWU_STEP_STANDARD ? 2 : (o.step == MWU_STEP_BINARY ? 1 : 0);
+    reset_probe_fields(h);
+    if ((rc = push_state(c)) != MWU_OK) return rc;
+    c->have_direction = false;
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_x_init(p, c->stream); }));
+    c->launches += 2;
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    return probe_status(h) == MWU_ERR_NUMERIC ? fail(c, MWU_ERR_NUMERIC, "NaN/Inf in the initial reductions") : MWU_OK;
+}
+
+int mwu_set_x(mwu_ctx *c, const void *x, int32_t x_is_fp64) {
+    if (!c || !x) return MWU_ERR_INVALID;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    reset_probe_fields(*c->st_host);
+    if ((rc = push_state(c)) != MWU_OK) return rc;
+    // stage a copy on the device when x is host memory
+    cudaPointerAttributes at{};
+    const void *src = x;
+    void *tmp = nullptr;
+    if (cudaPointerGetAttributes(&at, x) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        size_t nb = (size_t)c->n * (x_is_fp64 ? 8 : 4);
+        TRY_CUDA(c, cudaMalloc(&tmp, nb));
+        cudaError_t e = cudaMemcpyAsync(tmp, x, nb, cudaMemcpyDefault, c->stream);
+        if (e != cudaSuccess) { cudaFree(tmp); return fail_cuda(c, e, "copy x"); }
+        src = tmp;
+    }
+    cudaError_t e = with_prob(c, [&](auto &p) { return launch_x_set(p, src, x_is_fp64, c->stream); });
+    if (tmp) { cudaStreamSynchronize(c->stream); cudaFree(tmp); }
+    if (e != cudaSuccess) return fail_cuda(c, e, "launch_x_set");
+    c->have_direction = false;
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    return MWU_OK;
+}
+
+// ------------------------------------------------------------ iterations
+// kernels of one iteration; ev (5 events or nullptr) brackets the kernel classes.  The
+// events are recorded as external event nodes when the sequence is captured.
+static int kernels_per_iteration(const mwu_ctx *c) { return 2 + c->opt.max_passes; }
+
+static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev) {
+    return with_prob(c, [&](auto &p) -> cudaError_t {
+        cudaError_t e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if ((e = launch_dir(p, 0, c->stream)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if ((e = launch_cand(p, 1, 0, c->stream)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        for (int k = 1; k < c->opt.max_passes; ++k)
+            if ((e = launch_cand(p, 0, 0, c->stream)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[3], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if ((e = launch_update(p, c->stream)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[4], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        return cudaSuccess;
+    });
+}
+
+static int make_events(mwu_ctx *c, std::vector<cudaEvent_t> &ev, int n) {
+    while ((int)ev.size() < n) {
+        cudaEvent_t e;
+        TRY_CUDA(c, cudaEventCreate(&e));
+        ev.push_back(e);
+    }
+    return MWU_OK;
+}
+
+static int capture(mwu_ctx *c, int iters, std::vector<cudaEvent_t> &ev, cudaGraphExec_t *out) {
+    int rc;
+    if (c->opt.timing && (rc = make_events(c, ev, 5 * iters)) != MWU_OK) return rc;
+    cudaGraph_t g = nullptr;
+    TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < iters && e == cudaSuccess; ++k)
+        e = enqueue_iteration(c, c->opt.timing ? &ev[5 * k] : nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail_cuda(c, e, "capture iteration"); }
+    if (e2 != cudaSuccess) return fail_cuda(c, e2, "end capture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { *out = nullptr; return fail_cuda(c, e, "instantiate iteration graph"); }
+    return MWU_OK;
+}
+
+static int ensure_graphs(mwu_ctx *c) {
+    int rc;
+    if (!c->gexec_chunk && (rc = capture(c, c->opt.check_every, c->ev, &c->gexec_chunk)) != MWU_OK) return rc;
+    if (!c->gexec_one && (rc = capture(c, 1, c->ev_one, &c->gexec_one)) != MWU_OK) return rc;
+    return MWU_OK;
+}
+
+// add the event times of the first `real` iterations recorded in ev
+static int accumulate_timing(mwu_ctx *c, const std::vector<cudaEvent_t> &ev, int real) {
+    for (int k = 0; k < real; ++k) {
+        float t[4];
+        for (int j = 0; j < 4; ++j) TRY_CUDA(c, cudaEventElapsedTime(&t[j], ev[5 * k + j], ev[5 * k + j + 1]));
+        c->tim.dir_ms += t[0];
+        c->tim.cand_first_ms += t[1];
+        c->tim.cand_rest_ms += t[2];
+        c->tim.update_ms += t[3];
+        c->tim.iters += 1;
+    }
+    return MWU_OK;
+}
+
+static void fill_stats(mwu_ctx *c, mwu_iter_stats *s) {
+    if (!s) return;
+    const DevState &h = *c->st_host;
+    s->status = probe_status(h);
+    s->reason = h.reason;
+    s->iters = h.iter;
+    s->last_passes = h.last_passes;
+    s->evals = h.evals;
+    s->passes = h.total_passes;
+    s->alpha = h.alpha_prev;
+    s->ymax = h.ymax;
+    s->zmin = h.zmin;
+}
+
+int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
+    if (!c || n_iters < 0) return MWU_ERR_INVALID;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    c->have_direction = false;
+    const bool graph = !c->fp64 && c->opt.use_graph;
+    if (graph && (rc = ensure_graphs(c)) != MWU_OK) return rc;
+    const int kpi = kernels_per_iteration(c);
+    int done = 0;
+    while (done < n_iters && c->st_host->status == ST_RUNNING) {
+        const int iter0 = c->st_host->iter;
+        const int64_t passes0 = c->st_host->total_passes;
+        if (c->fp64) {
+            // plain form: host-driven search, one readback per candidate pass
+            std::vector<cudaEvent_t> &ev = c->ev_one;
+            if (c->opt.timing && (rc = make_events(c, ev, 5)) != MWU_OK) return rc;
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[0], c->stream));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 0, c->stream); }));
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[1], c->stream));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, 0, c->stream); }));
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[2], c->stream));
+            c->launches += 2;
+            if ((rc = pull_state(c)) != MWU_OK) return rc;
+            int guard = 0;
+            while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE && guard++ < 256) {
+                TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, 0, c->stream); }));
+                c->launches += 1;
+                if ((rc = pull_state(c)) != MWU_OK) return rc;
+            }
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[3], c->stream));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_update(p, c->stream); }));
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[4], c->stream));
+            c->launches += 1;
+            if ((rc = pull_state(c)) != MWU_OK) return rc;
+            if (c->opt.timing && (rc = accumulate_timing(c, ev, c->st_host->iter - iter0)) != MWU_OK) return rc;
+            done += 1;
+        } else if (graph) {
+            bool chunk = n_iters - done >= c->opt.check_every;
+            int n = chunk ? c->opt.check_every : 1;
+            TRY_CUDA(c, cudaGraphLaunch(chunk ? c->gexec_chunk : c->gexec_one, c->stream));
+            c->launches += (int64_t)n * kpi;
+            if ((rc = pull_state(c)) != MWU_OK) return rc;
+            if (c->opt.timing &&
+                (rc = accumulate_timing(c, chunk ? c->ev : c->ev_one, c->st_host->iter - iter0)) != MWU_OK)
+                return rc;
+            done += n;
+        } else {
+            int n = std::min(c->opt.check_every, n_iters - done);
+            for (int k = 0; k < n; ++k) TRY_CUDA(c, enqueue_iteration(c, nullptr));
+            c->launches += (int64_t)n * kpi;
+            if ((rc = pull_state(c)) != MWU_OK) return rc;
+            done += n;
+        }
+        c->tim.cand_passes += c->st_host->total_passes - passes0;
+    }
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_flush(p, c->stream); }));
+    c->launches += 1;
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    fill_stats(c, stats);
+    int st = probe_status(*c->st_host);
+    if (st == MWU_ERR_NUMERIC) return fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a reduction");
+    return st;
+}
+
+int mwu_get_timing(mwu_ctx *c, mwu_timing *out, int32_t reset) {
+    if (!c) return MWU_ERR_INVALID;
+    if (out) *out = c->tim;
+    if (reset) c->tim = mwu_timing{};
+    return MWU_OK;
+}
+
+int mwu_direction(mwu_ctx *c, int64_t *n_positive) {
+    if (!c) return MWU_ERR_INVALID;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    if (c->st_host->status != ST_RUNNING) return fail(c, MWU_ERR_STATE, "probe not running (set a target or x first)");
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 1, c->stream); }));
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, 1, c->stream); }));
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    if (n_positive) *n_positive = c->st_host->n_pos;
+    c->have_direction = true;
+    int st = probe_status(*c->st_host);
+    if (st == MWU_ERR_NUMERIC) return fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a reduction");
+    return st == MWU_RUNNING ? MWU_OK : st;
+}
+
+int mwu_eval_candidates(mwu_ctx *c, const double *alphas, int32_t K, double *psi, double *phi, double *zmin) {
+    if (!c || !alphas || K < 1 || K > KMAX) return MWU_ERR_INVALID;
+    if (!c->have_direction) return fail(c, MWU_ERR_STATE, "call mwu_direction first");
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    DevState saved = *c->st_host;
+    DevState &h = *c->st_host;
+    h.K = K;
+    for (int k = 0; k < K; ++k) h.alpha[k] = alphas[k];
+    if ((rc = push_state(c)) != MWU_OK) return rc;
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, 1, c->stream); }));
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    for (int k = 0; k < K; ++k) {
+        if (psi) psi[k] = h.psi[k];
+        if (phi) phi[k] = h.phi[k];
+        if (zmin) zmin[k] = h.zmink[k];
+    }
+    int bad = h.status == ST_NUMERIC;
+    // restore the search state of the direction
+    saved.psi[0] = h.psi[0];
+    *c->st_host = saved;
+    if ((rc = push_state(c)) != MWU_OK) return rc;
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    return bad ? fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a candidate") : MWU_OK;
+}
+
+int mwu_search(mwu_ctx *c, double *alpha, int64_t *evals) {
+    if (!c) return MWU_ERR_INVALID;
+    if (!c->have_direction) return fail(c, MWU_ERR_STATE, "call mwu_direction first");
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    int guard = 0;
+    while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE && guard++ < 256) {
+        TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, 0, c->stream); }));
+        if ((rc = pull_state(c)) != MWU_OK) return rc;
+    }
+    if (alpha) *alpha = c->st_host->status == ST_RUNNING ? c->st_host->alpha_acc : 0.0;
+    if (evals) *evals = c->st_host->evals;
+    int st = probe_status(*c->st_host);
+    if (st == MWU_ERR_NUMERIC) return fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a candidate");
+    return st == MWU_RUNNING ? MWU_OK : st;
+}
+
+// ------------------------------------------------------------ read back
+int mwu_get_scalars(mwu_ctx *c, mwu_scalars *o) {
+    if (!c || !o) return MWU_ERR_INVALID;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    const DevState &h = *c->st_host;
+    o->eta = h.eta;
+    o->c_d = h.c_d;
+    o->eps = h.eps;
+    o->target = h.target;
+    o->s_p = h.s[0];
+    o->S_p = h.S[0];
+    o->s_c = h.s[1];
+    o->S_c = h.S[1];
+    o->ymax = h.ymax;
+    o->zmin = h.zmin;
+    o->alpha = h.alpha_acc > 0 ? h.alpha_acc : h.alpha_prev;
+    o->n_positive = h.n_pos;
+    o->n = c->n;
+    o->m_P = c->mP;
+    o->m_C = c->mC;
+    o->K = h.K;
+    o->iters = h.iter;
+    return MWU_OK;
+}
+
+int mwu_get_vector(mwu_ctx *c, int32_t which, void *dst, int64_t n, int32_t as_fp64) {
+    if (!c || !dst) return MWU_ERR_INVALID;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    const void *src = nullptr;
+    int64_t len = 0;
+    int side = -1;
+    bool dv = false;
+    switch (which) {
+    case MWU_VEC_X: len = c->n; break;
+    case MWU_VEC_D: len = c->n; break;
+    case MWU_VEC_G: len = c->n; break;
+    case MWU_VEC_H: len = c->n; break;
+    case MWU_VEC_Y: side = 0; break;
+    case MWU_VEC_Z: side = 1; break;
+    case MWU_VEC_DY: side = 0; dv = true; break;
+    case MWU_VEC_DZ: side = 1; dv = true; break;
+    default: return fail(c, MWU_ERR_INVALID, "unknown vector id");
+    }
+    auto pick = [&](auto &p) {
+        using T = std::remove_pointer_t<decltype(p.x)>;
+        const T *s = nullptr;
+        if (side < 0) s = which == MWU_VEC_X ? p.x : which == MWU_VEC_D ? p.d : which == MWU_VEC_G ? p.g : p.h;
+        else { s = dv ? p.side[side].dv : p.side[side].v; len = p.side[side].m; }
+        return (const void *)s;
+    };
+    src = c->fp64 ? pick(c->pd) : pick(c->pf);
+    if (n != len) return fail(c, MWU_ERR_INVALID, "length mismatch");
+    if (side >= 0 && !src) {   // the single objective row: a scalar held in the state
+        double v = dv ? c->st_host->dense_dv[side] : c->st_host->dense_v[side];
+        if (as_fp64) { double t = v; TRY_CUDA(c, cudaMemcpy(dst, &t, 8, cudaMemcpyDefault)); }
+        else { float t = (float)v; TRY_CUDA(c, cudaMemcpy(dst, &t, 4, cudaMemcpyDefault)); }
+        return MWU_OK;
+    }
+    bool same = (as_fp64 != 0) == c->fp64;
+    cudaPointerAttributes at{};
+    bool dst_dev = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    size_t nb = (size_t)len * (as_fp64 ? 8 : 4);
+    if (same) {
+        TRY_CUDA(c, cudaMemcpyAsync(dst, src, nb, cudaMemcpyDefault, c->stream));
+    } else if (dst_dev) {
+        if (c->fp64) TRY_CUDA(c, launch_copy_vec<double>((const double *)src, dst, len, as_fp64, c->stream));
+        else TRY_CUDA(c, launch_copy_vec<float>((const float *)src, dst, len, as_fp64, c->stream));
+    } else {
+        void *tmp = nullptr;
+        TRY_CUDA(c, cudaMalloc(&tmp, nb));
+        cudaError_t e = c->fp64 ? launch_copy_vec<double>((const double *)src, tmp, len, as_fp64, c->stream)
+                                : launch_copy_vec<float>((const float *)src, tmp, len, as_fp64, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, nb, cudaMemcpyDefault, c->stream);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return fail_cuda(c, e, "copy vector");
+    }
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MWU_OK;
+}
+
+// ------------------------------------------------------------ certificate
+// Recompute y = Px and z = Cx exactly from x and return the certified
+// objective of the homogeneous LP (c^T x / max(Px), c^T x / min(Cx), or
+// max(Oz)/min(Wz)); the probe's status is left unchanged.
+static int certify(mwu_ctx *c, double *cert) {
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_x_set(p, p.x, c->fp64 ? 1 : 0, c->stream); }));
+    c->launches += 2;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    const DevState &h = *c->st_host;
+    double M = c->target;
+    switch (c->kind) {
+    case MWU_PACKING: *cert = h.s[0] > 0 ? M * h.dense_v[1] / h.s[0] : 0.0; break;
+    case MWU_COVERING: *cert = h.s[1] > 0 ? M * h.dense_v[0] / h.s[1] : INFINITY; break;
+    case MWU_DENSEST: *cert = h.s[1] > 0 ? M * h.s[0] / h.s[1] : INFINITY; break;
+    default: *cert = h.s[1] > 0 ? h.s[0] / h.s[1] : INFINITY; break;
+    }
+    return MWU_OK;
+}
+
+static int auto_bracket(mwu_ctx *c, double *lo, double *hi) {
+    double a = 0, b = 0, dmax = 0;
+    cudaStream_t s = c->stream;
+    auto side_views = [&](int sd, RowView &rv, ColView &cv, int64_t &m) {
+        if (c->fp64) { rv = c->pd.side[sd].rv; cv = c->pd.side[sd].cv; m = c->pd.side[sd].m; }
+        else { rv = c->pf.side[sd].rv; cv = c->pf.side[sd].cv; m = c->pf.side[sd].m; }
+    };
+    RowView rv;
+    ColView cv;
+    int64_t m;
+    switch (c->kind) {
+    case MWU_PACKING:
+        // hi = sum_i c_i max_j 1/a_ji (Sec. 2.2), lo = value of x_i = 1/(n max_j a_ji)
+        side_views(0, rv, cv, m);
+        TRY_CUDA(c, bracket_stats(c->ar, cv, c->n, c->objective, &a, &b, &dmax, s));
+        *hi = a;
+        *lo = b / (double)c->n;
+        break;
+    case MWU_COVERING:
+        // hi = c^T x for x_i = 1/min_j a_ji (feasible), lo = max_j min_i c_i / a_ji
+        side_views(1, rv, cv, m);
+        TRY_CUDA(c, bracket_stats(c->ar, cv, c->n, c->objective, &a, &b, &dmax, s));
+        *hi = a;
+        TRY_CUDA(c, bracket_rowratio(c->ar, rv, m, c->objective, lo, s));
+        break;
+    case MWU_DENSEST: {
+        // lo = |E| / |V| (density of the whole graph), hi = d_max / 2
+        side_views(0, rv, cv, m);
+        int64_t nv = m, E = c->n / 2;
+        std::vector<int32_t> ptr(nv + 1);
+        TRY_CUDA(c, cudaMemcpyAsync(ptr.data(), rv.ptr, sizeof(int32_t) * (nv + 1), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(c, cudaStreamSynchronize(s));
+        int32_t dm = 0;
+        for (int64_t v = 0; v < nv; ++v) dm = std::max(dm, ptr[v + 1] - ptr[v]);
+        *lo = (double)E / (double)nv;
+        *hi = dm / 2.0;
+        break;
+    }
+    default:
+        *lo = *hi = 1.0;
+    }
+    c->ar.release_tmp();
+    return MWU_OK;
+}
+
+int mwu_solve(mwu_ctx *c, double lo, double hi, mwu_result *res) {
+    if (!c) return MWU_ERR_INVALID;
+    auto t0 = std::chrono::steady_clock::now();
+    mwu_result r{};
+    int rc;
+    const int64_t launches0 = c->launches;
+    if (c->kind == MWU_MIXED) {
+        if ((rc = mwu_set_target(c, 1.0)) != MWU_OK) return rc;
+        mwu_iter_stats s{};
+        rc = mwu_iterate(c, c->opt.max_iter, &s);
+        if (rc < 0) return rc;
+        double cert;
+        if ((rc = certify(c, &cert)) != MWU_OK) return rc;
+        r.status = s.status;
+        r.objective = cert;
+        r.probes = 1;
+        r.iters = s.iters;
+        r.evals = s.evals;
+        r.passes = s.passes;
+    } else {
+        if (lo <= 0.0 || hi <= 0.0) {
+            double alo = 0, ahi = 0;
+            if ((rc = auto_bracket(c, &alo, &ahi)) != MWU_OK) return rc;
+            if (lo <= 0.0) lo = alo;
+            if (hi <= 0.0) hi = ahi;
+        }
+        if (!(lo > 0.0) || !(hi >= lo)) return fail(c, MWU_ERR_INVALID, "bad bracket");
+        const bool maximize = c->kind == MWU_PACKING;
+        double best = maximize ? lo : hi;
+        bool have_best = false;
+        int probes = 0;
+        int64_t iters = 0, evals = 0, passes = 0;
+        size_t xb = (size_t)c->n * (c->fp64 ? 8 : 4);
+        while (hi > (1.0 + c->opt.outer_tol) * lo && probes < c->opt.max_probes) {
+            double M = std::sqrt(lo * hi);
+            if ((rc = mwu_set_target(c, M)) != MWU_OK) return rc;
+            mwu_iter_stats s{};
+            rc = mwu_iterate(c, c->opt.max_iter, &s);
+            if (rc < 0) return rc;
+            double cert;
+            if ((rc = certify(c, &cert)) != MWU_OK) return rc;
+            ++probes;
+            iters += s.iters;
+            evals += s.evals;
+            passes += s.passes;
+            bool better = maximize ? cert > best : cert < best;
+            if (better || !have_best) {
+                if (better) best = cert;
+                have_best = true;
+                const void *xs = c->fp64 ? (const void *)c->pd.x : (const void *)c->pf.x;
+                TRY_CUDA(c, cudaMemcpyAsync(c->x_best, xs, xb, cudaMemcpyDeviceToDevice, c->stream));
+            }
+            if (maximize) {
+                lo = std::max(lo, cert);
+                if (s.status == MWU_FEASIBLE) lo = std::max(lo, M);
+                else hi = std::min(hi, M);
+            } else {
+                hi = std::min(hi, cert);
+                if (s.status == MWU_FEASIBLE) hi = std::min(hi, M);
+                else lo = std::max(lo, M);
+            }
+        }
+        if (have_best) {
+            void *xs = c->fp64 ? (void *)c->pd.x : (void *)c->pf.x;
+            TRY_CUDA(c, cudaMemcpyAsync(xs, c->x_best, xb, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+        r.status = MWU_OK;
+        r.objective = best;
+        r.lo = lo;
+        r.hi = hi;
+        r.probes = probes;
+        r.iters = iters;
+        r.evals = evals;
+        r.passes = passes;
+    }
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    r.launches = c->launches - launches0;
+    if (res) *res = r;
+    return MWU_OK;
+}
+
+// ------------------------------------------------------------ potential
+int mwu_potential(mwu_ctx *c, const float *x, double *pot, float *grad_x, float *grad_obj, float *grad_vals) {
+    if (!c || !x) return MWU_ERR_INVALID;
+    int rc = mwu_set_x(c, x, 0);
+    if (rc != MWU_OK) return rc;
+    const DevState &h = *c->st_host;
+    double smx = h.s[0] + std::log(h.S[0]) / h.eta;
+    double smn = h.s[1] - std::log(h.S[1]) / h.eta;
+    if (pot) *pot = smx - smn;
+    float *gp = nullptr, *gc = nullptr;
+    if (grad_vals) {
+        bool pcsr = c->fp64 ? c->pd.side[0].rv.kind == RK_CSR : c->pf.side[0].rv.kind == RK_CSR;
+        bool ccsr = c->fp64 ? c->pd.side[1].rv.kind == RK_CSR : c->pf.side[1].rv.kind == RK_CSR;
+        if (pcsr) gp = grad_vals;
+        if (ccsr) {
+            int64_t off = 0;
+            if (pcsr) {
+                int32_t last = 0;
+                const int32_t *pp = c->fp64 ? c->pd.side[0].rv.ptr : c->pf.side[0].rv.ptr;
+                int64_t rows = c->fp64 ? c->pd.side[0].m : c->pf.side[0].m;
+                TRY_CUDA(c, cudaMemcpy(&last, pp + rows, sizeof(int32_t), cudaMemcpyDeviceToHost));
+                off = last;
+            }
+            gc = grad_vals + off;
+        }
+    }
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_potential_grads(p, x, grad_x, grad_obj, gp, gc, c->stream); }));
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_direction = false;
+    return MWU_OK;
+}
+
+// ------------------------------------------------------------ batch
+int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt, mwu_ctx **out) {
+    if (!out || !P || count <= 0) return fail(nullptr, MWU_ERR_INVALID, "bad batch arguments");
+    *out = nullptr;
+    mwu_ctx *c = new mwu_ctx();
+    c->kind = -1;
+    if (opt) c->opt = *opt;
+    else mwu_default_options(&c->opt);
+    for (int k = 0; k < count; ++k) {
+        if (P[k].kind != MWU_MAT_INCIDENCE && P[k].kind != MWU_MAT_CSR) {
+            mwu_destroy(c);
+            return fail(nullptr, MWU_ERR_INVALID, "batch instances must be PACKING over INCIDENCE or CSR");
+        }
+        mwu_ctx *sub = nullptr;
+        int rc = mwu_create(MWU_PACKING, &P[k], nullptr, nullptr, &c->opt, &sub);
+        if (rc != MWU_OK) {
+            std::string m = g_create_error;
+            mwu_destroy(c);
+            return fail(nullptr, rc, "batch instance " + std::to_string(k) + ": " + m);
+        }
+        c->batch.push_back(sub);
+    }
+    *out = c;
+    return MWU_OK;
+}
+
+int mwu_solve_batch(mwu_ctx *c, double *objective, int64_t *iters, mwu_result *total) {
+    if (!c || c->batch.empty()) return MWU_ERR_INVALID;
+    auto t0 = std::chrono::steady_clock::now();
+    mwu_result tot{};
+    for (size_t k = 0; k < c->batch.size(); ++k) {
+        mwu_result r{};
+        int rc = mwu_solve(c->batch[k], 0.0, 0.0, &r);
+        if (rc != MWU_OK) return fail(c, rc, std::string("instance ") + std::to_string(k) + ": " + c->batch[k]->err);
+        if (objective) objective[k] = r.objective;
+        if (iters) iters[k] = r.iters;
+        tot.objective += r.objective;
+        tot.probes += r.probes;
+        tot.iters += r.iters;
+        tot.evals += r.evals;
+        tot.passes += r.passes;
+        tot.launches += r.launches;
+    }
+    tot.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (total) *total = tot;
+    return MWU_OK;
+}

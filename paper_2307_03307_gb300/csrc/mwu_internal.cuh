@@ -1,0 +1,149 @@
+// Internal declarations shared by the translation units of libmwu.
+//
+// Data layout in HBM (one context):
+//   variables : x[n], d[n] (and g[n], h[n] when kept for inspection), type T
+//   side P    : y[m_P], dy[m_P]  (absent when P is the single objective row)
+//   side C    : z[m_C], dz[m_C]  (absent when C is the single objective row)
+//   structure : each side has a row view (for A x, rows j) and a column view
+//               (for A^T w, one "row" per variable i listing the rows j with
+//               A_ji != 0).  Implicit graph matrices (Sec. 5.1.2) keep only an
+//               int32 edge list and a vertex -> slot CSR.
+//   scalars   : DevState (FP64 shifts/sums, search state, status) in device memory
+//   partials  : per-block FP64 records merged by the last block of each kernel
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mwu {
+
+constexpr int KMAX = 8;           // candidates per pass (compile-time bound)
+constexpr int BLOCK = 256;        // threads per block of the sweep kernels
+constexpr int REC = 64;           // doubles per per-block partial record
+
+// Row views (constraint rows of one side, for y = A x).
+enum RowKind : int32_t {
+    RK_NONE = 0,
+    RK_CSR = 1,      // ptr/idx/val; val == nullptr -> ones
+    RK_FIXED2 = 2,   // row j = edge (u,v): x[u] + x[v]; idx = int2 edge list
+    RK_PAIRSUM = 3,  // row j: x[2j] + x[2j+1] (interweaved identity W)
+    RK_DENSE1 = 4    // the single objective row c^T x (a reduction over variables)
+};
+
+// Column views (for A^T w: per variable i, the rows j holding it).
+enum ColKind : int32_t {
+    CK_NONE = 0,
+    CK_CSR = 1,      // ptr/idx/val over variables, idx = row j
+    CK_FIXED2 = 2,   // variable i = edge (u,v): rows u and v (incidence M)
+    CK_FIXED1 = 3,   // variable i = slot: row idx[i] (pair matrix O)
+    CK_HALF1 = 4,    // variable i = slot: row i/2 (interweaved W)
+    CK_DENSE1 = 5    // single objective row: coefficient c[i]
+};
+
+struct RowView {
+    int32_t kind;
+    int32_t G;            // lanes per CSR row (power of two <= 32)
+    int64_t rows;
+    int64_t nnz;          // stored entries (CSR), 2 rows (FIXED2 / PAIRSUM), 0 (DENSE1)
+    const int32_t *ptr;   // CSR row pointer (rows+1)
+    const int32_t *idx;   // CSR column index / FIXED2 edge pairs
+    const float *val;     // CSR values or nullptr
+    const float *rdiv;    // row divisor b_j (bounds) or nullptr
+    int32_t n_heavy;      // rows longer than heavy_len, processed one block each
+    int32_t heavy_len;
+    const int32_t *heavy;
+};
+
+struct ColView {
+    int32_t kind;
+    int32_t G;
+    const int32_t *ptr;
+    const int32_t *idx;   // CSR: row ids ; FIXED2: edge pairs ; FIXED1: row per variable
+    const float *val;
+    const float *rdiv;    // divisor of row j (same array as the side's RowView)
+    const float *cvec;    // DENSE1 objective values (nullptr -> ones)
+    int32_t n_heavy;
+    int32_t heavy_len;
+    const int32_t *heavy;
+};
+
+template <class T>
+struct Side {
+    RowView rv;
+    ColView cv;
+    int32_t sign;    // +1 packing (smax), -1 covering (smin)
+    int64_t m;       // rows (1 for the objective row)
+    T *v;            // y or z (nullptr for DENSE1)
+    T *dv;           // dy or dz
+};
+
+// Probe status values stored on the device.
+enum : int32_t { ST_FEASIBLE = 0, ST_INFEASIBLE = 1, ST_MAX_ITER = 2, ST_RUNNING = 3, ST_NUMERIC = -4 };
+enum : int32_t { RS_NONE = 0, RS_COVERED = 1, RS_PACKING = 2, RS_DZERO = 3, RS_ALPHA = 4, RS_MAXITER = 5 };
+
+// Search phases.
+enum : int32_t { PH_EXP = 0, PH_REFINE = 1, PH_DONE = 2 };
+
+struct DevState {
+    // problem scalars
+    double eta, eps, c_d, target;
+    double scale[2];            // side factors: 1/M (objective row), 1/D (O), else 1
+    int32_t max_iter, K, max_passes, warm_start;
+    int32_t step_mode;          // 0 kary, 1 binary (K=1 semantics), 2 standard
+    int32_t pad0;
+    // reductions of the current y, z (side 0 = P, side 1 = C)
+    double s[2], S[2];
+    double dense_v[2], dense_dv[2];   // single objective row value and direction
+    double ymax, zmin;
+    // direction
+    long long n_pos;
+    // search
+    int32_t phase, b, passes, early;
+    double lb, ub;
+    double alpha[KMAX];
+    double psi[KMAX], phi[KMAX], zmink[KMAX];
+    int32_t okk[KMAX];
+    double alpha_acc;           // accepted alpha of this iteration (0 if none)
+    double alpha_prev;
+    int32_t pending;            // x += alpha_acc * d not yet applied
+    int32_t last_passes;
+    // status
+    int32_t status, reason, iter, numeric_bad;
+    long long evals, total_passes;
+    // last-block-done counters
+    unsigned int counter[8];
+};
+
+template <class T>
+struct Problem {
+    Side<T> side[2];
+    int64_t n;          // variables
+    T *x, *d, *g, *h;   // g, h may be nullptr (not kept)
+    DevState *st;
+    double *part_var;   // per-block records of variable-side kernels
+    double *part_row;   // per-block records of row-side kernels
+    int32_t grid_var, grid_row;   // grid sizes (blocks)
+    int32_t G_var;      // lanes per variable for CSR column views
+    int32_t heavy_var_len;
+    int32_t n_heavy_var;
+    const int32_t *heavy_var;
+};
+
+// ---------------------------------------------------------------- launchers
+// (implemented in mwu_kernels.cu for T = float and T = double)
+template <class T> cudaError_t launch_x_init(const Problem<T> &p, cudaStream_t s);                // a0: x0 + dense dots
+template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, int fp64, cudaStream_t s);
+template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s);             // a1-a3 at a new x
+template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s);      // a4-a5 (+ fused x update)
+template <class T> cudaError_t launch_cand(const Problem<T> &p, int first, int external, cudaStream_t s);  // a6-a7
+template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s);                // a8
+template <class T> cudaError_t launch_flush(const Problem<T> &p, cudaStream_t s);                 // pending x update
+template <class T> cudaError_t launch_search_begin(const Problem<T> &p, cudaStream_t s);
+template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const float *x, float *gx, float *gobj,
+                                                      float *gvals_p, float *gvals_c, cudaStream_t s);
+template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t n, int fp64, cudaStream_t s);
+
+// Kernel occupancy helper (blocks per SM of the heaviest sweep kernel).
+template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps);
+
+}  // namespace mwu

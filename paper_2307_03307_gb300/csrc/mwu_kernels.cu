@@ -1,0 +1,1188 @@
+// Hot-path kernels of one MWU iteration (Alg. 2 with the step-size search of
+// Alg. 3 / Sec. 4.2), for T = float (FP32 vectors, FP64 reductions) and
+// T = double (plain FP64 form).
+//
+// Kernel sequence of one iteration (all on one stream, no host round trip):
+//   k_dir     per variable: x += alpha_prev d (deferred update of the previous
+//             iteration), g = P^T w_p, h = C^T w_c with the weights computed
+//             in flight from y, z and the LSE shifts, d = c_d max(0,1-g/h) x,
+//             counts of d > 0, dense-row dots.  Last block: d = 0 test, search init.
+//   k_cand    per constraint row: (first pass) dv = A d, then K step candidates
+//             accumulated with online shifts.  Last block: merge, Psi_k / Phi_k
+//             in FP64, next candidates or the accepted alpha.
+//   k_update  per constraint row: v += alpha dv with online LSE of the new v.
+//             Last block: shifts and sums for the next iteration, stop test.
+//
+// Reductions: each thread accumulates in T, warps merge with shuffles, blocks
+// write one FP64 record, and the last block to finish (threadfence + atomic
+// ticket) merges the records in a fixed order.
+#include "mwu_internal.cuh"
+
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+
+namespace mwu {
+
+// ---------------------------------------------------------------- math
+__device__ __forceinline__ float t_exp(float x) { return expf(x); }
+__device__ __forceinline__ double t_exp(double x) { return exp(x); }
+__device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
+template <class T> __device__ __forceinline__ T exp_T(double x) { return t_exp((T)x); }
+__device__ __forceinline__ float t_log(float x) { return logf(x); }
+__device__ __forceinline__ double t_log(double x) { return log(x); }
+__device__ __forceinline__ float t_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double t_log1p(double x) { return log1p(x); }
+template <class T> __device__ __forceinline__ T t_inf();
+template <> __device__ __forceinline__ float t_inf<float>() { return INFINITY; }
+template <> __device__ __forceinline__ double t_inf<double>() { return (double)INFINITY; }
+
+template <class T> __device__ __forceinline__ T shfl_x(T v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+
+template <class T> __device__ __forceinline__ T group_sum(T v, int G) {
+    for (int off = G >> 1; off > 0; off >>= 1) v += shfl_x(v, off);
+    return v;
+}
+template <class T> __device__ __forceinline__ T group_max(T v, int G) {
+    for (int off = G >> 1; off > 0; off >>= 1) v = fmax(v, shfl_x(v, off));
+    return v;
+}
+
+// Block-wide sum (all threads get the result).  smem: >= 32 T.
+template <class T> __device__ T block_sum(T v, T *smem) {
+    v = group_sum(v, 32);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem[w] = v;
+    __syncthreads();
+    T r = (threadIdx.x < (blockDim.x >> 5)) ? smem[threadIdx.x] : T(0);
+    if (w == 0) r = group_sum(r, 32);
+    if (threadIdx.x == 0) smem[0] = r;
+    __syncthreads();
+    r = smem[0];
+    __syncthreads();
+    return r;
+}
+template <class T> __device__ T block_max(T v, T *smem) {
+    v = group_max(v, 32);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem[w] = v;
+    __syncthreads();
+    T r = (threadIdx.x < (blockDim.x >> 5)) ? smem[threadIdx.x] : -t_inf<T>();
+    if (w == 0) r = group_max(r, 32);
+    if (threadIdx.x == 0) smem[0] = r;
+    __syncthreads();
+    r = smem[0];
+    __syncthreads();
+    return r;
+}
+
+// Online log-sum-exp pair: sum_i exp(sgn*eta*(v_i - s)) with s the running
+// max (sgn = +1) or min (sgn = -1).  S == 0 means empty.
+template <class T> struct Lse { T s; T S; };
+
+template <class T> __device__ __forceinline__ void lse_push(Lse<T> &a, T v, T eta_sgn, int sgn) {
+    if (a.S == T(0)) { a.s = v; a.S = T(1); return; }
+    bool up = sgn > 0 ? (v > a.s) : (v < a.s);
+    if (up) { a.S = a.S * t_exp(eta_sgn * (a.s - v)) + T(1); a.s = v; }
+    else    { a.S += t_exp(eta_sgn * (v - a.s)); }
+}
+template <class T, class U> __device__ __forceinline__ void lse_merge(Lse<U> &a, U bs, U bS, U eta_sgn, int sgn) {
+    if (bS == U(0)) return;
+    if (a.S == U(0)) { a.s = bs; a.S = bS; return; }
+    U s = sgn > 0 ? fmax(a.s, bs) : fmin(a.s, bs);
+    // rescale factors in T precision (FP32 for the fast form), accumulation in U
+    U fa = (U)t_exp((T)(eta_sgn * (a.s - s)));
+    U fb = (U)t_exp((T)(eta_sgn * (bs - s)));
+    a.S = a.S * fa + bS * fb;
+    a.s = s;
+}
+
+// ---------------------------------------------------------------- last block
+__device__ __forceinline__ bool last_block_done(unsigned int *counter) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int ticket = atomicAdd(counter, 1u);
+        am_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+// ---------------------------------------------------------------- row weights
+// w_j (unnormalised) = exp(sgn*eta*(v_j - s)) / rdiv_j
+template <class T> struct WeightFn {
+    const T *v; const float *rdiv; T eta_sgn; T s;
+    __device__ __forceinline__ T operator()(int64_t j) const {
+        T w = t_exp(eta_sgn * (v[j] - s));
+        if (rdiv) w /= (T)rdiv[j];
+        return w;
+    }
+};
+
+// Column-view gather for variable i: sum_j A_ji w_j (without the side's scale).
+// Simple kinds are computed by lane 0 of the group only.
+template <class T, class F>
+__device__ __forceinline__ T col_gather(const ColView &cv, int64_t i, int lane, int G, const F &w, T dense_w) {
+    T acc = T(0);
+    switch (cv.kind) {
+    case CK_CSR: {
+        int beg = cv.ptr[i], end = cv.ptr[i + 1];
+        if (end - beg > cv.heavy_len) return T(0);   // heavy variable: block path
+        for (int k = beg + lane; k < end; k += G) {
+            T t = w(cv.idx[k]);
+            if (cv.val) t *= (T)cv.val[k];
+            acc += t;
+        }
+        break;
+    }
+    case CK_FIXED2:
+        if (lane == 0) { int2 e = reinterpret_cast<const int2 *>(cv.idx)[i]; acc = w(e.x) + w(e.y); }
+        break;
+    case CK_FIXED1:
+        if (lane == 0) acc = w(cv.idx[i]);
+        break;
+    case CK_HALF1:
+        if (lane == 0) acc = w(i >> 1);
+        break;
+    case CK_DENSE1:
+        if (lane == 0) acc = (cv.cvec ? (T)cv.cvec[i] : T(1)) * dense_w;
+        break;
+    default:
+        break;
+    }
+    return acc;
+}
+
+// Row-view product for row j: sum_k A_jk x_k (without scale and rdiv).
+template <class T>
+__device__ __forceinline__ T row_gather(const RowView &rv, int64_t j, int lane, int G, const T *x) {
+    T acc = T(0);
+    switch (rv.kind) {
+    case RK_CSR: {
+        int beg = rv.ptr[j], end = rv.ptr[j + 1];
+        if (end - beg > rv.heavy_len) return T(0);
+        for (int k = beg + lane; k < end; k += G) {
+            T t = x[rv.idx[k]];
+            if (rv.val) t *= (T)rv.val[k];
+            acc += t;
+        }
+        break;
+    }
+    case RK_FIXED2:
+        if (lane == 0) { int2 e = reinterpret_cast<const int2 *>(rv.idx)[j]; acc = x[e.x] + x[e.y]; }
+        break;
+    case RK_PAIRSUM:
+        if (lane == 0) acc = x[2 * j] + x[2 * j + 1];
+        break;
+    default:
+        break;
+    }
+    return acc;
+}
+
+template <class T> __device__ __forceinline__ bool row_is_heavy(const RowView &rv, int64_t j) {
+    return rv.kind == RK_CSR && (rv.ptr[j + 1] - rv.ptr[j]) > rv.heavy_len;
+}
+
+// Block-wide product of one heavy CSR row.
+template <class T>
+__device__ T heavy_row_gather(const RowView &rv, int64_t j, const T *x, T *smem) {
+    int beg = rv.ptr[j], end = rv.ptr[j + 1];
+    T acc = T(0);
+    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        T t = x[rv.idx[k]];
+        if (rv.val) t *= (T)rv.val[k];
+        acc += t;
+    }
+    return block_sum(acc, smem);
+}
+
+template <class T, class F>
+__device__ T heavy_col_gather(const ColView &cv, int64_t i, const F &w, T *smem) {
+    int beg = cv.ptr[i], end = cv.ptr[i + 1];
+    T acc = T(0);
+    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        T t = w(cv.idx[k]);
+        if (cv.val) t *= (T)cv.val[k];
+        acc += t;
+    }
+    return block_sum(acc, smem);
+}
+
+// (A x)_j = coef_j * sum_k val_jk x_k with coef_j = scale / rdiv_j; the scale
+// (1/M of the objective row, 1/D of O) lives in device state so that a captured
+// iteration stays valid when the probe target changes.
+template <class T> __device__ __forceinline__ T row_coef(const Side<T> &sd, int64_t j, double scale) {
+    T c = (T)scale;
+    if (sd.rv.rdiv) c /= (T)sd.rv.rdiv[j];
+    return c;
+}
+
+// ============================================================ x initialisation
+// a0: x_i = eps / (n ||P_{:,i}||_inf) (Alg. 1), and the dense-row dots c^T x.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_x_prep(Problem<T> p, const void *xin, int fp64, int mode) {
+    __shared__ double sm_d[32];
+    const Side<T> &P = p.side[0];
+    const double eps = p.st->eps;
+    double dot[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+        T xi;
+        if (mode == 0) {
+            double cm = 0.0;
+            const ColView &cv = P.cv;
+            switch (cv.kind) {
+            case CK_CSR:
+                for (int k = cv.ptr[i]; k < cv.ptr[i + 1]; ++k) {
+                    double a = (cv.val ? (double)cv.val[k] : 1.0) / (cv.rdiv ? (double)cv.rdiv[cv.idx[k]] : 1.0);
+                    cm = fmax(cm, a);
+                }
+                break;
+            case CK_FIXED2: {
+                int2 e = reinterpret_cast<const int2 *>(cv.idx)[i];
+                double a = cv.rdiv ? 1.0 / (double)cv.rdiv[e.x] : 1.0;
+                double b = cv.rdiv ? 1.0 / (double)cv.rdiv[e.y] : 1.0;
+                cm = fmax(a, b);
+                break;
+            }
+            case CK_FIXED1: cm = cv.rdiv ? 1.0 / (double)cv.rdiv[cv.idx[i]] : 1.0; break;
+            case CK_HALF1: cm = cv.rdiv ? 1.0 / (double)cv.rdiv[i >> 1] : 1.0; break;
+            case CK_DENSE1: cm = cv.cvec ? (double)cv.cvec[i] : 1.0; break;
+            default: cm = 1.0;
+            }
+            cm *= p.st->scale[0];
+            if (!(cm > 0.0)) cm = 1.0;
+            xi = (T)(eps / ((double)p.n * cm));
+        } else {
+            xi = fp64 ? (T)((const double *)xin)[i] : (T)((const float *)xin)[i];
+        }
+        p.x[i] = xi;
+        for (int s = 0; s < 2; ++s)
+            if (p.side[s].cv.kind == CK_DENSE1)
+                dot[s] += (double)(p.side[s].cv.cvec ? (T)p.side[s].cv.cvec[i] : T(1)) * (double)xi;
+    }
+    double t0 = block_sum(dot[0], sm_d);
+    double t1 = block_sum(dot[1], sm_d);
+    if (threadIdx.x == 0) {
+        p.part_var[blockIdx.x * REC + 0] = t0;
+        p.part_var[blockIdx.x * REC + 1] = t1;
+    }
+}
+
+// ============================================================ finalisation helpers
+// Merge per-block LSE records of the row kernels plus dense-row values and set
+// s, S, ymax, zmin and the stop status (Alg. 2 loop test, see the oracle).
+template <class T>
+__device__ void finalize_reductions(Problem<T> &p, int nb_row, int nb_var, bool dense_from_var, double alpha) {
+    static_assert(BLOCK == 256, "merge layout assumes 256 threads");
+    DevState *st = p.st;
+    __shared__ double sh_s[2][BLOCK], sh_S[2][BLOCK];
+    __shared__ double sh_d[32];
+    // each thread merges a strided subset of the block records ...
+    for (int s = 0; s < 2; ++s) {
+        Lse<double> a{0.0, 0.0};
+        double eta_sgn = st->eta * (double)p.side[s].sign;
+        for (int b = threadIdx.x; b < nb_row; b += blockDim.x) {
+            const double *r = p.part_row + (size_t)b * REC;
+            lse_merge<T, double>(a, r[2 * s], r[2 * s + 1], eta_sgn, p.side[s].sign);
+        }
+        sh_s[s][threadIdx.x] = a.s;
+        sh_S[s][threadIdx.x] = a.S;
+    }
+    double dense[2] = {0.0, 0.0};
+    if (dense_from_var) {
+        double d0 = 0.0, d1 = 0.0;
+        for (int b = threadIdx.x; b < nb_var; b += blockDim.x) {
+            d0 += p.part_var[(size_t)b * REC + 0];
+            d1 += p.part_var[(size_t)b * REC + 1];
+        }
+        dense[0] = block_sum(d0, sh_d);
+        dense[1] = block_sum(d1, sh_d);
+    }
+    __syncthreads();
+    // ... then a tree over the threads (fixed order)
+    for (int half = BLOCK / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) {
+            for (int s = 0; s < 2; ++s) {
+                Lse<double> a{sh_s[s][threadIdx.x], sh_S[s][threadIdx.x]};
+                lse_merge<T, double>(a, sh_s[s][threadIdx.x + half], sh_S[s][threadIdx.x + half],
+                                     st->eta * (double)p.side[s].sign, p.side[s].sign);
+                sh_s[s][threadIdx.x] = a.s;
+                sh_S[s][threadIdx.x] = a.S;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bool bad = false;
+        for (int s = 0; s < 2; ++s) {
+            const Side<T> &sd = p.side[s];
+            if (sd.rv.kind == RK_DENSE1) {
+                if (dense_from_var) st->dense_v[s] = st->scale[s] * dense[s];
+                else st->dense_v[s] += alpha * st->dense_dv[s];
+                st->s[s] = st->dense_v[s];
+                st->S[s] = 1.0;
+            } else {
+                st->s[s] = sh_s[s][0];
+                st->S[s] = sh_S[s][0];
+            }
+            if (!isfinite(st->s[s]) || !isfinite(st->S[s]) || !(st->S[s] > 0.0)) bad = true;
+        }
+        st->ymax = st->s[0];
+        st->zmin = st->s[1];
+        if (bad) {
+            st->status = ST_NUMERIC;
+            st->numeric_bad = 1;
+        } else if (st->status == ST_RUNNING) {
+            double eps = st->eps;
+            if (st->zmin >= 1.0 || st->ymax > 1.0 + eps) {
+                if (st->ymax <= (1.0 + eps) * st->zmin) { st->status = ST_FEASIBLE; st->reason = RS_COVERED; }
+                else { st->status = ST_INFEASIBLE; st->reason = RS_PACKING; }
+            } else if (st->iter >= st->max_iter) {
+                st->status = ST_MAX_ITER;
+                st->reason = RS_MAXITER;
+            }
+        }
+    }
+}
+
+// ============================================================ rows at a new x
+// y = P x, z = C x (a1) and the LSE reductions of both (a2, a3).
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_rows_eval(Problem<T> p, int gP, int nb_var) {
+    __shared__ T sm[32];
+    DevState *st = p.st;
+    int s = (blockIdx.x < gP) ? 0 : 1;
+    int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
+    int nbs = s == 0 ? gP : gridDim.x - gP;
+    const Side<T> &sd = p.side[s];
+    T eta_sgn = (T)(st->eta * sd.sign);
+    Lse<T> acc{T(0), T(0)};
+    if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
+        const RowView &rv = sd.rv;
+        // heavy rows: one block each
+        for (int h = bid; h < rv.n_heavy; h += nbs) {
+            int64_t j = rv.heavy[h];
+            T sum = heavy_row_gather(rv, j, p.x, sm);
+            if (threadIdx.x == 0) {
+                T vj = sum * row_coef(sd, j, st->scale[s]);
+                sd.v[j] = vj;
+                lse_push(acc, vj, eta_sgn, sd.sign);
+            }
+        }
+        int G = rv.G, lane = threadIdx.x & (G - 1);
+        int64_t groups = (int64_t)nbs * (blockDim.x / G);
+        int64_t gid = (int64_t)bid * (blockDim.x / G) + threadIdx.x / G;
+        int64_t stride_rows = groups;
+        int64_t warp_base = gid - (threadIdx.x & 31) / G;
+        for (int64_t base = warp_base; base < sd.m; base += stride_rows) {
+            int64_t j = base + (threadIdx.x & 31) / G;
+            bool live = j < sd.m;
+            T sum = live ? row_gather(rv, j, lane, G, p.x) : T(0);
+            sum = group_sum(sum, G);
+            if (live && lane == 0 && !row_is_heavy<T>(rv, j)) {
+                T vj = sum * row_coef(sd, j, st->scale[s]);
+                sd.v[j] = vj;
+                lse_push(acc, vj, eta_sgn, sd.sign);
+            }
+        }
+    }
+    // block merge of (s, S): warp shuffles then shared memory
+    __shared__ double bs[BLOCK / 32], bS[BLOCK / 32];
+    Lse<double> a{(double)acc.s, (double)acc.S};
+    double eds = st->eta * sd.sign;
+    for (int off = 16; off > 0; off >>= 1) {
+        double os = __shfl_xor_sync(0xffffffffu, a.s, off);
+        double oS = __shfl_xor_sync(0xffffffffu, a.S, off);
+        lse_merge<T, double>(a, os, oS, eds, sd.sign);
+    }
+    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = a.s; bS[threadIdx.x >> 5] = a.S; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Lse<double> r{0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge<T, double>(r, bs[w], bS[w], eds, sd.sign);
+        double *rec = p.part_row + (size_t)blockIdx.x * REC;
+        rec[2 * s] = r.s;
+        rec[2 * s + 1] = r.S;
+        rec[2 * (1 - s)] = 0.0;
+        rec[2 * (1 - s) + 1] = 0.0;
+    }
+    if (last_block_done(&st->counter[0])) {
+        finalize_reductions(p, gridDim.x, nb_var, true, 0.0);
+        if (threadIdx.x == 0) st->counter[0] = 0;
+    }
+}
+
+// ============================================================ gradient + direction
+// a4, a5 with the deferred x update of the previous iteration fused in.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int potential_mode, float *grad_obj) {
+    __shared__ T sm[32];
+    __shared__ double smd[32];
+    DevState *st = p.st;
+    if (!potential_mode && st->status != ST_RUNNING && !st->pending) return;
+    const bool running = potential_mode || st->status == ST_RUNNING;
+    const T alpha_prev = st->pending ? (T)st->alpha_acc : T(0);
+    const Side<T> &P = p.side[0];
+    const Side<T> &C = p.side[1];
+    WeightFn<T> wp{P.v, P.rv.rdiv, (T)st->eta, (T)st->s[0]};
+    WeightFn<T> wc{C.v, C.rv.rdiv, (T)(-st->eta), (T)st->s[1]};
+    const T fp = (T)(st->scale[0] / st->S[0]);
+    const T fc = (T)(st->scale[1] / st->S[1]);
+    const T cd = (T)st->c_d;
+    long long npos = 0;
+    double dense_dot[2] = {0.0, 0.0};
+
+    auto finish = [&](int64_t i, T sg, T sh) {
+        T xi = p.x[i];
+        if (alpha_prev != T(0)) { xi += alpha_prev * p.d[i]; p.x[i] = xi; }
+        if (!running) return;
+        T g = sg * fp, h = sh * fc;
+        if (potential_mode) {
+            p.d[i] = g - h;   // d holds the potential gradient in this mode
+            if (grad_obj) {
+                for (int s = 0; s < 2; ++s)
+                    if (p.side[s].cv.kind == CK_DENSE1)
+                        grad_obj[i] = (float)((double)p.side[s].sign * st->scale[s] * (double)xi);
+            }
+            return;
+        }
+        T di = (g < h) ? cd * (T(1) - g / h) * xi : T(0);
+        p.d[i] = di;
+        if (keep_gh) { p.g[i] = g; p.h[i] = h; }
+        npos += (di > T(0));
+        for (int s = 0; s < 2; ++s)
+            if (p.side[s].cv.kind == CK_DENSE1)
+                dense_dot[s] += (double)((p.side[s].cv.cvec ? (T)p.side[s].cv.cvec[i] : T(1)) * di);
+    };
+
+    // heavy variables (long CSR columns): whole block
+    for (int hh = blockIdx.x; hh < p.n_heavy_var; hh += gridDim.x) {
+        int64_t i = p.heavy_var[hh];
+        T sg, sh;
+        if (P.cv.kind == CK_CSR) sg = heavy_col_gather<T>(P.cv, i, wp, sm);
+        else { sg = col_gather<T>(P.cv, i, threadIdx.x, 1 << 30, wp, T(1)); sg = block_sum(threadIdx.x == 0 ? sg : T(0), sm); }
+        if (C.cv.kind == CK_CSR) sh = heavy_col_gather<T>(C.cv, i, wc, sm);
+        else { sh = col_gather<T>(C.cv, i, threadIdx.x, 1 << 30, wc, T(1)); sh = block_sum(threadIdx.x == 0 ? sh : T(0), sm); }
+        if (threadIdx.x == 0) finish(i, sg, sh);
+    }
+    int G = p.G_var, lane = threadIdx.x & (G - 1);
+    int64_t per_block = blockDim.x / G;
+    int64_t stride = (int64_t)gridDim.x * per_block;
+    int64_t warp_base = (int64_t)blockIdx.x * per_block + (threadIdx.x & ~31) / G;
+    for (int64_t base = warp_base; base < p.n; base += stride) {
+        int64_t i = base + (threadIdx.x & 31) / G;
+        bool live = i < p.n;
+        T sg = T(0), sh = T(0);
+        bool heavy = false;
+        if (live) {
+            heavy = (P.cv.kind == CK_CSR && P.cv.ptr[i + 1] - P.cv.ptr[i] > P.cv.heavy_len) ||
+                    (C.cv.kind == CK_CSR && C.cv.ptr[i + 1] - C.cv.ptr[i] > C.cv.heavy_len);
+            if (!heavy) {
+                sg = col_gather<T>(P.cv, i, lane, G, wp, T(1));
+                sh = col_gather<T>(C.cv, i, lane, G, wc, T(1));
+            }
+        }
+        sg = group_sum(sg, G);
+        sh = group_sum(sh, G);
+        if (live && lane == 0 && !heavy) finish(i, sg, sh);
+    }
+    if (potential_mode) return;
+    // block partials: n_pos, dense dots
+    double np = block_sum((double)npos, smd);
+    double d0 = block_sum(dense_dot[0], smd);
+    double d1 = block_sum(dense_dot[1], smd);
+    if (threadIdx.x == 0) {
+        double *rec = p.part_var + (size_t)blockIdx.x * REC;
+        rec[0] = np; rec[1] = d0; rec[2] = d1;
+    }
+    if (last_block_done(&st->counter[1])) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            const double *rec = p.part_var + (size_t)b * REC;
+            a0 += rec[0]; a1 += rec[1]; a2 += rec[2];
+        }
+        double np_t = block_sum(a0, smd);
+        double dd[2] = {block_sum(a1, smd), block_sum(a2, smd)};
+        if (threadIdx.x == 0) {
+            if (st->pending) {   // the deferred update of x is now applied
+                st->pending = 0;
+            }
+            if (running) {
+                st->n_pos = (long long)np_t;
+                for (int s = 0; s < 2; ++s) st->dense_dv[s] = st->scale[s] * dd[s];
+                if (np_t <= 0.0) {
+                    st->status = ST_INFEASIBLE;
+                    st->reason = RS_DZERO;
+                    st->phase = PH_DONE;
+                } else {
+                    // search initialisation (Alg. 3: alpha starts at 1; warm start optional)
+                    st->phase = PH_EXP;
+                    st->lb = 0.0;
+                    st->ub = (double)INFINITY;
+                    st->passes = 0;
+                    st->early = 0;
+                    st->alpha_acc = 0.0;
+                    int b0 = 0;
+                    if (st->warm_start && st->alpha_prev >= 1.0) b0 = (int)floor(log2(st->alpha_prev));
+                    st->b = b0;
+                    for (int k = 0; k < st->K; ++k) st->alpha[k] = ldexp(1.0, b0 + k);
+                    if (st->step_mode == 2) {   // standard step alpha = 1 (Alg. 1)
+                        st->phase = PH_DONE;
+                        st->alpha_acc = 1.0;
+                    }
+                }
+            }
+            st->counter[1] = 0;
+        }
+    }
+}
+
+// ============================================================ step candidates
+// Per-thread accumulators of K candidates for one side.
+template <class T> struct CandAcc {
+    T mx[KMAX], R[KMAX], Tt[KMAX], zm[KMAX];
+};
+
+template <class T>
+__device__ __forceinline__ void cand_init(CandAcc<T> &c, int sgn) {
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        c.mx[k] = sgn > 0 ? T(0) : -t_inf<T>();
+        c.R[k] = T(0); c.Tt[k] = T(0); c.zm[k] = t_inf<T>();
+    }
+}
+
+// Candidate schedule of one pass (identical for every row).
+//   mode 0: alpha_{k+1} = 2 alpha_k          (exponential phase of the search)
+//   mode 1: alpha_{k+1} = alpha_k + delta    (refinement on [lb, ub])
+//   mode 2: arbitrary alphas                 (mwu_eval_candidates)
+// ca[k] = alpha_k eta, al[k] = alpha_k, cd = delta eta, all in T.
+template <class T> struct CandSched {
+    int K, mode;
+    T ca[KMAX], al[KMAX];
+    T cd;
+};
+
+__device__ __forceinline__ float fast_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double fast_exp(double x) { return exp(x); }
+
+// One row (v, dv) of a side, all K candidates.  With b_k = alpha_k eta dv and
+// u_k = 1 - exp(-b_k) (cancellation free):
+//   packing (sgn = +1), x_k = eta (y - s_p) + b_k:
+//     R_k += exp(x_k - mx_k)            T_k += exp(x_k - mx_k) u_k
+//     (T is R - S without cancellation: sum e^{eta(y - s)} expm1(b_k), shifted)
+//   covering (sgn = -1), x_k = -eta (z - s_c) - b_k:
+//     R_k += exp(x_k - mx_k)            T_k += exp(-eta (z - s_c)) u_k (unshifted, <= S_c)
+//     zm_k = min(zm_k, z + alpha_k dz)
+// u_k comes from one expm1 per row and an exact recurrence along the schedule:
+// doubling b gives u' = u (2 - u); adding delta eta dv gives u' = u + u_d (1 - u).
+// mx_k is a running max per thread (rescale on a new max); exp of arguments
+// <= 0 uses the __expf intrinsic in FP32 (error 2 + 1.2|x| ulp, and terms with
+// large |x| are negligible in the sums).
+template <class T>
+__device__ __forceinline__ void cand_push(CandAcc<T> &c, const CandSched<T> &sc, int sgn, T v, T dv, T eta, T s) {
+    const int K = sc.K;
+    T b = sc.ca[0] * dv;
+    T u = -t_expm1(-b);
+    T ud = T(0);
+    if (sc.mode == 1) ud = -t_expm1(-sc.cd * dv);
+    if (sgn > 0) {
+        const T a = eta * (v - s);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < K) {
+                if (k > 0) {
+                    b = sc.ca[k] * dv;
+                    if (sc.mode == 0) u = u * (T(2) - u);
+                    else if (sc.mode == 1) u = u + ud * (T(1) - u);
+                    else u = -t_expm1(-b);
+                }
+                const T x = a + b;
+                if (x > c.mx[k]) { T f = fast_exp(c.mx[k] - x); c.R[k] *= f; c.Tt[k] *= f; c.mx[k] = x; }
+                const T t = fast_exp(x - c.mx[k]);
+                c.R[k] += t;
+                c.Tt[k] += t * u;
+            }
+        }
+    } else {
+        const T a = -eta * (v - s);
+        const T A = fast_exp(a);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < K) {
+                if (k > 0) {
+                    b = sc.ca[k] * dv;
+                    if (sc.mode == 0) u = u * (T(2) - u);
+                    else if (sc.mode == 1) u = u + ud * (T(1) - u);
+                    else u = -t_expm1(-b);
+                }
+                const T x = a - b;
+                if (x > c.mx[k]) { T f = fast_exp(c.mx[k] - x); c.R[k] *= f; c.mx[k] = x; }
+                c.R[k] += fast_exp(x - c.mx[k]);
+                c.Tt[k] += A * u;
+                c.zm[k] = fmin(c.zm[k], v + sc.al[k] * dv);
+            }
+        }
+    }
+}
+
+// merge b into a (sgn as above), in precision U with rescale factors in T
+template <class T, class U>
+__device__ __forceinline__ void cand_merge1(U &mx, U &R, U &Tt, U &zm, U bmx, U bR, U bT, U bzm, int sgn) {
+    zm = fmin(zm, bzm);
+    if (sgn < 0) {
+        Tt += bT;
+        if (bR == U(0)) return;
+        if (R == U(0)) { mx = bmx; R = bR; return; }
+        U m = fmax(mx, bmx);
+        R = R * (U)t_exp((T)(mx - m)) + bR * (U)t_exp((T)(bmx - m));
+        mx = m;
+    } else {
+        if (bR == U(0)) return;
+        if (R == U(0)) { mx = bmx; R = bR; Tt = bT; return; }
+        U m = fmax(mx, bmx);
+        U fa = (U)t_exp((T)(mx - m)), fb = (U)t_exp((T)(bmx - m));
+        R = R * fa + bR * fb;
+        Tt = Tt * fa + bT * fb;
+        mx = m;
+    }
+}
+
+// The search step after a pass (runs on one thread).  Mirrors the K-candidate
+// search of the oracle: prefix of passing candidates, early exit on
+// min(z + alpha dz) >= 1 in the exponential phase, refinement on [lb, ub].
+__device__ void search_decide(DevState *st, const int *ok, const double *zmin_k) {
+    int K = st->K;
+    int p = 0;
+    while (p < K && ok[p]) ++p;
+    st->passes += 1;
+    st->evals += K;
+    st->total_passes += 1;
+    double *al = st->alpha;
+    bool done = false;
+    double acc = 0.0;
+    if (st->phase == PH_REFINE) {
+        if (p > 0) st->lb = al[p - 1];
+        if (p < K) st->ub = al[p];
+    } else {
+        for (int k = 0; k < p; ++k)
+            if (zmin_k[k] >= 1.0) { acc = al[k]; done = true; st->early = 1; break; }
+        if (!done) {
+            if (p > 0) st->lb = fmax(st->lb, al[p - 1]);
+            if (p < K) st->ub = fmin(st->ub, al[p]);
+            if (st->lb > 0.0 && st->ub < (double)INFINITY) st->phase = PH_REFINE;
+            else if (st->lb == 0.0) {
+                if (st->b == 0) { acc = 0.0; done = true; }
+                else st->b = max(0, st->b - K);
+            } else st->b += K;
+        }
+    }
+    if (!done && st->phase == PH_REFINE && (st->ub - st->lb) <= st->eps * st->lb) { acc = st->lb; done = true; }
+    if (!done && st->passes >= st->max_passes) { acc = st->lb; done = true; }
+    if (done) {
+        st->phase = PH_DONE;
+        st->last_passes = st->passes;
+        if (acc >= 1.0) st->alpha_acc = acc;
+        else {
+            st->alpha_acc = 0.0;
+            st->status = ST_INFEASIBLE;
+            st->reason = RS_ALPHA;
+        }
+        return;
+    }
+    // next candidate set
+    if (st->phase == PH_REFINE) {
+        double lb = st->lb, ub = st->ub;
+        for (int j = 1; j <= K; ++j) al[j - 1] = lb + j * (ub - lb) / (K + 1);
+    } else {
+        for (int k = 0; k < K; ++k) al[k] = ldexp(1.0, st->b + k);
+    }
+}
+
+// a6 + a7: dv = A d on the first pass, then K candidates per row.
+// external = 1: evaluate st->alpha[0..K) and store psi/phi/zmin, no decision.
+template <class T>
+__global__ void __launch_bounds__(BLOCK, 3) k_cand(Problem<T> p, int gP, int first, int external) {
+    __shared__ T sm[32];
+    __shared__ CandSched<T> s_sc;
+    DevState *st = p.st;
+    if (st->status != ST_RUNNING) return;
+    const bool searching = external || st->phase != PH_DONE;
+    if (!first && !searching) return;
+    const int K = st->K;
+    int s = (blockIdx.x < gP) ? 0 : 1;
+    int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
+    int nbs = s == 0 ? gP : gridDim.x - gP;
+    const Side<T> &sd = p.side[s];
+    const T eta = (T)st->eta;
+    const T sh = (T)st->s[s];
+    if (threadIdx.x == 0) {
+        s_sc.K = K;
+        s_sc.mode = external ? 2 : (st->phase == PH_EXP ? 0 : 1);
+        s_sc.cd = (T)((st->ub - st->lb) / (K + 1) * st->eta);
+    }
+    if (threadIdx.x < KMAX) {
+        double a = threadIdx.x < K ? st->alpha[threadIdx.x] : 0.0;
+        s_sc.ca[threadIdx.x] = (T)(a * st->eta);
+        s_sc.al[threadIdx.x] = (T)a;
+    }
+    __syncthreads();
+    const CandSched<T> &sc = s_sc;
+    CandAcc<T> acc;
+    cand_init(acc, sd.sign);
+    const int64_t m = sd.m;
+    const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nbs * blockDim.x;
+    const bool csr_first = first && sd.rv.kind == RK_CSR;
+    if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) {
+        // single objective row: handled exactly by the decision step
+    } else if (!csr_first) {
+        // stream: four consecutive rows per thread; dv from the stored vector or,
+        // on the first pass, from the implicit row kinds (pairs / edges)
+        const RowView &rv = sd.rv;
+        const double scale = st->scale[s];
+        for (int64_t j0 = 4 * tid; j0 < m; j0 += 4 * nthr) {
+            T vv[4], dd[4];
+            const int nr = (int)min((int64_t)4, m - j0);
+            if (nr == 4 && sizeof(T) == 4) {
+                float4 a4 = *reinterpret_cast<const float4 *>(sd.v + j0);
+                vv[0] = a4.x; vv[1] = a4.y; vv[2] = a4.z; vv[3] = a4.w;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) vv[r] = r < nr ? sd.v[j0 + r] : T(0);
+            }
+            if (!first) {
+                if (nr == 4 && sizeof(T) == 4) {
+                    float4 b4 = *reinterpret_cast<const float4 *>(sd.dv + j0);
+                    dd[0] = b4.x; dd[1] = b4.y; dd[2] = b4.z; dd[3] = b4.w;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) dd[r] = r < nr ? sd.dv[j0 + r] : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    dd[r] = T(0);
+                    if (r < nr) {
+                        int64_t j = j0 + r;
+                        T sum = (rv.kind == RK_PAIRSUM) ? p.d[2 * j] + p.d[2 * j + 1] : row_gather(rv, j, 0, 1, p.d);
+                        dd[r] = sum * row_coef(sd, j, scale);
+                    }
+                }
+                if (nr == 4 && sizeof(T) == 4) {
+                    *reinterpret_cast<float4 *>(sd.dv + j0) = make_float4((float)dd[0], (float)dd[1], (float)dd[2], (float)dd[3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (r < nr) sd.dv[j0 + r] = dd[r];
+                }
+            }
+            if (searching) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r < nr) cand_push(acc, sc, sd.sign, vv[r], dd[r], eta, sh);
+            }
+        }
+    } else {
+        // first pass over explicit CSR rows: heavy rows one block each, light rows by
+        // groups of G lanes; a group forms G row sums in turn and lane r keeps row r,
+        // so the candidate work is spread over all lanes
+        const RowView &rv = sd.rv;
+        const double scale = st->scale[s];
+        for (int h = bid; h < rv.n_heavy; h += nbs) {
+            int64_t j = rv.heavy[h];
+            T dvj = heavy_row_gather(rv, j, p.d, sm) * row_coef(sd, j, scale);
+            if (threadIdx.x == 0) {
+                sd.dv[j] = dvj;
+                if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
+            }
+        }
+        const int G = rv.G, lane = threadIdx.x & (G - 1), grp = (threadIdx.x & 31) / G;
+        const int64_t wid = (int64_t)bid * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        const int64_t nw = (int64_t)nbs * (blockDim.x >> 5);
+        for (int64_t base = wid * 32; base < m; base += nw * 32) {
+            T mine = T(0);
+            for (int r = 0; r < G; ++r) {
+                int64_t j = base + grp * G + r;
+                T sum = j < m ? row_gather(rv, j, lane, G, p.d) : T(0);
+                sum = group_sum(sum, G);
+                if (lane == r) mine = sum;
+            }
+            int64_t j = base + grp * G + lane;
+            if (j < m && !row_is_heavy<T>(rv, j)) {
+                T dvj = mine * row_coef(sd, j, scale);
+                sd.dv[j] = dvj;
+                if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
+            }
+        }
+    }
+    if (!searching) return;   // standard step: dv written, nothing to evaluate
+    // block merge: warp shuffles in T, then warps in FP64
+    __shared__ double wm[BLOCK / 32][KMAX][4];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        T mx = acc.mx[k], R = acc.R[k], Tt = acc.Tt[k], zm = acc.zm[k];
+        for (int off = 16; off > 0; off >>= 1) {
+            T omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off);
+            cand_merge1<T, T>(mx, R, Tt, zm, omx, oR, oT, oz, sd.sign);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            wm[threadIdx.x >> 5][k][0] = mx; wm[threadIdx.x >> 5][k][1] = R;
+            wm[threadIdx.x >> 5][k][2] = Tt; wm[threadIdx.x >> 5][k][3] = zm;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < KMAX) {
+        int k = threadIdx.x;
+        double mx = sd.sign > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            cand_merge1<T, double>(mx, R, Tt, zm, wm[w][k][0], wm[w][k][1], wm[w][k][2], wm[w][k][3], sd.sign);
+        double *rec = p.part_row + (size_t)blockIdx.x * REC;
+        rec[k * 4 + 0] = mx; rec[k * 4 + 1] = R; rec[k * 4 + 2] = Tt; rec[k * 4 + 3] = zm;
+        rec[32] = s;
+    }
+    if (last_block_done(&st->counter[2])) {
+        __shared__ double fin[2][KMAX][4];
+        // 16 lanes per (side, k) pair, strided over the block records, then a
+        // shuffle tree inside each half warp
+        {
+            static_assert(BLOCK == 16 * 2 * KMAX, "merge layout assumes 256 threads and KMAX = 8");
+            int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
+            int ss = q / KMAX, k = q % KMAX;
+            int sg = p.side[ss].sign;
+            double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
+            int b0 = ss == 0 ? 0 : gP, b1 = ss == 0 ? gP : gridDim.x;
+#pragma unroll 4
+            for (int b = b0 + ln; b < b1; b += 16) {
+                const double *rec = p.part_row + (size_t)b * REC + k * 4;
+                cand_merge1<T, double>(mx, R, Tt, zm, rec[0], rec[1], rec[2], rec[3], sg);
+            }
+            for (int off = 8; off > 0; off >>= 1) {
+                double omx = __shfl_xor_sync(0xffffffffu, mx, off), oR = __shfl_xor_sync(0xffffffffu, R, off);
+                double oT = __shfl_xor_sync(0xffffffffu, Tt, off), oz = __shfl_xor_sync(0xffffffffu, zm, off);
+                cand_merge1<T, double>(mx, R, Tt, zm, omx, oR, oT, oz, sg);
+            }
+            if (ln == 0) {
+                // Psi_k (packing side) or Phi_k (covering side) from the merged sums.  The
+                // transcendentals run in T precision (FP32 for the fast form, whose FP64 units
+                // are scarce), the sums and the final combination in FP64.
+                const Side<T> &q = p.side[ss];
+                double a = k < K ? st->alpha[k] : 0.0;
+                double val;
+                double eta_d = st->eta, S0 = st->S[ss];
+                double lS0 = (double)t_log((T)S0);
+                if (q.rv.kind == RK_DENSE1) {
+                    val = a * st->dense_dv[ss];          // single row: smax / smin exact
+                } else if (sg > 0) {
+                    // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p)
+                    double lq = mx + (double)t_log((T)Tt) - lS0;
+                    val = (lq < 0.0) ? (double)t_log1p((T)exp_T<T>(lq)) / eta_d
+                                     : (mx + (double)t_log((T)R) - lS0) / eta_d;
+                } else {
+                    // Phi = -(1/eta) ln(R_true / S_c) = -(1/eta) ln(1 - T_true / S_c)
+                    double qv = Tt / S0;
+                    val = (qv <= 0.5) ? -(double)t_log1p((T)(-qv)) / eta_d
+                                      : -(mx + (double)t_log((T)R) - lS0) / eta_d;
+                }
+                fin[ss][k][0] = val;
+                fin[ss][k][3] = (q.rv.kind == RK_DENSE1) ? st->dense_v[ss] + a * st->dense_dv[ss] : zm;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int ok[KMAX];
+            double zmk[KMAX];
+            bool bad = false;
+            for (int k = 0; k < K; ++k) {
+                double val[2] = {fin[0][k][0], fin[1][k][0]};
+                if (!isfinite(val[0]) || !isfinite(val[1])) bad = true;
+                st->psi[k] = val[0];
+                st->phi[k] = val[1];
+                zmk[k] = fin[1][k][3];
+                st->zmink[k] = zmk[k];
+                ok[k] = val[1] >= val[0];
+                st->okk[k] = ok[k];
+            }
+            if (bad) {
+                st->status = ST_NUMERIC;
+                st->numeric_bad = 2;
+            } else if (!external) {
+                search_decide(st, ok, zmk);
+            }
+            st->counter[2] = 0;
+        }
+    }
+}
+
+// ============================================================ update
+// a8: v += alpha dv with the LSE reductions of the new v; x is updated lazily
+// by the next k_dir (or k_flush).
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
+    DevState *st = p.st;
+    if (st->status != ST_RUNNING || st->phase != PH_DONE || !(st->alpha_acc >= 1.0)) return;
+    const double alpha = st->alpha_acc;
+    int s = (blockIdx.x < gP) ? 0 : 1;
+    int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
+    int nbs = s == 0 ? gP : gridDim.x - gP;
+    const Side<T> &sd = p.side[s];
+    T eta_sgn = (T)(st->eta * sd.sign);
+    const T a = (T)alpha;
+    Lse<T> acc{T(0), T(0)};
+    if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
+        const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x, nthr = (int64_t)nbs * blockDim.x;
+        for (int64_t j0 = 4 * tid; j0 < sd.m; j0 += 4 * nthr) {
+            const int nr = (int)min((int64_t)4, sd.m - j0);
+            if (nr == 4 && sizeof(T) == 4) {
+                float4 v4 = *reinterpret_cast<const float4 *>(sd.v + j0);
+                float4 d4 = *reinterpret_cast<const float4 *>(sd.dv + j0);
+                v4.x += (float)a * d4.x; v4.y += (float)a * d4.y; v4.z += (float)a * d4.z; v4.w += (float)a * d4.w;
+                *reinterpret_cast<float4 *>(sd.v + j0) = v4;
+                lse_push(acc, (T)v4.x, eta_sgn, sd.sign);
+                lse_push(acc, (T)v4.y, eta_sgn, sd.sign);
+                lse_push(acc, (T)v4.z, eta_sgn, sd.sign);
+                lse_push(acc, (T)v4.w, eta_sgn, sd.sign);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (r >= nr) break;
+                    T vj = sd.v[j0 + r] + a * sd.dv[j0 + r];
+                    sd.v[j0 + r] = vj;
+                    lse_push(acc, vj, eta_sgn, sd.sign);
+                }
+            }
+        }
+    }
+    __shared__ double bs[BLOCK / 32], bS[BLOCK / 32];
+    Lse<double> r{(double)acc.s, (double)acc.S};
+    double eds = st->eta * sd.sign;
+    for (int off = 16; off > 0; off >>= 1) {
+        double os = __shfl_xor_sync(0xffffffffu, r.s, off);
+        double oS = __shfl_xor_sync(0xffffffffu, r.S, off);
+        lse_merge<T, double>(r, os, oS, eds, sd.sign);
+    }
+    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = r.s; bS[threadIdx.x >> 5] = r.S; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Lse<double> q{0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge<T, double>(q, bs[w], bS[w], eds, sd.sign);
+        double *rec = p.part_row + (size_t)blockIdx.x * REC;
+        rec[2 * s] = q.s; rec[2 * s + 1] = q.S;
+        rec[2 * (1 - s)] = 0.0; rec[2 * (1 - s) + 1] = 0.0;
+    }
+    if (last_block_done(&st->counter[3])) {
+        if (threadIdx.x == 0) {
+            st->iter += 1;
+            st->pending = 1;
+            st->alpha_prev = alpha;
+        }
+        __syncthreads();
+        finalize_reductions(p, gridDim.x, 0, false, alpha);
+        if (threadIdx.x == 0) st->counter[3] = 0;
+    }
+}
+
+// apply a pending x += alpha d
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_flush(Problem<T> p) {
+    DevState *st = p.st;
+    if (!st->pending) return;
+    const T a = (T)st->alpha_acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x)
+        p.x[i] += a * p.d[i];
+    if (last_block_done(&st->counter[4])) {
+        if (threadIdx.x == 0) { st->pending = 0; st->counter[4] = 0; }
+    }
+}
+
+// d pot / d val for the explicit CSR values of one side: sign * coef_j * w_j * x_i
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_grad_vals(Problem<T> p, int s, float *gv) {
+    DevState *st = p.st;
+    const Side<T> &sd = p.side[s];
+    const RowView &rv = sd.rv;
+    const double eta_sgn = st->eta * sd.sign;
+    const double s0 = st->s[s], S0 = st->S[s];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < sd.m; j += (int64_t)gridDim.x * blockDim.x) {
+        double w = exp(eta_sgn * ((double)sd.v[j] - s0)) / S0;
+        double coef = st->scale[s] / (rv.rdiv ? (double)rv.rdiv[j] : 1.0);
+        for (int k = rv.ptr[j]; k < rv.ptr[j + 1]; ++k)
+            gv[k] = (float)((double)sd.sign * coef * w * (double)p.x[rv.idx[k]]);
+    }
+}
+
+template <class T, class U>
+__global__ void k_convert(const T *src, U *dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (U)src[i];
+}
+
+// ============================================================ launchers
+static int grid_for(int64_t n, int cap) {
+    int64_t g = (n + BLOCK - 1) / BLOCK;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC) {
+    int total = p.grid_row;
+    auto work = [&](const Side<T> &s) -> double {   // gathers + rows
+        if (s.rv.kind == RK_DENSE1 || s.rv.kind == RK_NONE) return 0.0;
+        if (s.rv.kind == RK_CSR) return (double)s.rv.nnz + (double)s.m;
+        return 3.0 * (double)s.m;
+    };
+    double wP = work(p.side[0]), wC = work(p.side[1]);
+    auto need = [&](const Side<T> &s) -> int {
+        if (s.rv.kind == RK_DENSE1 || s.rv.kind == RK_NONE) return 0;
+        int64_t groups_per_block = BLOCK / s.rv.G;
+        int64_t g = (s.m + groups_per_block - 1) / groups_per_block;
+        return (int)std::max<int64_t>(1, std::max<int64_t>(g, (int64_t)s.rv.n_heavy));
+    };
+    int nP = need(p.side[0]), nC = need(p.side[1]);
+    if (wP + wC <= 0.0) { *gP = 1; *gC = 0; return; }
+    int aP = (int)((double)total * wP / (wP + wC) + 0.5);
+    if (wP > 0 && aP < 1) aP = 1;
+    if (wC > 0 && total - aP < 1) aP = total - 1;
+    int aC = total - aP;
+    if (wP <= 0) aP = 0;
+    if (wC <= 0) aC = 0;
+    *gP = std::min(aP, nP);
+    *gC = std::min(aC, nC);
+    if (*gP + *gC == 0) *gP = 1;
+}
+
+template <class T> cudaError_t launch_x_init(const Problem<T> &p, cudaStream_t s) {
+    int g = grid_for(p.n, p.grid_var);
+    k_x_prep<T><<<g, BLOCK, 0, s>>>(p, nullptr, 0, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int gP, gC;
+    split_rows(p, &gP, &gC);
+    k_rows_eval<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, g);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, int fp64, cudaStream_t s) {
+    int g = grid_for(p.n, p.grid_var);
+    k_x_prep<T><<<g, BLOCK, 0, s>>>(p, x, fp64, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int gP, gC;
+    split_rows(p, &gP, &gC);
+    k_rows_eval<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, g);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s) {
+    int gP, gC;
+    split_rows(p, &gP, &gC);
+    k_rows_eval<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, 0);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s) {
+    int64_t per_block = BLOCK / p.G_var;
+    int64_t need = std::max<int64_t>((p.n + per_block - 1) / per_block, p.n_heavy_var);
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, p.grid_var));
+    k_dir<T><<<g, BLOCK, 0, s>>>(p, keep_gh, 0, nullptr);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_cand(const Problem<T> &p, int first, int external, cudaStream_t s) {
+    int gP, gC;
+    split_rows(p, &gP, &gC);
+    k_cand<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, first, external);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s) {
+    int gP, gC;
+    split_rows(p, &gP, &gC);
+    // the update is a plain stream over the rows: size by rows, not groups
+    auto need = [&](const Side<T> &sd) -> int {
+        if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) return 0;
+        return grid_for(sd.m, p.grid_row);
+    };
+    int nP = need(p.side[0]), nC = need(p.side[1]);
+    gP = std::min(std::max(gP, nP > 0 ? 1 : 0), nP);
+    gC = std::min(std::max(gC, nC > 0 ? 1 : 0), nC);
+    if (gP + gC == 0) gP = 1;
+    k_update<T><<<gP + gC, BLOCK, 0, s>>>(p, gP);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_flush(const Problem<T> &p, cudaStream_t s) {
+    k_flush<T><<<grid_for(p.n, p.grid_var), BLOCK, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_search_begin(const Problem<T> &, cudaStream_t) { return cudaSuccess; }
+
+template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const float *x, float *gx, float *gobj,
+                                                      float *gvals_p, float *gvals_c, cudaStream_t s) {
+    (void)x;
+    int64_t per_block = BLOCK / p.G_var;
+    int64_t need = std::max<int64_t>((p.n + per_block - 1) / per_block, p.n_heavy_var);
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, p.grid_var));
+    k_dir<T><<<g, BLOCK, 0, s>>>(p, 0, 1, gobj);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (gx) {
+        k_convert<T, float><<<grid_for(p.n, p.grid_var), BLOCK, 0, s>>>(p.d, gx, p.n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (gvals_p && p.side[0].rv.kind == RK_CSR) {
+        k_grad_vals<T><<<grid_for(p.side[0].m, p.grid_row), BLOCK, 0, s>>>(p, 0, gvals_p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (gvals_c && p.side[1].rv.kind == RK_CSR) {
+        k_grad_vals<T><<<grid_for(p.side[1].m, p.grid_row), BLOCK, 0, s>>>(p, 1, gvals_c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t n, int fp64, cudaStream_t s) {
+    int g = grid_for(n, 4096);
+    if (fp64) k_convert<T, double><<<g, BLOCK, 0, s>>>(src, (double *)dst, n);
+    else k_convert<T, float><<<g, BLOCK, 0, s>>>(src, (float *)dst, n);
+    return cudaGetLastError();
+}
+
+template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps) {
+    int a = 0, b = 0, c = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dir<T>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cand<T>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_update<T>, BLOCK, 0);
+    *var_bps = a > 0 ? a : 1;
+    int r = b < c ? b : c;
+    *row_bps = r > 0 ? r : 1;
+    return 0;
+}
+
+#define MWU_INSTANTIATE(T)                                                                                     \
+    template cudaError_t launch_x_init<T>(const Problem<T> &, cudaStream_t);                                   \
+    template cudaError_t launch_x_set<T>(const Problem<T> &, const void *, int, cudaStream_t);                 \
+    template cudaError_t launch_rows_eval<T>(const Problem<T> &, cudaStream_t);                                \
+    template cudaError_t launch_dir<T>(const Problem<T> &, int, cudaStream_t);                                 \
+    template cudaError_t launch_cand<T>(const Problem<T> &, int, int, cudaStream_t);                           \
+    template cudaError_t launch_update<T>(const Problem<T> &, cudaStream_t);                                   \
+    template cudaError_t launch_flush<T>(const Problem<T> &, cudaStream_t);                                    \
+    template cudaError_t launch_search_begin<T>(const Problem<T> &, cudaStream_t);                             \
+    template cudaError_t launch_potential_grads<T>(const Problem<T> &, const float *, float *, float *,        \
+                                                   float *, float *, cudaStream_t);                            \
+    template cudaError_t launch_copy_vec<T>(const T *, void *, int64_t, int, cudaStream_t);                    \
+    template int sweep_blocks_per_sm<T>(int *, int *);
+
+MWU_INSTANTIATE(float)
+MWU_INSTANTIATE(double)
+
+}  // namespace mwu
