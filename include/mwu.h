@@ -48,7 +48,8 @@ typedef enum {
 
 /* Infeasibility reasons reported in mwu_iter_stats.reason. */
 enum { MWU_REASON_NONE = 0, MWU_REASON_COVERED = 1, MWU_REASON_PACKING = 2,
-       MWU_REASON_D_ZERO = 3, MWU_REASON_ALPHA = 4, MWU_REASON_MAX_ITER = 5 };
+       MWU_REASON_D_ZERO = 3, MWU_REASON_ALPHA = 4, MWU_REASON_MAX_ITER = 5,
+       MWU_REASON_RATIO = 6 /* FEASIBLE by the scale-invariant rule (stop_rule = 1) */ };
 
 /* ------------------------------------------------------------ problem kind */
 typedef enum {
@@ -109,6 +110,16 @@ typedef struct {
     int32_t group;             /* lanes per CSR row, 0 = automatic; else 1,2,4,8,16,32       */
     int32_t timing;            /* record CUDA events around each kernel class of every
                                   iteration (read with mwu_get_timing); default 0           */
+    int32_t stop_rule;         /* 0 (default): a probe ends FEASIBLE once min(Cx) >= 1 with
+                                  max(Px) <= (1+eps) min(Cx) (Alg. 2); 1: as soon as
+                                  max(Px) <= (1+eps) min(Cx), min(Cx) > 0 -- x/min(Cx) is
+                                  then the (1+eps)-relative solution of Theorem 4.1 (the LP
+                                  is homogeneous).  Inside mwu_solve a probe also ends as
+                                  soon as its certificate closes the search bracket.     */
+    double grad_tol;           /* gradient test d_i > 0 iff g_i < (1 - grad_tol) h_i; < 0
+                                  selects the default: 2^-16 for F32_R64 (a few FP32
+                                  roundings of g/h, below which d = 0 is undecidable in
+                                  FP32), 0 for FP64 (the exact test of Alg. 2)             */
     void *stream;              /* cudaStream_t; NULL = a non-blocking stream the context
                                   creates and owns                                           */
 } mwu_options;

@@ -114,15 +114,17 @@ def gradients(P, C, y, z, eta):
     return P.T @ grad_smax(y, eta), C.T @ grad_smin(z, eta)
 
 
-def direction(g, h, x, c_d):
+def direction(g, h, x, c_d, tol=0.0):
     """d_i = c_d max{0, 1 - g_i/h_i} x_i (Alg. 2, new step direction).
 
     Reading: h_i = 0 gives d_i = 0 (the variable cannot help any covering row).
+    ``tol`` > 0 makes the gradient test g_i < (1 - tol) h_i: the test d = 0 of
+    Alg. 2 is then decided at the resolution of the arithmetic (0 is exact).
     """
     g = np.asarray(g, dtype=np.float64)
     h = np.asarray(h, dtype=np.float64)
     d = np.zeros_like(np.asarray(x, dtype=np.float64))
-    ok = (h > 0) & (g < h)
+    ok = (h > 0) & (g < (1.0 - tol) * h)
     d[ok] = c_d * (1.0 - g[ok] / h[ok]) * np.asarray(x, dtype=np.float64)[ok]
     return d
 
@@ -301,7 +303,8 @@ class MWUResult:
 
 
 def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_passes=64,
-        double_single=True, warm_start=False, x0=None, on_iter=None):
+        double_single=True, warm_start=False, x0=None, on_iter=None, stop_rule=0, grad_tol=0.0,
+        ratio_stop=0.0):
     """MWU_STEPSIZE_SEARCH (Alg. 2) on explicit P (m_P x n) and C (m_C x n).
 
     Per iteration: test, g and h, d, max(d) = 0 -> INFEASIBLE, dy = Pd and
@@ -311,13 +314,19 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
 
     Reading of the stopping rule (Alg. 2 loops until the constraints are
     approximately met; the text after it ends MWU once a step pushes the
-    packing rows past 1, with a y/z typo in that formula): before each
-    iteration the probe stops when min(z) >= 1 or max(y) > 1 + eps.  It is
-    FEASIBLE when max(y) <= (1 + eps) min(z): the LP is homogeneous, so
-    x / min(z) then meets Px <= (1 + eps) 1 and Cx >= 1, the (1 + eps)-relative
-    solution of Theorem 4.1.  Otherwise it is INFEASIBLE.  ``max_iter`` (5000
-    in Sec. 6) ends it as MAX_ITER.  ``step`` is "kary" (K candidates per
-    pass), "binary" (Alg. 3) or "standard" (alpha = 1, Alg. 1).
+    packing rows past 1, with a y/z typo in that formula).  The LP is
+    homogeneous: whenever max(y) <= (1 + eps) min(z) with min(z) > 0, x / min(z)
+    meets Px <= (1 + eps) 1 and Cx >= 1, the (1 + eps)-relative solution of
+    Theorem 4.1.  Before each iteration:
+      stop_rule = 0 (default, Alg. 2): min(z) >= 1 or max(y) > 1 + eps ends it,
+      FEASIBLE when the ratio test holds, INFEASIBLE otherwise;
+      stop_rule = 1: the ratio test alone already ends the probe FEASIBLE.
+    ``ratio_stop`` > 0 adds the exit max(y) <= ratio_stop min(z) (FEASIBLE);
+    the outer search uses it to stop a probe whose certificate closes the
+    bracket.
+    ``max_iter`` (5000 in Sec. 6) ends it as MAX_ITER.  ``step`` is "kary" (K
+    candidates per pass), "binary" (Alg. 3) or "standard" (alpha = 1, Alg. 1).
+    ``grad_tol`` is the tolerance of the gradient test (see ``direction``).
     """
     P = sp.csr_matrix(P, dtype=np.float64)
     C = sp.csr_matrix(C, dtype=np.float64)
@@ -334,6 +343,10 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
     reason = ""
     while True:
         ymax, zmin = y.max(), z.min()
+        rho = max(ratio_stop, (1.0 + eps) if stop_rule == 1 else 0.0)
+        if rho > 0.0 and zmin > 0.0 and ymax <= rho * zmin:
+            status, reason = FEASIBLE, "ratio"
+            break
         if zmin >= 1.0 or ymax > 1.0 + eps:
             if ymax <= (1.0 + eps) * zmin:
                 status, reason = FEASIBLE, "covered"
@@ -344,7 +357,7 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
             status, reason = MAX_ITER, "max_iter"
             break
         g, h = gradients(P, C, y, z, eta)
-        d = direction(g, h, x, c_d)
+        d = direction(g, h, x, c_d, grad_tol)
         if d.max() <= 0.0:
             status, reason = INFEASIBLE, "d=0"
             break
@@ -439,7 +452,9 @@ def solve_packing(A, c, eps, *, tol=None, **kw):
     Reading (the paper gives no bracket or tolerance): geometric bisection
     M = sqrt(lo hi) until hi <= (1 + tol) lo, tol = eps by default.  A FEASIBLE
     probe raises lo to M, any other lowers hi to M; every probe's certified
-    objective also raises lo.  The answer is the best certified objective.
+    objective also raises lo.  A probe also stops (FEASIBLE) as soon as its
+    certificate M min(z)/max(y) reaches hi/(1 + tol), which ends the search.
+    The answer is the best certified objective.
     """
     tol = eps if tol is None else tol
     A = sp.csc_matrix(A, dtype=np.float64)
@@ -455,7 +470,7 @@ def solve_packing(A, c, eps, *, tol=None, **kw):
     tot = {"iters": 0, "evals": 0}
 
     def probe(M, lo, hi):
-        r = mwu(A, lpm.objective_row(c, M), eps, **kw)
+        r = mwu(A, lpm.objective_row(c, M), eps, ratio_stop=(1 + tol) * M / hi, **kw)
         cert = certified_packing(A, c, r.x)
         tot["iters"] += r.iters
         tot["evals"] += r.evals
@@ -504,7 +519,7 @@ def solve_covering(A, c, eps, *, tol=None, **kw):
     tot = {"iters": 0, "evals": 0}
 
     def probe(M, lo, hi):
-        r = mwu(lpm.objective_row(c, M), A, eps, **kw)
+        r = mwu(lpm.objective_row(c, M), A, eps, ratio_stop=(1 + tol) * lo / M, **kw)
         cert = certified_covering(A, c, r.x)
         tot["iters"] += r.iters
         tot["evals"] += r.evals
@@ -540,7 +555,7 @@ def solve_densest(n, u, v, eps, *, tol=None, **kw):
     tot = {"iters": 0, "evals": 0}
 
     def probe(D, lo, hi):
-        r = mwu(O / D, W, eps, **kw)
+        r = mwu(O / D, W, eps, ratio_stop=(1 + tol) * lo / D, **kw)
         cert = certified_densest(O, W, r.x)
         tot["iters"] += r.iters
         tot["evals"] += r.evals

@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -49,6 +50,7 @@ struct mwu_ctx {
     int n_sms = 0;
     double target = 1.0;
     bool have_direction = false;
+    bool trace = false;          // MWU_TRACE=1: one line per probe on stderr
     // batch front end
     std::vector<mwu_ctx *> batch;
 };
@@ -106,6 +108,9 @@ int mwu_default_options(mwu_options *o) {
     o->use_graph = 1;
     o->check_every = 8;
     o->group = 0;
+    o->timing = 0;
+    o->stop_rule = 0;
+    o->grad_tol = -1.0;   // precision default
     o->stream = nullptr;
     return MWU_OK;
 }
@@ -178,7 +183,7 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
         float *tv;
         TRY_CUDA(c, csr_transpose(c->ar, ptr, idx, val, A->rows, A->cols, A->nnz, &tp, &ti, &tv, s));
         double avg_r = (double)A->nnz / (double)A->rows, avg_c = (double)A->nnz / (double)A->cols;
-        sb.rv = RowView{RK_CSR, choose_G(avg_r, forced_G), A->rows, A->nnz, ptr, idx, val, rdiv, 0, 0, nullptr};
+        sb.rv = RowView{RK_CSR, choose_G(avg_r, forced_G), A->rows, A->nnz, ptr, idx, val, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
         sb.cv = ColView{CK_CSR, choose_G(avg_c, forced_G), tp, ti, tv, rdiv, nullptr, 0, 0, nullptr};
         sb.m = A->rows;
         sb.nvar = A->cols;
@@ -211,25 +216,25 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
                 if ((rc = check_err_flag(c, d_err)) != MWU_OK) return rc;
             }
             if ((rc = load_bounds(nv)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, eids, nullptr, rdiv, 0, 0, nullptr};
+            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, eids, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
             sb.cv = ColView{CK_FIXED2, 1, nullptr, edges, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = nv;
             sb.nvar = E;
         } else if (A->kind == MWU_MAT_INCIDENCE_T) {
             if ((rc = load_bounds(E)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_FIXED2, 1, E, 2 * E, nullptr, edges, nullptr, rdiv, 0, 0, nullptr};
+            sb.rv = RowView{RK_FIXED2, 1, E, 2 * E, nullptr, edges, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
             sb.cv = ColView{CK_CSR, choose_G(avg, forced_G), vptr, eids, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = E;
             sb.nvar = nv;
         } else if (A->kind == MWU_MAT_PAIR) {
             if ((rc = load_bounds(nv)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, slots, nullptr, rdiv, 0, 0, nullptr};
+            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, slots, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
             sb.cv = ColView{CK_FIXED1, 1, nullptr, edges, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = nv;
             sb.nvar = 2 * E;
         } else {
             if ((rc = load_bounds(E)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_PAIRSUM, 1, E, 2 * E, nullptr, nullptr, nullptr, rdiv, 0, 0, nullptr};
+            sb.rv = RowView{RK_PAIRSUM, 1, E, 2 * E, nullptr, nullptr, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
             sb.cv = ColView{CK_HALF1, 1, nullptr, nullptr, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = E;
             sb.nvar = 2 * E;
@@ -246,6 +251,12 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
         TRY_CUDA(c, heavy_list(c->ar, sb.rv.ptr, sb.rv.rows, sb.rv.heavy_len, &list, &cnt, s));
         sb.rv.heavy = list;
         sb.rv.n_heavy = cnt;
+        TRY_CUDA(c, bin_list(c->ar, sb.rv.ptr, sb.rv.rows, -1, SHORT_LEN, &list, &cnt, s));
+        sb.rv.short_rows = list;
+        sb.rv.n_short = cnt;
+        TRY_CUDA(c, bin_list(c->ar, sb.rv.ptr, sb.rv.rows, SHORT_LEN, sb.rv.heavy_len, &list, &cnt, s));
+        sb.rv.med_rows = list;
+        sb.rv.n_med = cnt;
     }
     if (sb.cv.kind == CK_CSR) sb.cv.heavy_len = heavy_len_for(sb.cv.G);
     return MWU_OK;
@@ -254,7 +265,7 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
 static void dense_side(SideBuild &sb, const float *c, int32_t sign) {
     sb.sign = sign;
     sb.dense = true;
-    sb.rv = RowView{RK_DENSE1, 1, 1, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr};
+    sb.rv = RowView{RK_DENSE1, 1, 1, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, 0, 0, nullptr, nullptr};
     sb.cv = ColView{CK_DENSE1, 1, nullptr, nullptr, nullptr, nullptr, c, 0, 0, nullptr};
     sb.m = 1;
     sb.nvar = -1;
@@ -262,7 +273,7 @@ static void dense_side(SideBuild &sb, const float *c, int32_t sign) {
 
 template <class T>
 static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32_t *heavy_var, int32_t n_heavy_var,
-                         int G_var, int var_bps, int row_bps) {
+                         int G_var, int var_bps, int row_bps, int upd_bps) {
     p.n = c->n;
     p.x = c->ar.alloc<T>(c->n);
     p.d = c->ar.alloc<T>(c->n);
@@ -286,10 +297,13 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.st = c->st_dev;
     p.grid_var = std::max(1, c->n_sms * var_bps);
     p.grid_row = std::max(2, c->n_sms * row_bps);
-    size_t recs = (size_t)std::max(p.grid_var, p.grid_row) + 8;
+    p.grid_upd = std::max(2, c->n_sms * std::min(upd_bps, row_bps));
+    size_t recs = (size_t)std::max(p.grid_var, std::max(p.grid_row, p.grid_upd)) + 8;
     p.part_var = c->ar.alloc<double>((int64_t)(recs * REC));
     p.part_row = c->ar.alloc<double>((int64_t)(recs * REC));
-    if (!p.part_var || !p.part_row) return fail(c, MWU_ERR_OOM, "allocating partial buffers");
+    p.part_grp = c->ar.alloc<double>((int64_t)2 * GRP_MAX * REC);
+    if (!p.part_var || !p.part_row || !p.part_grp) return fail(c, MWU_ERR_OOM, "allocating partial buffers");
+    if (std::max(p.grid_row, p.grid_upd) > GRP * GRP_MAX) return fail(c, MWU_ERR_INVALID, "grid too large for the group tickets");
     p.G_var = G_var;
     p.heavy_var = heavy_var;
     p.n_heavy_var = n_heavy_var;
@@ -317,11 +331,15 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     mwu_ctx *c = new mwu_ctx();
     c->kind = kind;
     c->fp64 = o.precision == MWU_PREC_FP64;
+    if (const char *tr = std::getenv("MWU_TRACE")) c->trace = tr[0] == '1';
     if (c->fp64 || o.step == MWU_STEP_BINARY) o.K = 1;
     if (o.max_passes <= 0) o.max_passes = (c->fp64 || o.K == 1) ? 64 : 6;
     if (o.outer_tol <= 0.0) o.outer_tol = o.eps;
     if (o.max_probes <= 0) o.max_probes = 64;
     if (o.check_every <= 0) o.check_every = 8;
+    if (o.grad_tol < 0.0) o.grad_tol = c->fp64 ? 0.0 : std::ldexp(1.0, -16);
+    if (o.grad_tol >= 1.0) { c->err = "grad_tol must be < 1"; g_create_error = c->err; delete c; return MWU_ERR_INVALID; }
+    if (o.stop_rule != 0 && o.stop_rule != 1) { c->err = "stop_rule must be 0 or 1"; g_create_error = c->err; delete c; return MWU_ERR_INVALID; }
     c->opt = o;
     auto bail = [&](int rc) {
         g_create_error = c->err;
@@ -420,9 +438,9 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         c->err = "clearing state";
         return bail(MWU_ERR_CUDA);
     }
-    int vb = 1, rb = 1;
-    if (c->fp64) { sweep_blocks_per_sm<double>(&vb, &rb); rc = alloc_problem(c, c->pd, sb, hv, nhv, G_var, vb, rb); }
-    else { sweep_blocks_per_sm<float>(&vb, &rb); rc = alloc_problem(c, c->pf, sb, hv, nhv, G_var, vb, rb); }
+    int vb = 1, rb = 1, ub = 1;
+    if (c->fp64) { sweep_blocks_per_sm<double>(&vb, &rb, &ub); rc = alloc_problem(c, c->pd, sb, hv, nhv, G_var, vb, rb, ub); }
+    else { sweep_blocks_per_sm<float>(&vb, &rb, &ub); rc = alloc_problem(c, c->pf, sb, hv, nhv, G_var, vb, rb, ub); }
     if (rc != MWU_OK) return bail(rc);
     c->x_best = c->ar.raw((size_t)c->n * (c->fp64 ? sizeof(double) : sizeof(float)));
     if (!c->x_best) { c->err = "allocating best x"; return bail(MWU_ERR_OOM); }
@@ -478,6 +496,8 @@ static void reset_probe_fields(DevState &h) {
     h.total_passes = 0;
     h.n_pos = 0;
     for (int k = 0; k < 8; ++k) h.counter[k] = 0;
+    for (int r = 0; r < 2; ++r)
+        for (int g = 0; g < GRP_MAX; ++g) h.grp_counter[r][g] = 0;
 }
 
 static int probe_status(const DevState &h) {
@@ -510,6 +530,9 @@ int mwu_set_target(mwu_ctx *c, double target) {
     h.max_passes = o.max_passes;
     h.warm_start = o.warm_start;
     h.step_mode = o.step == MWU_STEP_STANDARD ? 2 : (o.step == MWU_STEP_BINARY ? 1 : 0);
+    h.stop_rule = o.stop_rule;
+    h.grad_tol = o.grad_tol;
+    h.ratio_stop = o.stop_rule == 1 ? 1.0 + o.eps : 0.0;
     reset_probe_fields(h);
     if ((rc = push_state(c)) != MWU_OK) return rc;
     c->have_direction = false;
@@ -942,6 +965,16 @@ int mwu_solve(mwu_ctx *c, double lo, double hi, mwu_result *res) {
         while (hi > (1.0 + c->opt.outer_tol) * lo && probes < c->opt.max_probes) {
             double M = std::sqrt(lo * hi);
             if ((rc = mwu_set_target(c, M)) != MWU_OK) return rc;
+            // The probe may also stop as soon as its certificate closes the search:
+            // cert = M zmin/ymax >= hi/(1+tol) (max) or M ymax/zmin <= (1+tol) lo (min).
+            {
+                const double tol1 = 1.0 + c->opt.outer_tol;
+                double rho = maximize ? tol1 * M / hi : tol1 * lo / M;
+                DevState &h = *c->st_host;
+                h.ratio_stop = std::max(h.ratio_stop, rho);
+                TRY_CUDA(c, cudaMemcpyAsync(&c->st_dev->ratio_stop, &h.ratio_stop, sizeof(double),
+                                            cudaMemcpyHostToDevice, c->stream));
+            }
             mwu_iter_stats s{};
             rc = mwu_iterate(c, c->opt.max_iter, &s);
             if (rc < 0) return rc;
@@ -951,6 +984,10 @@ int mwu_solve(mwu_ctx *c, double lo, double hi, mwu_result *res) {
             iters += s.iters;
             evals += s.evals;
             passes += s.passes;
+            if (c->trace)
+                std::fprintf(stderr, "[mwu] probe %d target=%.9g status=%d reason=%d iters=%d passes=%lld cert=%.9g "
+                             "lo=%.9g hi=%.9g\n", probes, M, s.status, s.reason, s.iters, (long long)s.passes, cert,
+                             lo, hi);
             bool better = maximize ? cert > best : cert < best;
             if (better || !have_best) {
                 if (better) best = cert;

@@ -20,6 +20,8 @@ namespace mwu {
 constexpr int KMAX = 8;           // candidates per pass (compile-time bound)
 constexpr int BLOCK = 256;        // threads per block of the sweep kernels
 constexpr int REC = 64;           // doubles per per-block partial record
+constexpr int GRP = 16;           // blocks per group of the two-level completion
+constexpr int GRP_MAX = 128;      // groups (grids up to 2048 blocks)
 
 // Row views (constraint rows of one side, for y = A x).
 enum RowKind : int32_t {
@@ -52,7 +54,14 @@ struct RowView {
     int32_t n_heavy;      // rows longer than heavy_len, processed one block each
     int32_t heavy_len;
     const int32_t *heavy;
+    // length bins of the light rows for the forward SpMV pass (CSR only):
+    // short rows (<= SHORT_LEN) one thread each, medium rows MED_LANES lanes each
+    int32_t n_short, n_med;
+    const int32_t *short_rows, *med_rows;
 };
+
+constexpr int SHORT_LEN = 16;
+constexpr int MED_LANES = 16;
 
 struct ColView {
     int32_t kind;
@@ -79,7 +88,8 @@ struct Side {
 
 // Probe status values stored on the device.
 enum : int32_t { ST_FEASIBLE = 0, ST_INFEASIBLE = 1, ST_MAX_ITER = 2, ST_RUNNING = 3, ST_NUMERIC = -4 };
-enum : int32_t { RS_NONE = 0, RS_COVERED = 1, RS_PACKING = 2, RS_DZERO = 3, RS_ALPHA = 4, RS_MAXITER = 5 };
+enum : int32_t { RS_NONE = 0, RS_COVERED = 1, RS_PACKING = 2, RS_DZERO = 3, RS_ALPHA = 4, RS_MAXITER = 5,
+                 RS_RATIO = 6 };
 
 // Search phases.
 enum : int32_t { PH_EXP = 0, PH_REFINE = 1, PH_DONE = 2 };
@@ -90,7 +100,9 @@ struct DevState {
     double scale[2];            // side factors: 1/M (objective row), 1/D (O), else 1
     int32_t max_iter, K, max_passes, warm_start;
     int32_t step_mode;          // 0 kary, 1 binary (K=1 semantics), 2 standard
-    int32_t pad0;
+    int32_t stop_rule;          // 1: stop FEASIBLE once ymax <= (1+eps) zmin
+    double grad_tol;            // gradient test: d_i > 0 iff g_i < (1 - grad_tol) h_i
+    double ratio_stop;          // > 0: stop FEASIBLE once ymax <= ratio_stop * zmin
     // reductions of the current y, z (side 0 = P, side 1 = C)
     double s[2], S[2];
     double dense_v[2], dense_dv[2];   // single objective row value and direction
@@ -112,6 +124,8 @@ struct DevState {
     long long evals, total_passes;
     // last-block-done counters
     unsigned int counter[8];
+    // per-group tickets of the two-level completion (row 0: candidate passes, row 1: update)
+    unsigned int grp_counter[2][GRP_MAX];
 };
 
 template <class T>
@@ -122,7 +136,9 @@ struct Problem {
     DevState *st;
     double *part_var;   // per-block records of variable-side kernels
     double *part_row;   // per-block records of row-side kernels
-    int32_t grid_var, grid_row;   // grid sizes (blocks)
+    double *part_grp;   // per-group records (2 x GRP_MAX x REC): candidate passes, update
+    int32_t grid_var, grid_row;   // grid sizes (blocks): variable kernels, candidate passes
+    int32_t grid_upd;             // grid of the update kernel (higher occupancy)
     int32_t G_var;      // lanes per variable for CSR column views
     int32_t heavy_var_len;
     int32_t n_heavy_var;
@@ -144,6 +160,6 @@ template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const
 template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t n, int fp64, cudaStream_t s);
 
 // Kernel occupancy helper (blocks per SM of the heaviest sweep kernel).
-template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps);
+template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_bps);
 
 }  // namespace mwu

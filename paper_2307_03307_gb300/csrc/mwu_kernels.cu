@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(BLOCK) k_x_prep(Problem<T> p, const void *xin,
 // Merge per-block LSE records of the row kernels plus dense-row values and set
 // s, S, ymax, zmin and the stop status (Alg. 2 loop test, see the oracle).
 template <class T>
-__device__ void finalize_reductions(Problem<T> &p, int nb_row, int nb_var, bool dense_from_var, double alpha) {
+__device__ void finalize_reductions(Problem<T> &p, const double *recs, int nb_row, int nb_var, bool dense_from_var,
+                                    double alpha) {
     static_assert(BLOCK == 256, "merge layout assumes 256 threads");
     DevState *st = p.st;
     __shared__ double sh_s[2][BLOCK], sh_S[2][BLOCK];
@@ -289,7 +290,7 @@ __device__ void finalize_reductions(Problem<T> &p, int nb_row, int nb_var, bool 
         Lse<double> a{0.0, 0.0};
         double eta_sgn = st->eta * (double)p.side[s].sign;
         for (int b = threadIdx.x; b < nb_row; b += blockDim.x) {
-            const double *r = p.part_row + (size_t)b * REC;
+            const double *r = recs + (size_t)b * REC;
             lse_merge<T, double>(a, r[2 * s], r[2 * s + 1], eta_sgn, p.side[s].sign);
         }
         sh_s[s][threadIdx.x] = a.s;
@@ -341,7 +342,10 @@ __device__ void finalize_reductions(Problem<T> &p, int nb_row, int nb_var, bool 
             st->numeric_bad = 1;
         } else if (st->status == ST_RUNNING) {
             double eps = st->eps;
-            if (st->zmin >= 1.0 || st->ymax > 1.0 + eps) {
+            if (st->ratio_stop > 0.0 && st->zmin > 0.0 && st->ymax <= st->ratio_stop * st->zmin) {
+                st->status = ST_FEASIBLE;   // x / zmin is a (ratio_stop)-relative solution
+                st->reason = RS_RATIO;
+            } else if (st->zmin >= 1.0 || st->ymax > 1.0 + eps) {
                 if (st->ymax <= (1.0 + eps) * st->zmin) { st->status = ST_FEASIBLE; st->reason = RS_COVERED; }
                 else { st->status = ST_INFEASIBLE; st->reason = RS_PACKING; }
             } else if (st->iter >= st->max_iter) {
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(BLOCK) k_rows_eval(Problem<T> p, int gP, int n
         rec[2 * (1 - s) + 1] = 0.0;
     }
     if (last_block_done(&st->counter[0])) {
-        finalize_reductions(p, gridDim.x, nb_var, true, 0.0);
+        finalize_reductions(p, p.part_row, gridDim.x, nb_var, true, 0.0);
         if (threadIdx.x == 0) st->counter[0] = 0;
     }
 }
@@ -436,6 +440,7 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
     const T fp = (T)(st->scale[0] / st->S[0]);
     const T fc = (T)(st->scale[1] / st->S[1]);
     const T cd = (T)st->c_d;
+    const T thr = (T)(1.0 - st->grad_tol);   // gradient test threshold on g/h
     long long npos = 0;
     double dense_dot[2] = {0.0, 0.0};
 
@@ -453,7 +458,7 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
             }
             return;
         }
-        T di = (g < h) ? cd * (T(1) - g / h) * xi : T(0);
+        T di = (g < thr * h) ? cd * (T(1) - g / h) * xi : T(0);
         p.d[i] = di;
         if (keep_gh) { p.g[i] = g; p.h[i] = h; }
         npos += (di > T(0));
@@ -548,6 +553,7 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
 // Per-thread accumulators of K candidates for one side.
 template <class T> struct CandAcc {
     T mx[KMAX], R[KMAX], Tt[KMAX], zm[KMAX];
+    T mxmin;   // min_k mx[k] (covering side), maintained on rescale
 };
 
 template <class T>
@@ -557,6 +563,7 @@ __device__ __forceinline__ void cand_init(CandAcc<T> &c, int sgn) {
         c.mx[k] = sgn > 0 ? T(0) : -t_inf<T>();
         c.R[k] = T(0); c.Tt[k] = T(0); c.zm[k] = t_inf<T>();
     }
+    c.mxmin = sgn > 0 ? T(0) : -t_inf<T>();
 }
 
 // Candidate schedule of one pass (identical for every row).
@@ -586,50 +593,87 @@ __device__ __forceinline__ double fast_exp(double x) { return exp(x); }
 // mx_k is a running max per thread (rescale on a new max); exp of arguments
 // <= 0 uses the __expf intrinsic in FP32 (error 2 + 1.2|x| ulp, and terms with
 // large |x| are negligible in the sums).
-template <class T>
-__device__ __forceinline__ void cand_push(CandAcc<T> &c, const CandSched<T> &sc, int sgn, T v, T dv, T eta, T s) {
-    const int K = sc.K;
-    T b = sc.ca[0] * dv;
+// Exponent margin below which a term is dropped: exp(-NEGL) ~ 1.8e-35 relative
+// to the running shift, beyond FP32 resolution (and FP64 never drops: NEGL_D).
+template <class T> __device__ __forceinline__ T negl_margin();
+template <> __device__ __forceinline__ float negl_margin<float>() { return 80.0f; }
+template <> __device__ __forceinline__ double negl_margin<double>() { return 1.0e300; }
+
+template <class T, int MODE, int SGN, int KC>
+__device__ __forceinline__ void cand_push_m(CandAcc<T> &c, const T *ca, const T *al, T cd, int Kr, T v, T dv, T eta,
+                                            T s) {
+    const int K = KC > 0 ? KC : Kr;
+    const T a = (SGN > 0 ? eta : -eta) * (v - s);
+    // A row whose exponents lie more than NEGL below every shift adds nothing
+    // representable to R_k and T_k.  Packing: x_k = a + b_k <= a + b_{K-1} and
+    // mx_k >= 0.  Covering: x_k <= a <= 0 and exp(a) is the T weight (S_c >= 1).
+    if (SGN > 0) {
+        if (a + ca[K - 1] * dv < -negl_margin<T>()) return;
+    } else {
+        if (a < -negl_margin<T>() && a < c.mxmin - negl_margin<T>()) {
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) c.zm[k] = fmin(c.zm[k], v + al[k] * dv);
+            return;
+        }
+    }
+    T b = ca[0] * dv;
     T u = -t_expm1(-b);
     T ud = T(0);
-    if (sc.mode == 1) ud = -t_expm1(-sc.cd * dv);
-    if (sgn > 0) {
-        const T a = eta * (v - s);
+    if (MODE == 1) ud = -t_expm1(-cd * dv);
+    T A = T(0);
+    if (SGN < 0) A = fast_exp(a);
+    // rescale only when some lane of the warp meets a new maximum
+    const unsigned act = __activemask();
+    bool moved = false;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            if (k < K) {
-                if (k > 0) {
-                    b = sc.ca[k] * dv;
-                    if (sc.mode == 0) u = u * (T(2) - u);
-                    else if (sc.mode == 1) u = u + ud * (T(1) - u);
-                    else u = -t_expm1(-b);
-                }
-                const T x = a + b;
-                if (x > c.mx[k]) { T f = fast_exp(c.mx[k] - x); c.R[k] *= f; c.Tt[k] *= f; c.mx[k] = x; }
-                const T t = fast_exp(x - c.mx[k]);
-                c.R[k] += t;
-                c.Tt[k] += t * u;
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < K) {
+            if (k > 0) {
+                b = ca[k] * dv;
+                if (MODE == 0) u = u * (T(2) - u);
+                else if (MODE == 1) u = u + ud * (T(1) - u);
+                else u = -t_expm1(-b);
             }
-        }
-    } else {
-        const T a = -eta * (v - s);
-        const T A = fast_exp(a);
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            if (k < K) {
-                if (k > 0) {
-                    b = sc.ca[k] * dv;
-                    if (sc.mode == 0) u = u * (T(2) - u);
-                    else if (sc.mode == 1) u = u + ud * (T(1) - u);
-                    else u = -t_expm1(-b);
+            const T x = SGN > 0 ? a + b : a - b;
+            const bool up = x > c.mx[k];
+            if (__any_sync(act, up)) {
+                if (up) {
+                    T f = fast_exp(c.mx[k] - x);
+                    c.R[k] *= f;
+                    if (SGN > 0) c.Tt[k] *= f;
+                    c.mx[k] = x;
+                    moved = true;
                 }
-                const T x = a - b;
-                if (x > c.mx[k]) { T f = fast_exp(c.mx[k] - x); c.R[k] *= f; c.mx[k] = x; }
-                c.R[k] += fast_exp(x - c.mx[k]);
+            }
+            const T t = fast_exp(x - c.mx[k]);
+            c.R[k] += t;
+            if (SGN > 0) c.Tt[k] += t * u;
+            else {
                 c.Tt[k] += A * u;
-                c.zm[k] = fmin(c.zm[k], v + sc.al[k] * dv);
+                c.zm[k] = fmin(c.zm[k], v + al[k] * dv);
             }
         }
+    }
+    if (SGN < 0 && moved) {
+        T mn = c.mx[0];
+#pragma unroll
+        for (int k = 1; k < KMAX; ++k)
+            if (k < K) mn = fmin(mn, c.mx[k]);
+        c.mxmin = mn;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void cand_push(CandAcc<T> &c, const CandSched<T> &sc, int sgn, T v, T dv, T eta, T s) {
+    if (sgn > 0) {
+        if (sc.mode == 0) cand_push_m<T, 0, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
+        else if (sc.mode == 1) cand_push_m<T, 1, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
+        else cand_push_m<T, 2, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
+    } else {
+        if (sc.mode == 0) cand_push_m<T, 0, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
+        else if (sc.mode == 1) cand_push_m<T, 1, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
+        else cand_push_m<T, 2, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
     }
 }
 
@@ -706,10 +750,40 @@ __device__ void search_decide(DevState *st, const int *ok, const double *zmin_k)
     }
 }
 
+// Later candidate passes: stream the stored (v, dv) of one side.
+template <class T, int MODE, int SGN, int KC>
+__device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> &sc, const Side<T> &sd, int64_t m,
+                                            int64_t tid, int64_t nthr, T eta, T sh) {
+    T ca[KMAX], al[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) { ca[k] = sc.ca[k]; al[k] = sc.al[k]; }
+    const T cd = sc.cd;
+    const int K = sc.K;
+    for (int64_t j0 = 4 * tid; j0 < m; j0 += 4 * nthr) {
+        const int nr = (int)min((int64_t)4, m - j0);
+        T vv[4], dd[4];
+        if (nr == 4 && sizeof(T) == 4) {
+            float4 a4 = *reinterpret_cast<const float4 *>(sd.v + j0);
+            float4 b4 = *reinterpret_cast<const float4 *>(sd.dv + j0);
+            vv[0] = a4.x; vv[1] = a4.y; vv[2] = a4.z; vv[3] = a4.w;
+            dd[0] = b4.x; dd[1] = b4.y; dd[2] = b4.z; dd[3] = b4.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                vv[r] = r < nr ? sd.v[j0 + r] : T(0);
+                dd[r] = r < nr ? sd.dv[j0 + r] : T(0);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (r < nr) cand_push_m<T, MODE, SGN, KC>(acc, ca, al, cd, K, vv[r], dd[r], eta, sh);
+    }
+}
+
 // a6 + a7: dv = A d on the first pass, then K candidates per row.
 // external = 1: evaluate st->alpha[0..K) and store psi/phi/zmin, no decision.
 template <class T>
-__global__ void __launch_bounds__(BLOCK, 3) k_cand(Problem<T> p, int gP, int first, int external) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int first, int external) {
     __shared__ T sm[32];
     __shared__ CandSched<T> s_sc;
     DevState *st = p.st;
@@ -743,11 +817,29 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cand(Problem<T> p, int gP, int fir
     const bool csr_first = first && sd.rv.kind == RK_CSR;
     if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) {
         // single objective row: handled exactly by the decision step
+    } else if (!first && searching) {
+        // later passes: a pure stream over the stored (v, dv), four rows per thread,
+        // with the schedule in registers and the loop specialised per (mode, side)
+        const int md = sc.mode;
+        if (sc.K == KMAX) {
+            if (sd.sign > 0) {
+                if (md == 0) cand_stream<T, 0, 1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
+                else if (md == 1) cand_stream<T, 1, 1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
+                else cand_stream<T, 2, 1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
+            } else {
+                if (md == 0) cand_stream<T, 0, -1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
+                else if (md == 1) cand_stream<T, 1, -1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
+                else cand_stream<T, 2, -1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
+            }
+        } else {
+            if (sd.sign > 0) cand_stream<T, 2, 1, 0>(acc, sc, sd, m, tid, nthr, eta, sh);
+            else cand_stream<T, 2, -1, 0>(acc, sc, sd, m, tid, nthr, eta, sh);
+        }
     } else if (!csr_first) {
-        // stream: four consecutive rows per thread; dv from the stored vector or,
-        // on the first pass, from the implicit row kinds (pairs / edges)
+        // first pass over implicit row kinds (pairs / edges): dv formed, stored and used
         const RowView &rv = sd.rv;
         const double scale = st->scale[s];
+        {
         for (int64_t j0 = 4 * tid; j0 < m; j0 += 4 * nthr) {
             T vv[4], dd[4];
             const int nr = (int)min((int64_t)4, m - j0);
@@ -790,10 +882,11 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cand(Problem<T> p, int gP, int fir
                     if (r < nr) cand_push(acc, sc, sd.sign, vv[r], dd[r], eta, sh);
             }
         }
+        }
     } else {
-        // first pass over explicit CSR rows: heavy rows one block each, light rows by
-        // groups of G lanes; a group forms G row sums in turn and lane r keeps row r,
-        // so the candidate work is spread over all lanes
+        // first pass over CSR rows, binned by length at setup: heavy rows one block
+        // each, medium rows MED_LANES lanes each (lane 0 evaluates the candidates),
+        // short rows one thread each (every lane evaluates its own row)
         const RowView &rv = sd.rv;
         const double scale = st->scale[s];
         for (int h = bid; h < rv.n_heavy; h += nbs) {
@@ -804,23 +897,50 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cand(Problem<T> p, int gP, int fir
                 if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
             }
         }
-        const int G = rv.G, lane = threadIdx.x & (G - 1), grp = (threadIdx.x & 31) / G;
-        const int64_t wid = (int64_t)bid * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        const int64_t nw = (int64_t)nbs * (blockDim.x >> 5);
-        for (int64_t base = wid * 32; base < m; base += nw * 32) {
-            T mine = T(0);
-            for (int r = 0; r < G; ++r) {
-                int64_t j = base + grp * G + r;
-                T sum = j < m ? row_gather(rv, j, lane, G, p.d) : T(0);
-                sum = group_sum(sum, G);
-                if (lane == r) mine = sum;
+        {
+            const int lane = threadIdx.x & (MED_LANES - 1);
+            const int64_t gid = tid / MED_LANES, ngroups = nthr / MED_LANES;
+            const int64_t wbase = gid - (threadIdx.x & 31) / MED_LANES;   // first group of this warp
+            for (int64_t b0 = wbase; b0 < rv.n_med; b0 += ngroups) {
+                int64_t i = b0 + (threadIdx.x & 31) / MED_LANES;
+                T sum = T(0);
+                int64_t j = -1;
+                if (i < rv.n_med) {
+                    j = rv.med_rows[i];
+                    int beg = rv.ptr[j], end = rv.ptr[j + 1];
+                    for (int k = beg + lane; k < end; k += MED_LANES) {
+                        T t = p.d[rv.idx[k]];
+                        if (rv.val) t *= (T)rv.val[k];
+                        sum += t;
+                    }
+                }
+                sum = group_sum(sum, MED_LANES);
+                if (j >= 0 && lane == 0) {
+                    T dvj = sum * row_coef(sd, j, scale);
+                    sd.dv[j] = dvj;
+                    if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
+                }
             }
-            int64_t j = base + grp * G + lane;
-            if (j < m && !row_is_heavy<T>(rv, j)) {
-                T dvj = mine * row_coef(sd, j, scale);
-                sd.dv[j] = dvj;
-                if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
+        }
+        for (int64_t i = tid; i < rv.n_short; i += nthr) {
+            const int64_t j = rv.short_rows[i];
+            const int beg = rv.ptr[j], end = rv.ptr[j + 1];
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            int k = beg;
+            for (; k + 4 <= end; k += 4) {
+                int i0 = rv.idx[k], i1 = rv.idx[k + 1], i2 = rv.idx[k + 2], i3 = rv.idx[k + 3];
+                T t0 = p.d[i0], t1 = p.d[i1], t2 = p.d[i2], t3 = p.d[i3];
+                if (rv.val) { t0 *= (T)rv.val[k]; t1 *= (T)rv.val[k + 1]; t2 *= (T)rv.val[k + 2]; t3 *= (T)rv.val[k + 3]; }
+                s0 += t0; s1 += t1; s2 += t2; s3 += t3;
             }
+            for (; k < end; ++k) {
+                T t = p.d[rv.idx[k]];
+                if (rv.val) t *= (T)rv.val[k];
+                s0 += t;
+            }
+            T dvj = ((s0 + s1) + (s2 + s3)) * row_coef(sd, j, scale);
+            sd.dv[j] = dvj;
+            if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
         }
     }
     if (!searching) return;   // standard step: dv written, nothing to evaluate
@@ -848,20 +968,57 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cand(Problem<T> p, int gP, int fir
         rec[k * 4 + 0] = mx; rec[k * 4 + 1] = R; rec[k * 4 + 2] = Tt; rec[k * 4 + 3] = zm;
         rec[32] = s;
     }
-    if (last_block_done(&st->counter[2])) {
+    // two-level completion: the last block of each group of GRP blocks merges the
+    // group's records (one per lane), the last group merges the group records, so
+    // the FP64 merge work is spread over the SMs instead of one block
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    const int grp = blockIdx.x / GRP, ngrp = (gridDim.x + GRP - 1) / GRP;
+    const int gsz = min(GRP, (int)gridDim.x - grp * GRP);
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->grp_counter[0][grp], 1u) == (unsigned)(gsz - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    static_assert(BLOCK == 16 * 2 * KMAX, "merge layout assumes 256 threads and KMAX = 8");
+    static_assert(GRP == 16, "one record per lane of a 16-lane group");
+    double *grec = p.part_grp;   // row 0 of the group records
+    {
+        const int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
+        const int ss = q / KMAX, k = q % KMAX;
+        const int sg = p.side[ss].sign;
+        double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
+        const int b = grp * GRP + ln;
+        if (ln < gsz && (b < gP ? 0 : 1) == ss) {
+            const double *rec = p.part_row + (size_t)b * REC + k * 4;
+            cand_merge1<T, double>(mx, R, Tt, zm, rec[0], rec[1], rec[2], rec[3], sg);
+        }
+        for (int off = 8; off > 0; off >>= 1) {
+            double omx = __shfl_xor_sync(0xffffffffu, mx, off), oR = __shfl_xor_sync(0xffffffffu, R, off);
+            double oT = __shfl_xor_sync(0xffffffffu, Tt, off), oz = __shfl_xor_sync(0xffffffffu, zm, off);
+            cand_merge1<T, double>(mx, R, Tt, zm, omx, oR, oT, oz, sg);
+        }
+        if (ln == 0) {
+            double *g = grec + (size_t)grp * REC + ss * 32 + k * 4;
+            g[0] = mx; g[1] = R; g[2] = Tt; g[3] = zm;
+        }
+    }
+    if (threadIdx.x == 0) st->grp_counter[0][grp] = 0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->counter[2], 1u) == (unsigned)(ngrp - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    {
         __shared__ double fin[2][KMAX][4];
-        // 16 lanes per (side, k) pair, strided over the block records, then a
-        // shuffle tree inside each half warp
         {
-            static_assert(BLOCK == 16 * 2 * KMAX, "merge layout assumes 256 threads and KMAX = 8");
-            int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
-            int ss = q / KMAX, k = q % KMAX;
-            int sg = p.side[ss].sign;
+            const int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
+            const int ss = q / KMAX, k = q % KMAX;
+            const int sg = p.side[ss].sign;
             double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
-            int b0 = ss == 0 ? 0 : gP, b1 = ss == 0 ? gP : gridDim.x;
-#pragma unroll 4
-            for (int b = b0 + ln; b < b1; b += 16) {
-                const double *rec = p.part_row + (size_t)b * REC + k * 4;
+            for (int gg = ln; gg < ngrp; gg += 16) {
+                const double *rec = grec + (size_t)gg * REC + ss * 32 + k * 4;
                 cand_merge1<T, double>(mx, R, Tt, zm, rec[0], rec[1], rec[2], rec[3], sg);
             }
             for (int off = 8; off > 0; off >>= 1) {
@@ -960,15 +1117,14 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
             }
         }
     }
+    // warp merge in T (FP32 for the fast form), warps and blocks in FP64
     __shared__ double bs[BLOCK / 32], bS[BLOCK / 32];
-    Lse<double> r{(double)acc.s, (double)acc.S};
-    double eds = st->eta * sd.sign;
+    const double eds = st->eta * sd.sign;
     for (int off = 16; off > 0; off >>= 1) {
-        double os = __shfl_xor_sync(0xffffffffu, r.s, off);
-        double oS = __shfl_xor_sync(0xffffffffu, r.S, off);
-        lse_merge<T, double>(r, os, oS, eds, sd.sign);
+        T os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
+        lse_merge<T, T>(acc, os, oS, eta_sgn, sd.sign);
     }
-    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = r.s; bS[threadIdx.x >> 5] = r.S; }
+    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = (double)acc.s; bS[threadIdx.x >> 5] = (double)acc.S; }
     __syncthreads();
     if (threadIdx.x == 0) {
         Lse<double> q{0.0, 0.0};
@@ -977,16 +1133,51 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
         rec[2 * s] = q.s; rec[2 * s + 1] = q.S;
         rec[2 * (1 - s)] = 0.0; rec[2 * (1 - s) + 1] = 0.0;
     }
-    if (last_block_done(&st->counter[3])) {
-        if (threadIdx.x == 0) {
-            st->iter += 1;
-            st->pending = 1;
-            st->alpha_prev = alpha;
+    // two-level completion (see k_cand): group merge, then the last group finalises
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    const int grp = blockIdx.x / GRP, ngrp = (gridDim.x + GRP - 1) / GRP;
+    const int gsz = min(GRP, (int)gridDim.x - grp * GRP);
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->grp_counter[1][grp], 1u) == (unsigned)(gsz - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double *grec = p.part_grp + (size_t)GRP_MAX * REC;   // row 1 of the group records
+    if (threadIdx.x < 32) {
+        const int ss = threadIdx.x >> 4, ln = threadIdx.x & 15;
+        const int sg = p.side[ss].sign;
+        Lse<double> q{0.0, 0.0};
+        if (ln < gsz) {
+            const double *rec = p.part_row + (size_t)(grp * GRP + ln) * REC;
+            q.s = rec[2 * ss];
+            q.S = rec[2 * ss + 1];
         }
-        __syncthreads();
-        finalize_reductions(p, gridDim.x, 0, false, alpha);
-        if (threadIdx.x == 0) st->counter[3] = 0;
+        const double e2 = st->eta * sg;
+        for (int off = 8; off > 0; off >>= 1) {
+            double os = __shfl_xor_sync(0xffffffffu, q.s, off), oS = __shfl_xor_sync(0xffffffffu, q.S, off);
+            lse_merge<T, double>(q, os, oS, e2, sg);
+        }
+        if (ln == 0) {
+            grec[(size_t)grp * REC + 2 * ss] = q.s;
+            grec[(size_t)grp * REC + 2 * ss + 1] = q.S;
+        }
     }
+    if (threadIdx.x == 0) st->grp_counter[1][grp] = 0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->counter[3], 1u) == (unsigned)(ngrp - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        st->iter += 1;
+        st->pending = 1;
+        st->alpha_prev = alpha;
+    }
+    __syncthreads();
+    finalize_reductions(p, grec, ngrp, 0, false, alpha);
+    if (threadIdx.x == 0) st->counter[3] = 0;
 }
 
 // apply a pending x += alpha d
@@ -1104,16 +1295,21 @@ template <class T> cudaError_t launch_cand(const Problem<T> &p, int first, int e
 }
 
 template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s) {
-    int gP, gC;
-    split_rows(p, &gP, &gC);
-    // the update is a plain stream over the rows: size by rows, not groups
-    auto need = [&](const Side<T> &sd) -> int {
-        if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) return 0;
-        return grid_for(sd.m, p.grid_row);
+    // the update is a plain stream over the rows (four per thread): split the
+    // update grid by rows
+    auto rows = [&](const Side<T> &sd) -> int64_t {
+        return (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) ? 0 : sd.m;
     };
-    int nP = need(p.side[0]), nC = need(p.side[1]);
-    gP = std::min(std::max(gP, nP > 0 ? 1 : 0), nP);
-    gC = std::min(std::max(gC, nC > 0 ? 1 : 0), nC);
+    const int64_t mP = rows(p.side[0]), mC = rows(p.side[1]);
+    auto need = [&](int64_t m) -> int { return m > 0 ? grid_for((m + 3) / 4, p.grid_upd) : 0; };
+    int gP = 0, gC = 0;
+    if (mP + mC > 0) {
+        int total = p.grid_upd;
+        gP = mP > 0 ? std::max(1, (int)((double)total * (double)mP / (double)(mP + mC))) : 0;
+        gC = mC > 0 ? std::max(1, total - gP) : 0;
+        gP = std::min(gP, need(mP));
+        gC = std::min(gC, need(mC));
+    }
     if (gP + gC == 0) gP = 1;
     k_update<T><<<gP + gC, BLOCK, 0, s>>>(p, gP);
     return cudaGetLastError();
@@ -1157,14 +1353,14 @@ template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t 
     return cudaGetLastError();
 }
 
-template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps) {
+template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_bps) {
     int a = 0, b = 0, c = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dir<T>, BLOCK, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cand<T>, BLOCK, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_update<T>, BLOCK, 0);
     *var_bps = a > 0 ? a : 1;
-    int r = b < c ? b : c;
-    *row_bps = r > 0 ? r : 1;
+    *row_bps = b > 0 ? b : 1;
+    *upd_bps = c > 0 ? c : 1;
     return 0;
 }
 
@@ -1180,7 +1376,7 @@ template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps) {
     template cudaError_t launch_potential_grads<T>(const Problem<T> &, const float *, float *, float *,        \
                                                    float *, float *, cudaStream_t);                            \
     template cudaError_t launch_copy_vec<T>(const T *, void *, int64_t, int, cudaStream_t);                    \
-    template int sweep_blocks_per_sm<T>(int *, int *);
+    template int sweep_blocks_per_sm<T>(int *, int *, int *);
 
 MWU_INSTANTIATE(float)
 MWU_INSTANTIATE(double)

@@ -262,6 +262,21 @@ cudaError_t heavy_list(Arena &ar, const int32_t *ptr, int64_t rows, int thr, int
     return e;
 }
 
+__global__ void k_bin_flags(const int32_t *ptr, int64_t rows, int lo, int hi, char *flag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < rows; j += (int64_t)gridDim.x * blockDim.x) {
+        int len = ptr[j + 1] - ptr[j];
+        flag[j] = len > lo && len <= hi;
+    }
+}
+
+cudaError_t bin_list(Arena &ar, const int32_t *ptr, int64_t rows, int lo, int hi, int32_t **list, int32_t *count,
+                     cudaStream_t s) {
+    char *flag = ar.alloc_tmp<char>(rows > 0 ? rows : 1);
+    if (!flag) return cudaErrorMemoryAllocation;
+    k_bin_flags<<<g1d(rows), 256, 0, s>>>(ptr, rows, lo, hi, flag);
+    return select_flagged(ar, flag, rows, list, count, s);
+}
+
 cudaError_t heavy_list2(Arena &ar, const int32_t *p1, int thr1, const int32_t *p2, int thr2, int64_t rows,
                         int32_t **list, int32_t *count, cudaStream_t s) {
     char *flag = ar.alloc_tmp<char>(rows > 0 ? rows : 1);

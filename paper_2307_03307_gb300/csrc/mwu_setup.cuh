@@ -76,6 +76,9 @@ cudaError_t csr_transpose(Arena &ar, const int32_t *ptr, const int32_t *idx, con
                           int64_t cols, int64_t nnz, int32_t **tptr, int32_t **tidx, float **tval, cudaStream_t s);
 cudaError_t heavy_list(Arena &ar, const int32_t *ptr, int64_t rows, int thr, int32_t **list, int32_t *count,
                        cudaStream_t s);
+// rows j with lo < len(j) <= hi, in increasing order
+cudaError_t bin_list(Arena &ar, const int32_t *ptr, int64_t rows, int lo, int hi, int32_t **list, int32_t *count,
+                     cudaStream_t s);
 cudaError_t heavy_list2(Arena &ar, const int32_t *p1, int thr1, const int32_t *p2, int thr2, int64_t rows,
                         int32_t **list, int32_t *count, cudaStream_t s);
 cudaError_t bracket_stats(Arena &ar, const ColView &cv, int64_t n, const float *c, double *sum_inv_min,

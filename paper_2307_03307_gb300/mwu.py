@@ -25,7 +25,7 @@ MAT_CSR, MAT_INCIDENCE, MAT_INCIDENCE_T, MAT_PAIR, MAT_INTERWEAVE, MAT_NONE = 0,
 STEP_KARY, STEP_BINARY, STEP_STANDARD = 0, 1, 2
 PREC_F32_R64, PREC_FP64 = 0, 1
 VEC_X, VEC_Y, VEC_Z, VEC_D, VEC_DY, VEC_DZ, VEC_G, VEC_H = range(8)
-REASONS = {0: "none", 1: "covered", 2: "packing", 3: "d=0", 4: "alpha<1", 5: "max_iter"}
+REASONS = {0: "none", 1: "covered", 2: "packing", 3: "d=0", 4: "alpha<1", 5: "max_iter", 6: "ratio"}
 
 
 class mwu_matrix(C.Structure):
@@ -41,7 +41,7 @@ class mwu_options(C.Structure):
                 ("warm_start", C.c_int32), ("double_single", C.c_int32), ("precision", C.c_int32),
                 ("outer_tol", C.c_double), ("max_probes", C.c_int32), ("use_graph", C.c_int32),
                 ("check_every", C.c_int32), ("group", C.c_int32), ("timing", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p)]
 
 
 class mwu_iter_stats(C.Structure):
