@@ -264,6 +264,41 @@ int mwu_get_timing(mwu_ctx *ctx, mwu_timing *out, int32_t reset);
 int mwu_potential(mwu_ctx *ctx, const float *x, double *pot,
                   float *grad_x, float *grad_obj, float *grad_vals);
 
+/* ------------------------------------------- allocation-free evaluation */
+/* For callers that cannot allocate device memory -- code running where
+ * cudaMalloc is unavailable or forbidden (inside a graph-capture region, a
+ * custom allocator's own hooks, embedded runtimes with a fixed memory budget)
+ * -- this entry point evaluates step-size candidates of one constraint side
+ * without allocating anything and without a context.  The paper has no
+ * counterpart to it; it computes the same values as mwu_eval_candidates.
+ *
+ *   v, dv   : device float32 arrays of m rows (y and dy of a packing side,
+ *             sign = +1, or z and dz of a covering side, sign = -1)
+ *   shift, S: that side's log-sum-exp shift (max v for sign +1, min v for
+ *             sign -1) and shifted sum, as mwu_get_scalars reports them
+ *   eta     : the smoothing parameter
+ *   alphas  : host array of K (1..8) candidate step sizes
+ *   val     : host output, K doubles: Psi(alpha_k) = smax(v + a dv) - smax(v)
+ *             for sign +1, Phi(alpha_k) = smin(v + a dv) - smin(v) for -1
+ *   vmin    : host output or NULL, K doubles: min(v + alpha_k dv)
+ *   stream  : cudaStream_t or NULL (legacy default stream); the call waits
+ *             for its results
+ * Scratch lives in one static device array of MWU_STATIC_MAX_BLOCKS per-block
+ * records (256 KiB) that every GPU loading the library keeps until exit; m is
+ * limited to MWU_STATIC_MAX_ROWS (blocks x rows per block) and larger m returns
+ * MWU_ERR_INVALID.  The first call on each device looks the array up and
+ * clears its completion ticket (cudaGetSymbolAddress, cudaMemset); make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU (several streams or threads at once) race and must
+ * be serialised by the caller.  Errors: MWU_ERR_INVALID (bad argument, size
+ * beyond the maximum), MWU_ERR_CUDA; mwu_last_error(NULL) describes them. */
+#define MWU_STATIC_MAX_BLOCKS 1024
+#define MWU_STATIC_ROWS_PER_BLOCK 16384
+#define MWU_STATIC_MAX_ROWS ((int64_t)MWU_STATIC_MAX_BLOCKS * MWU_STATIC_ROWS_PER_BLOCK)
+int mwu_candidates_static(const float *v, const float *dv, int64_t m, int32_t sign, double eta,
+                          double shift, double S, const double *alphas, int32_t K,
+                          double *val, double *vmin, void *stream);
+
 /* ------------------------------------------------------------- batched */
 /* Many independent instances in one context (one launch per phase over all
  * instances, captured in a CUDA graph).  Supported: PACKING over INCIDENCE

@@ -115,6 +115,10 @@ int mwu_default_options(mwu_options *o) {
     return MWU_OK;
 }
 
+namespace mwu {
+void set_global_error(const char *msg) { g_create_error = msg ? msg : ""; }
+}  // namespace mwu
+
 const char *mwu_last_error(const mwu_ctx *ctx) {
     if (!ctx) return g_create_error.c_str();
     return ctx->err.c_str();

@@ -159,6 +159,9 @@ template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const
                                                       float *gvals_p, float *gvals_c, cudaStream_t s);
 template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t n, int fp64, cudaStream_t s);
 
+// Message for mwu_last_error(NULL) from entry points without a context.
+void set_global_error(const char *msg);
+
 // Kernel occupancy helper (blocks per SM of the heaviest sweep kernel).
 template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_bps);
 

@@ -17,10 +17,12 @@
 // write one FP64 record, and the last block to finish (threadfence + atomic
 // ticket) merges the records in a fixed order.
 #include "mwu_internal.cuh"
+#include "mwu.h"
 
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <string>
 
 namespace mwu {
 
@@ -1382,3 +1384,161 @@ MWU_INSTANTIATE(float)
 MWU_INSTANTIATE(double)
 
 }  // namespace mwu
+
+// ============================================================ allocation-free candidates
+// mwu_candidates_static (mwu.h): the candidate evaluation of one side with its
+// scratch in a static device array instead of context buffers.
+#include <mutex>
+
+namespace mwu {
+namespace stat {
+
+constexpr int MAXB = MWU_STATIC_MAX_BLOCKS;
+constexpr int RPB = MWU_STATIC_ROWS_PER_BLOCK;
+
+struct Scratch {
+    double rec[MAXB][KMAX][4];   // per-block (mx, R, T, min) of every candidate
+    double out[KMAX][2];         // value and min(v + alpha dv) per candidate
+    unsigned int ticket;         // completion count; the last block resets it to 0
+};
+
+__global__ void __launch_bounds__(BLOCK) k_cand_static(Scratch *scr, const float *v, const float *dv, int64_t m,
+                                                       int sign, double eta, double shift, double S,
+                                                       CandSched<float> sc) {
+    CandAcc<float> acc;
+    cand_init(acc, sign);
+    const float eta_f = (float)eta, sh = (float)shift;
+    const int64_t r0 = (int64_t)blockIdx.x * RPB, r1 = min(m, r0 + RPB);
+    for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+        if (sign > 0) cand_push_m<float, 2, 1, 0>(acc, sc.ca, sc.al, sc.cd, sc.K, v[j], dv[j], eta_f, sh);
+        else cand_push_m<float, 2, -1, 0>(acc, sc.ca, sc.al, sc.cd, sc.K, v[j], dv[j], eta_f, sh);
+    }
+    // block merge (as in k_cand), record to the static array
+    __shared__ double wm[BLOCK / 32][KMAX][4];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        float mx = acc.mx[k], R = acc.R[k], Tt = acc.Tt[k], zm = acc.zm[k];
+        for (int off = 16; off > 0; off >>= 1) {
+            float omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off);
+            cand_merge1<float, float>(mx, R, Tt, zm, omx, oR, oT, oz, sign);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            wm[threadIdx.x >> 5][k][0] = mx; wm[threadIdx.x >> 5][k][1] = R;
+            wm[threadIdx.x >> 5][k][2] = Tt; wm[threadIdx.x >> 5][k][3] = zm;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < KMAX) {
+        const int k = threadIdx.x;
+        double mx = sign > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            cand_merge1<float, double>(mx, R, Tt, zm, wm[w][k][0], wm[w][k][1], wm[w][k][2], wm[w][k][3], sign);
+        scr->rec[blockIdx.x][k][0] = mx; scr->rec[blockIdx.x][k][1] = R;
+        scr->rec[blockIdx.x][k][2] = Tt; scr->rec[blockIdx.x][k][3] = zm;
+    }
+    if (!last_block_done(&scr->ticket)) return;
+    if (threadIdx.x < KMAX) {
+        const int k = threadIdx.x;
+        double mx = sign > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
+        for (int b = 0; b < (int)gridDim.x; ++b)
+            cand_merge1<float, double>(mx, R, Tt, zm, scr->rec[b][k][0], scr->rec[b][k][1], scr->rec[b][k][2],
+                                       scr->rec[b][k][3], sign);
+        const double lS0 = (double)logf((float)S);
+        double val;
+        if (sign > 0) {
+            double lq = mx + (double)logf((float)Tt) - lS0;
+            val = (lq < 0.0) ? (double)log1pf(expf((float)lq)) / eta : (mx + (double)logf((float)R) - lS0) / eta;
+        } else {
+            double qv = Tt / S;
+            val = (qv <= 0.5) ? -(double)log1pf((float)(-qv)) / eta : -(mx + (double)logf((float)R) - lS0) / eta;
+        }
+        scr->out[k][0] = val;
+        scr->out[k][1] = zm;
+    }
+    if (threadIdx.x == 0) scr->ticket = 0;
+}
+
+// The scratch of every call: one copy per device that loads the library.
+static __device__ __align__(256) Scratch g_static_scratch;
+
+constexpr int MAXDEV = 64;
+static std::mutex g_mu;
+static Scratch *g_ptr[MAXDEV] = {nullptr};
+
+// Once per device, with that device current: the device address of the array
+// (its host-side name is only a stand-in) and a cleared completion ticket.
+static int device_scratch(Scratch **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) {
+        cudaGetLastError();
+        set_global_error("mwu_candidates_static: no usable CUDA device");
+        return MWU_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            set_global_error((std::string("mwu_candidates_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
+            return MWU_ERR_CUDA;
+        }
+        Scratch *sp = static_cast<Scratch *>(p);
+        e = cudaMemset(&sp->ticket, 0, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            set_global_error((std::string("mwu_candidates_static: clearing the ticket: ") + cudaGetErrorString(e)).c_str());
+            return MWU_ERR_CUDA;
+        }
+        g_ptr[dev] = sp;
+    }
+    *out = g_ptr[dev];
+    return MWU_OK;
+}
+
+}  // namespace stat
+}  // namespace mwu
+
+extern "C" int mwu_candidates_static(const float *v, const float *dv, int64_t m, int32_t sign, double eta,
+                                     double shift, double S, const double *alphas, int32_t K, double *val,
+                                     double *vmin, void *stream) {
+    using namespace mwu;
+    if (!v || !dv || !alphas || !val || m <= 0 || (sign != 1 && sign != -1) || K < 1 || K > KMAX ||
+        !(eta > 0.0) || !(S > 0.0) || !std::isfinite(shift)) {
+        set_global_error("mwu_candidates_static: bad argument (null pointer, m <= 0, sign not +-1, K not in 1..8, "
+                         "eta <= 0 or S <= 0)");
+        return MWU_ERR_INVALID;
+    }
+    if (m > MWU_STATIC_MAX_ROWS) {
+        set_global_error("mwu_candidates_static: m exceeds MWU_STATIC_MAX_ROWS (the static scratch holds "
+                         "MWU_STATIC_MAX_BLOCKS block records of MWU_STATIC_ROWS_PER_BLOCK rows)");
+        return MWU_ERR_INVALID;
+    }
+    stat::Scratch *scr = nullptr;
+    int rc = stat::device_scratch(&scr);
+    if (rc != MWU_OK) return rc;
+    CandSched<float> sc{};
+    sc.K = K;
+    sc.mode = 2;
+    sc.cd = 0.0f;
+    for (int k = 0; k < KMAX; ++k) {
+        double a = k < K ? alphas[k] : 0.0;
+        sc.ca[k] = (float)(a * eta);
+        sc.al[k] = (float)a;
+    }
+    const int grid = (int)((m + stat::RPB - 1) / stat::RPB);
+    cudaStream_t s = (cudaStream_t)stream;
+    stat::k_cand_static<<<grid, BLOCK, 0, s>>>(scr, v, dv, m, sign, eta, shift, S, sc);
+    cudaError_t e = cudaGetLastError();
+    double out[KMAX][2];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, scr->out, sizeof(out), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_global_error((std::string("mwu_candidates_static: ") + cudaGetErrorString(e)).c_str());
+        return MWU_ERR_CUDA;
+    }
+    for (int k = 0; k < K; ++k) {
+        val[k] = out[k][0];
+        if (vmin) vmin[k] = out[k][1];
+    }
+    return MWU_OK;
+}

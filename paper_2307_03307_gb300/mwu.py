@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         "mwu_get_scalars": (C.c_int, [V, P(mwu_scalars)]),
         "mwu_get_timing": (C.c_int, [V, P(mwu_timing), I32]),
         "mwu_potential": (C.c_int, [V, V, P(D), V, V, V]),
+        "mwu_candidates_static": (C.c_int, [V, V, I64, I32, D, D, D, P(D), I32, P(D), P(D), V]),
         "mwu_create_batch": (C.c_int, [I32, P(mwu_matrix), P(mwu_options), P(V)]),
         "mwu_solve_batch": (C.c_int, [V, P(D), P(I64), P(mwu_result)]),
     }
@@ -123,8 +124,8 @@ def exported_symbols():
     """Names of the C entry points this binding expects the library to export."""
     return ["mwu_default_options", "mwu_create", "mwu_destroy", "mwu_last_error", "mwu_set_target",
             "mwu_set_x", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_search", "mwu_solve",
-            "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_potential", "mwu_create_batch",
-            "mwu_solve_batch"]
+            "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_potential", "mwu_candidates_static",
+            "mwu_create_batch", "mwu_solve_batch"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -285,6 +286,19 @@ def mwu_potential(ctx, x, grad_x=None, grad_obj=None, grad_vals=None):
     pot = C.c_double()
     _check(ctx, load().mwu_potential(ctx, _ptr(x), C.byref(pot), _ptr(grad_x), _ptr(grad_obj), _ptr(grad_vals)))
     return pot.value
+
+
+def mwu_candidates_static(v, dv, sign, eta, shift, S, alphas, stream=None):
+    """Allocation-free candidate evaluation of one side (see mwu.h); returns (val, vmin) lists."""
+    K = len(alphas)
+    a = (C.c_double * K)(*[float(x) for x in alphas])
+    val, vmin = (C.c_double * K)(), (C.c_double * K)()
+    if stream is None:
+        stream = _current_stream()
+    rc = load().mwu_candidates_static(_ptr(v), _ptr(dv), int(v.numel()), int(sign), float(eta), float(shift),
+                                      float(S), a, K, val, vmin, stream)
+    _check(None, rc)
+    return list(val), list(vmin)
 
 
 def mwu_create_batch(matrices, options=None, **kw):
