@@ -157,7 +157,8 @@ typedef struct {
  * iteration (FP32 form) or around the launches (FP64 form). */
 typedef struct {
     double dir_ms;             /* gradient + direction kernel (with the deferred x update)   */
-    double cand_first_ms;      /* first candidate pass (forward SpMV dy = Pd, dz = Cd)       */
+    double spmv_ms;            /* forward SpMV dy = Pd, dz = Cd                              */
+    double cand_first_ms;      /* first candidate pass                                       */
     double cand_rest_ms;       /* further candidate passes (exit at once when done)          */
     double update_ms;          /* y, z update with the next iteration's reductions           */
     int64_t iters;             /* iterations timed                                           */

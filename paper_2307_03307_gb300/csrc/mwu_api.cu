@@ -187,7 +187,7 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
         float *tv;
         TRY_CUDA(c, csr_transpose(c->ar, ptr, idx, val, A->rows, A->cols, A->nnz, &tp, &ti, &tv, s));
         double avg_r = (double)A->nnz / (double)A->rows, avg_c = (double)A->nnz / (double)A->cols;
-        sb.rv = RowView{RK_CSR, choose_G(avg_r, forced_G), A->rows, A->nnz, ptr, idx, val, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
+        sb.rv = RowView{RK_CSR, choose_G(avg_r, forced_G), A->rows, A->nnz, ptr, idx, val, rdiv};
         sb.cv = ColView{CK_CSR, choose_G(avg_c, forced_G), tp, ti, tv, rdiv, nullptr, 0, 0, nullptr};
         sb.m = A->rows;
         sb.nvar = A->cols;
@@ -220,25 +220,25 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
                 if ((rc = check_err_flag(c, d_err)) != MWU_OK) return rc;
             }
             if ((rc = load_bounds(nv)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, eids, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
+            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, eids, nullptr, rdiv};
             sb.cv = ColView{CK_FIXED2, 1, nullptr, edges, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = nv;
             sb.nvar = E;
         } else if (A->kind == MWU_MAT_INCIDENCE_T) {
             if ((rc = load_bounds(E)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_FIXED2, 1, E, 2 * E, nullptr, edges, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
+            sb.rv = RowView{RK_FIXED2, 1, E, 2 * E, nullptr, edges, nullptr, rdiv};
             sb.cv = ColView{CK_CSR, choose_G(avg, forced_G), vptr, eids, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = E;
             sb.nvar = nv;
         } else if (A->kind == MWU_MAT_PAIR) {
             if ((rc = load_bounds(nv)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, slots, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
+            sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, slots, nullptr, rdiv};
             sb.cv = ColView{CK_FIXED1, 1, nullptr, edges, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = nv;
             sb.nvar = 2 * E;
         } else {
             if ((rc = load_bounds(E)) != MWU_OK) return rc;
-            sb.rv = RowView{RK_PAIRSUM, 1, E, 2 * E, nullptr, nullptr, nullptr, rdiv, 0, 0, nullptr, 0, 0, nullptr, nullptr};
+            sb.rv = RowView{RK_PAIRSUM, 1, E, 2 * E, nullptr, nullptr, nullptr, rdiv};
             sb.cv = ColView{CK_HALF1, 1, nullptr, nullptr, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = E;
             sb.nvar = 2 * E;
@@ -250,17 +250,45 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
     }
     // heavy rows of CSR row views
     if (sb.rv.kind == RK_CSR) {
-        sb.rv.heavy_len = heavy_len_for(sb.rv.G);
         int32_t *list = nullptr, cnt = 0;
-        TRY_CUDA(c, heavy_list(c->ar, sb.rv.ptr, sb.rv.rows, sb.rv.heavy_len, &list, &cnt, s));
-        sb.rv.heavy = list;
-        sb.rv.n_heavy = cnt;
         TRY_CUDA(c, bin_list(c->ar, sb.rv.ptr, sb.rv.rows, -1, SHORT_LEN, &list, &cnt, s));
         sb.rv.short_rows = list;
         sb.rv.n_short = cnt;
-        TRY_CUDA(c, bin_list(c->ar, sb.rv.ptr, sb.rv.rows, SHORT_LEN, sb.rv.heavy_len, &list, &cnt, s));
+        TRY_CUDA(c, bin_list(c->ar, sb.rv.ptr, sb.rv.rows, SHORT_LEN, MED_LEN, &list, &cnt, s));
         sb.rv.med_rows = list;
         sb.rv.n_med = cnt;
+        // long rows: segments of SEG_LEN entries (host-side table, uploaded once)
+        int32_t *lrows = nullptr, nl = 0;
+        TRY_CUDA(c, bin_list(c->ar, sb.rv.ptr, sb.rv.rows, MED_LEN, INT32_MAX, &lrows, &nl, s));
+        sb.rv.long_rows = lrows;
+        sb.rv.n_long = nl;
+        if (nl > 0) {
+            std::vector<int32_t> lr(nl), hptr(sb.rv.rows + 1);
+            TRY_CUDA(c, cudaMemcpyAsync(lr.data(), lrows, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(c, cudaMemcpyAsync(hptr.data(), sb.rv.ptr, sizeof(int32_t) * (sb.rv.rows + 1),
+                                        cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(c, cudaStreamSynchronize(s));
+            std::vector<int32_t> lseg(nl + 1), srow, sbeg;
+            for (int i = 0; i < nl; ++i) {
+                lseg[i] = (int32_t)srow.size();
+                for (int32_t k = hptr[lr[i]]; k < hptr[lr[i] + 1]; k += SEG_LEN) {
+                    srow.push_back(lr[i]);
+                    sbeg.push_back(k);
+                }
+            }
+            lseg[nl] = (int32_t)srow.size();
+            const int32_t ns = (int32_t)srow.size();
+            int32_t *d_lseg = c->ar.alloc<int32_t>(nl + 1), *d_srow = c->ar.alloc<int32_t>(ns), *d_sbeg = c->ar.alloc<int32_t>(ns);
+            if (!d_lseg || !d_srow || !d_sbeg) return fail(c, MWU_ERR_OOM, "allocating segment tables");
+            TRY_CUDA(c, cudaMemcpyAsync(d_lseg, lseg.data(), sizeof(int32_t) * (nl + 1), cudaMemcpyHostToDevice, s));
+            TRY_CUDA(c, cudaMemcpyAsync(d_srow, srow.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s));
+            TRY_CUDA(c, cudaMemcpyAsync(d_sbeg, sbeg.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s));
+            TRY_CUDA(c, cudaStreamSynchronize(s));
+            sb.rv.long_seg = d_lseg;
+            sb.rv.seg_row = d_srow;
+            sb.rv.seg_beg = d_sbeg;
+            sb.rv.n_seg = ns;
+        }
     }
     if (sb.cv.kind == CK_CSR) sb.cv.heavy_len = heavy_len_for(sb.cv.G);
     return MWU_OK;
@@ -269,7 +297,7 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
 static void dense_side(SideBuild &sb, const float *c, int32_t sign) {
     sb.sign = sign;
     sb.dense = true;
-    sb.rv = RowView{RK_DENSE1, 1, 1, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, 0, 0, nullptr, nullptr};
+    sb.rv = RowView{RK_DENSE1, 1, 1, 0, nullptr, nullptr, nullptr, nullptr};
     sb.cv = ColView{CK_DENSE1, 1, nullptr, nullptr, nullptr, nullptr, c, 0, 0, nullptr};
     sb.m = 1;
     sb.nvar = -1;
@@ -290,10 +318,15 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
         sd.cv = sb[s].cv;
         sd.sign = sb[s].sign;
         sd.m = sb[s].m;
+        sd.seg_part = nullptr;
         if (!sb[s].dense) {
             sd.v = c->ar.alloc<T>(sd.m);
             sd.dv = c->ar.alloc<T>(sd.m);
             if (!sd.v || !sd.dv) return fail(c, MWU_ERR_OOM, "allocating constraint vectors");
+            if (sd.rv.n_seg > 0) {
+                sd.seg_part = c->ar.alloc<T>(sd.rv.n_seg);
+                if (!sd.seg_part) return fail(c, MWU_ERR_OOM, "allocating segment partials");
+            }
         } else {
             sd.v = sd.dv = nullptr;
         }
@@ -302,6 +335,7 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.grid_var = std::max(1, c->n_sms * var_bps);
     p.grid_row = std::max(2, c->n_sms * row_bps);
     p.grid_upd = std::max(2, c->n_sms * std::min(upd_bps, row_bps));
+    p.grid_spmv = std::max(2, c->n_sms * std::min(8, spmv_blocks_per_sm<T>()));
     size_t recs = (size_t)std::max(p.grid_var, std::max(p.grid_row, p.grid_upd)) + 8;
     p.part_var = c->ar.alloc<double>((int64_t)(recs * REC));
     p.part_row = c->ar.alloc<double>((int64_t)(recs * REC));
@@ -573,9 +607,10 @@ int mwu_set_x(mwu_ctx *c, const void *x, int32_t x_is_fp64) {
 }
 
 // ------------------------------------------------------------ iterations
-// kernels of one iteration; ev (5 events or nullptr) brackets the kernel classes.  The
+// kernels of one iteration; ev (6 events or nullptr) brackets the kernel classes.  The
 // events are recorded as external event nodes when the sequence is captured.
-static int kernels_per_iteration(const mwu_ctx *c) { return 2 + c->opt.max_passes; }
+static int kernels_per_iteration(const mwu_ctx *c) { return 3 + c->opt.max_passes; }
+constexpr int EV_PER_IT = 6;
 
 static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev) {
     return with_prob(c, [&](auto &p) -> cudaError_t {
@@ -583,13 +618,15 @@ static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev) {
         if (ev && (e = cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_dir(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = launch_cand(p, 1, 0, c->stream)) != cudaSuccess) return e;
+        if ((e = launch_spmv(p, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        for (int k = 1; k < c->opt.max_passes; ++k)
-            if ((e = launch_cand(p, 0, 0, c->stream)) != cudaSuccess) return e;
+        if ((e = launch_cand(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[3], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = launch_update(p, c->stream)) != cudaSuccess) return e;
+        for (int k = 1; k < c->opt.max_passes; ++k)
+            if ((e = launch_cand(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[4], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if ((e = launch_update(p, c->stream)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[5], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         return cudaSuccess;
     });
 }
@@ -605,12 +642,12 @@ static int make_events(mwu_ctx *c, std::vector<cudaEvent_t> &ev, int n) {
 
 static int capture(mwu_ctx *c, int iters, std::vector<cudaEvent_t> &ev, cudaGraphExec_t *out) {
     int rc;
-    if (c->opt.timing && (rc = make_events(c, ev, 5 * iters)) != MWU_OK) return rc;
+    if (c->opt.timing && (rc = make_events(c, ev, EV_PER_IT * iters)) != MWU_OK) return rc;
     cudaGraph_t g = nullptr;
     TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < iters && e == cudaSuccess; ++k)
-        e = enqueue_iteration(c, c->opt.timing ? &ev[5 * k] : nullptr);
+        e = enqueue_iteration(c, c->opt.timing ? &ev[EV_PER_IT * k] : nullptr);
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail_cuda(c, e, "capture iteration"); }
     if (e2 != cudaSuccess) return fail_cuda(c, e2, "end capture");
@@ -630,12 +667,14 @@ static int ensure_graphs(mwu_ctx *c) {
 // add the event times of the first `real` iterations recorded in ev
 static int accumulate_timing(mwu_ctx *c, const std::vector<cudaEvent_t> &ev, int real) {
     for (int k = 0; k < real; ++k) {
-        float t[4];
-        for (int j = 0; j < 4; ++j) TRY_CUDA(c, cudaEventElapsedTime(&t[j], ev[5 * k + j], ev[5 * k + j + 1]));
+        float t[EV_PER_IT - 1];
+        for (int j = 0; j < EV_PER_IT - 1; ++j)
+            TRY_CUDA(c, cudaEventElapsedTime(&t[j], ev[EV_PER_IT * k + j], ev[EV_PER_IT * k + j + 1]));
         c->tim.dir_ms += t[0];
-        c->tim.cand_first_ms += t[1];
-        c->tim.cand_rest_ms += t[2];
-        c->tim.update_ms += t[3];
+        c->tim.spmv_ms += t[1];
+        c->tim.cand_first_ms += t[2];
+        c->tim.cand_rest_ms += t[3];
+        c->tim.update_ms += t[4];
         c->tim.iters += 1;
     }
     return MWU_OK;
@@ -670,23 +709,25 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
         if (c->fp64) {
             // plain form: host-driven search, one readback per candidate pass
             std::vector<cudaEvent_t> &ev = c->ev_one;
-            if (c->opt.timing && (rc = make_events(c, ev, 5)) != MWU_OK) return rc;
+            if (c->opt.timing && (rc = make_events(c, ev, EV_PER_IT)) != MWU_OK) return rc;
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[0], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 0, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[1], c->stream));
-            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, 0, c->stream); }));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_spmv(p, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[2], c->stream));
-            c->launches += 2;
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[3], c->stream));
+            c->launches += 3;
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             int guard = 0;
             while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE && guard++ < 256) {
-                TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, 0, c->stream); }));
+                TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
                 c->launches += 1;
                 if ((rc = pull_state(c)) != MWU_OK) return rc;
             }
-            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[3], c->stream));
-            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_update(p, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[4], c->stream));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_update(p, c->stream); }));
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[5], c->stream));
             c->launches += 1;
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             if (c->opt.timing && (rc = accumulate_timing(c, ev, c->st_host->iter - iter0)) != MWU_OK) return rc;
@@ -732,7 +773,8 @@ int mwu_direction(mwu_ctx *c, int64_t *n_positive) {
     if (rc != MWU_OK) return rc;
     if (c->st_host->status != ST_RUNNING) return fail(c, MWU_ERR_STATE, "probe not running (set a target or x first)");
     TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 1, c->stream); }));
-    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, 1, c->stream); }));
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_spmv(p, c->stream); }));
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, c->stream); }));
     if ((rc = pull_state(c)) != MWU_OK) return rc;
     if (n_positive) *n_positive = c->st_host->n_pos;
     c->have_direction = true;
@@ -751,7 +793,7 @@ int mwu_eval_candidates(mwu_ctx *c, const double *alphas, int32_t K, double *psi
     h.K = K;
     for (int k = 0; k < K; ++k) h.alpha[k] = alphas[k];
     if ((rc = push_state(c)) != MWU_OK) return rc;
-    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, 1, c->stream); }));
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, c->stream); }));
     if ((rc = pull_state(c)) != MWU_OK) return rc;
     for (int k = 0; k < K; ++k) {
         if (psi) psi[k] = h.psi[k];
@@ -774,7 +816,7 @@ int mwu_search(mwu_ctx *c, double *alpha, int64_t *evals) {
     if (rc != MWU_OK) return rc;
     int guard = 0;
     while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE && guard++ < 256) {
-        TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, 0, c->stream); }));
+        TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
         if ((rc = pull_state(c)) != MWU_OK) return rc;
     }
     if (alpha) *alpha = c->st_host->status == ST_RUNNING ? c->st_host->alpha_acc : 0.0;

@@ -51,17 +51,21 @@ struct RowView {
     const int32_t *idx;   // CSR column index / FIXED2 edge pairs
     const float *val;     // CSR values or nullptr
     const float *rdiv;    // row divisor b_j (bounds) or nullptr
-    int32_t n_heavy;      // rows longer than heavy_len, processed one block each
-    int32_t heavy_len;
-    const int32_t *heavy;
-    // length bins of the light rows for the forward SpMV pass (CSR only):
-    // short rows (<= SHORT_LEN) one thread each, medium rows MED_LANES lanes each
-    int32_t n_short, n_med;
-    const int32_t *short_rows, *med_rows;
+    // length bins of the rows for the forward SpMV (CSR only): short rows
+    // (<= SHORT_LEN) one thread each, medium (<= MED_LEN) MED_LANES lanes each,
+    // long rows cut into segments of SEG_LEN entries, one warp per segment, whose
+    // partial sums the last block adds up per row in order
+    int32_t n_short = 0, n_med = 0;
+    const int32_t *short_rows = nullptr, *med_rows = nullptr;
+    int32_t n_seg = 0, n_long = 0;
+    const int32_t *seg_row = nullptr, *seg_beg = nullptr;     // per segment: its row and first entry
+    const int32_t *long_rows = nullptr, *long_seg = nullptr;  // per long row: row id; segments [long_seg[i], long_seg[i+1])
 };
 
 constexpr int SHORT_LEN = 16;
+constexpr int MED_LEN = 256;
 constexpr int MED_LANES = 16;
+constexpr int SEG_LEN = 1024;
 
 struct ColView {
     int32_t kind;
@@ -84,6 +88,7 @@ struct Side {
     int64_t m;       // rows (1 for the objective row)
     T *v;            // y or z (nullptr for DENSE1)
     T *dv;           // dy or dz
+    T *seg_part;     // per-segment partial sums of long CSR rows
 };
 
 // Probe status values stored on the device.
@@ -138,7 +143,8 @@ struct Problem {
     double *part_row;   // per-block records of row-side kernels
     double *part_grp;   // per-group records (2 x GRP_MAX x REC): candidate passes, update
     int32_t grid_var, grid_row;   // grid sizes (blocks): variable kernels, candidate passes
-    int32_t grid_upd;             // grid of the update kernel (higher occupancy)
+    int32_t grid_upd;             // grid of the update kernel
+    int32_t grid_spmv;            // grid of the forward SpMV (its own occupancy)
     int32_t G_var;      // lanes per variable for CSR column views
     int32_t heavy_var_len;
     int32_t n_heavy_var;
@@ -151,7 +157,8 @@ template <class T> cudaError_t launch_x_init(const Problem<T> &p, cudaStream_t s
 template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, int fp64, cudaStream_t s);
 template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s);             // a1-a3 at a new x
 template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s);      // a4-a5 (+ fused x update)
-template <class T> cudaError_t launch_cand(const Problem<T> &p, int first, int external, cudaStream_t s);  // a6-a7
+template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s);                  // a6: dy = Pd, dz = Cd
+template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s);    // a7: one candidate pass
 template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s);                // a8
 template <class T> cudaError_t launch_flush(const Problem<T> &p, cudaStream_t s);                 // pending x update
 template <class T> cudaError_t launch_search_begin(const Problem<T> &p, cudaStream_t s);
@@ -164,5 +171,6 @@ void set_global_error(const char *msg);
 
 // Kernel occupancy helper (blocks per SM of the heaviest sweep kernel).
 template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_bps);
+template <class T> int spmv_blocks_per_sm();
 
 }  // namespace mwu

@@ -168,7 +168,6 @@ __device__ __forceinline__ T row_gather(const RowView &rv, int64_t j, int lane, 
     switch (rv.kind) {
     case RK_CSR: {
         int beg = rv.ptr[j], end = rv.ptr[j + 1];
-        if (end - beg > rv.heavy_len) return T(0);
         for (int k = beg + lane; k < end; k += G) {
             T t = x[rv.idx[k]];
             if (rv.val) t *= (T)rv.val[k];
@@ -188,33 +187,47 @@ __device__ __forceinline__ T row_gather(const RowView &rv, int64_t j, int lane, 
     return acc;
 }
 
-template <class T> __device__ __forceinline__ bool row_is_heavy(const RowView &rv, int64_t j) {
-    return rv.kind == RK_CSR && (rv.ptr[j + 1] - rv.ptr[j]) > rv.heavy_len;
-}
-
-// Block-wide product of one heavy CSR row.
+// Strided sum over [beg, end) with stride `step`, four independent loads in
+// flight per lane: sum_k val[k] * x[idx[k]] (val == nullptr -> ones).
 template <class T>
-__device__ T heavy_row_gather(const RowView &rv, int64_t j, const T *x, T *smem) {
-    int beg = rv.ptr[j], end = rv.ptr[j + 1];
-    T acc = T(0);
-    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
-        T t = x[rv.idx[k]];
-        if (rv.val) t *= (T)rv.val[k];
-        acc += t;
+__device__ __forceinline__ T strided_gather(const int32_t *idx, const float *val, const T *x, int beg, int end,
+                                            int step) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int k = beg;
+    for (; k + 3 * step < end; k += 4 * step) {
+        const int i0 = idx[k], i1 = idx[k + step], i2 = idx[k + 2 * step], i3 = idx[k + 3 * step];
+        T t0 = x[i0], t1 = x[i1], t2 = x[i2], t3 = x[i3];
+        if (val) {
+            t0 *= (T)val[k]; t1 *= (T)val[k + step]; t2 *= (T)val[k + 2 * step]; t3 *= (T)val[k + 3 * step];
+        }
+        a0 += t0; a1 += t1; a2 += t2; a3 += t3;
     }
-    return block_sum(acc, smem);
+    for (; k < end; k += step) {
+        T t = x[idx[k]];
+        if (val) t *= (T)val[k];
+        a0 += t;
+    }
+    return (a0 + a1) + (a2 + a3);
 }
 
 template <class T, class F>
 __device__ T heavy_col_gather(const ColView &cv, int64_t i, const F &w, T *smem) {
-    int beg = cv.ptr[i], end = cv.ptr[i + 1];
-    T acc = T(0);
-    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
+    const int beg = cv.ptr[i], end = cv.ptr[i + 1], step = (int)blockDim.x;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int k = beg + (int)threadIdx.x;
+    for (; k + 3 * step < end; k += 4 * step) {
+        T t0 = w(cv.idx[k]), t1 = w(cv.idx[k + step]), t2 = w(cv.idx[k + 2 * step]), t3 = w(cv.idx[k + 3 * step]);
+        if (cv.val) {
+            t0 *= (T)cv.val[k]; t1 *= (T)cv.val[k + step]; t2 *= (T)cv.val[k + 2 * step]; t3 *= (T)cv.val[k + 3 * step];
+        }
+        a0 += t0; a1 += t1; a2 += t2; a3 += t3;
+    }
+    for (; k < end; k += step) {
         T t = w(cv.idx[k]);
         if (cv.val) t *= (T)cv.val[k];
-        acc += t;
+        a0 += t;
     }
-    return block_sum(acc, smem);
+    return block_sum((a0 + a1) + (a2 + a3), smem);
 }
 
 // (A x)_j = coef_j * sum_k val_jk x_k with coef_j = scale / rdiv_j; the scale
@@ -358,74 +371,36 @@ __device__ void finalize_reductions(Problem<T> &p, const double *recs, int nb_ro
     }
 }
 
-// ============================================================ rows at a new x
-// y = P x, z = C x (a1) and the LSE reductions of both (a2, a3).
-template <class T>
-__global__ void __launch_bounds__(BLOCK) k_rows_eval(Problem<T> p, int gP, int nb_var) {
-    __shared__ T sm[32];
-    DevState *st = p.st;
-    int s = (blockIdx.x < gP) ? 0 : 1;
-    int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
-    int nbs = s == 0 ? gP : gridDim.x - gP;
-    const Side<T> &sd = p.side[s];
-    T eta_sgn = (T)(st->eta * sd.sign);
-    Lse<T> acc{T(0), T(0)};
-    if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
-        const RowView &rv = sd.rv;
-        // heavy rows: one block each
-        for (int h = bid; h < rv.n_heavy; h += nbs) {
-            int64_t j = rv.heavy[h];
-            T sum = heavy_row_gather(rv, j, p.x, sm);
-            if (threadIdx.x == 0) {
-                T vj = sum * row_coef(sd, j, st->scale[s]);
-                sd.v[j] = vj;
-                lse_push(acc, vj, eta_sgn, sd.sign);
-            }
-        }
-        int G = rv.G, lane = threadIdx.x & (G - 1);
-        int64_t groups = (int64_t)nbs * (blockDim.x / G);
-        int64_t gid = (int64_t)bid * (blockDim.x / G) + threadIdx.x / G;
-        int64_t stride_rows = groups;
-        int64_t warp_base = gid - (threadIdx.x & 31) / G;
-        for (int64_t base = warp_base; base < sd.m; base += stride_rows) {
-            int64_t j = base + (threadIdx.x & 31) / G;
-            bool live = j < sd.m;
-            T sum = live ? row_gather(rv, j, lane, G, p.x) : T(0);
-            sum = group_sum(sum, G);
-            if (live && lane == 0 && !row_is_heavy<T>(rv, j)) {
-                T vj = sum * row_coef(sd, j, st->scale[s]);
-                sd.v[j] = vj;
-                lse_push(acc, vj, eta_sgn, sd.sign);
-            }
-        }
+// ============================================================ gradient + direction
+// End of the direction step (one thread): d = 0 -> INFEASIBLE (Alg. 2), else the
+// step-size search starts (Alg. 3: alpha = 1, or the warm start).
+__device__ void dir_finish(DevState *st, double np_t, double dd0, double dd1) {
+    st->n_pos = (long long)np_t;
+    st->dense_dv[0] = st->scale[0] * dd0;
+    st->dense_dv[1] = st->scale[1] * dd1;
+    if (np_t <= 0.0) {
+        st->status = ST_INFEASIBLE;
+        st->reason = RS_DZERO;
+        st->phase = PH_DONE;
+        return;
     }
-    // block merge of (s, S): warp shuffles then shared memory
-    __shared__ double bs[BLOCK / 32], bS[BLOCK / 32];
-    Lse<double> a{(double)acc.s, (double)acc.S};
-    double eds = st->eta * sd.sign;
-    for (int off = 16; off > 0; off >>= 1) {
-        double os = __shfl_xor_sync(0xffffffffu, a.s, off);
-        double oS = __shfl_xor_sync(0xffffffffu, a.S, off);
-        lse_merge<T, double>(a, os, oS, eds, sd.sign);
-    }
-    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = a.s; bS[threadIdx.x >> 5] = a.S; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Lse<double> r{0.0, 0.0};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge<T, double>(r, bs[w], bS[w], eds, sd.sign);
-        double *rec = p.part_row + (size_t)blockIdx.x * REC;
-        rec[2 * s] = r.s;
-        rec[2 * s + 1] = r.S;
-        rec[2 * (1 - s)] = 0.0;
-        rec[2 * (1 - s) + 1] = 0.0;
-    }
-    if (last_block_done(&st->counter[0])) {
-        finalize_reductions(p, p.part_row, gridDim.x, nb_var, true, 0.0);
-        if (threadIdx.x == 0) st->counter[0] = 0;
+    st->phase = PH_EXP;
+    st->lb = 0.0;
+    st->ub = (double)INFINITY;
+    st->passes = 0;
+    st->early = 0;
+    st->alpha_acc = 0.0;
+    int b0 = 0;
+    if (st->warm_start && st->alpha_prev >= 1.0) b0 = (int)floor(log2(st->alpha_prev));
+    st->b = b0;
+    for (int k = 0; k < st->K; ++k) st->alpha[k] = ldexp(1.0, b0 + k);
+    if (st->step_mode == 2) {   // standard step alpha = 1 (Alg. 1)
+        st->phase = PH_DONE;
+        st->alpha_acc = 1.0;
     }
 }
 
-// ============================================================ gradient + direction
+
 // a4, a5 with the deferred x update of the previous iteration fused in.
 template <class T>
 __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int potential_mode, float *grad_obj) {
@@ -521,31 +496,100 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
             if (st->pending) {   // the deferred update of x is now applied
                 st->pending = 0;
             }
-            if (running) {
-                st->n_pos = (long long)np_t;
-                for (int s = 0; s < 2; ++s) st->dense_dv[s] = st->scale[s] * dd[s];
-                if (np_t <= 0.0) {
-                    st->status = ST_INFEASIBLE;
-                    st->reason = RS_DZERO;
-                    st->phase = PH_DONE;
-                } else {
-                    // search initialisation (Alg. 3: alpha starts at 1; warm start optional)
-                    st->phase = PH_EXP;
-                    st->lb = 0.0;
-                    st->ub = (double)INFINITY;
-                    st->passes = 0;
-                    st->early = 0;
-                    st->alpha_acc = 0.0;
-                    int b0 = 0;
-                    if (st->warm_start && st->alpha_prev >= 1.0) b0 = (int)floor(log2(st->alpha_prev));
-                    st->b = b0;
-                    for (int k = 0; k < st->K; ++k) st->alpha[k] = ldexp(1.0, b0 + k);
-                    if (st->step_mode == 2) {   // standard step alpha = 1 (Alg. 1)
-                        st->phase = PH_DONE;
-                        st->alpha_acc = 1.0;
-                    }
-                }
+            if (running) dir_finish(st, np_t, dd[0], dd[1]);
+            st->counter[1] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------ k_dir, pair matrices
+// The densest-subgraph LP (Sec. 3, Eq. densest_linalg): variable slots 2e, 2e+1
+// of edge e sit in packing rows u_e, v_e of O (column view FIXED1 over the edge
+// list) and both in covering row e of W (HALF1).  One thread takes both slots:
+// one covering weight per edge, two packing weights, 8-byte loads of x, d and
+// the endpoints.  Same arithmetic as the generic k_dir per slot.
+template <class T>
+__global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
+    __shared__ double smd[32];
+    DevState *st = p.st;
+    if (st->status != ST_RUNNING && !st->pending) return;
+    const bool running = st->status == ST_RUNNING;
+    const T alpha_prev = st->pending ? (T)st->alpha_acc : T(0);
+    const Side<T> &P = p.side[0];
+    const Side<T> &C = p.side[1];
+    const T eta = (T)st->eta, sp = (T)st->s[0], sc = (T)st->s[1];
+    const T fp = (T)(st->scale[0] / st->S[0]);
+    const T fc = (T)(st->scale[1] / st->S[1]);
+    const T cd = (T)st->c_d;
+    const T thr = (T)(1.0 - st->grad_tol);
+    const int64_t E = p.n >> 1;
+    const int2 *ends = reinterpret_cast<const int2 *>(P.cv.idx);
+    long long npos = 0;
+    // one edge per lane and iteration, two iterations' loads in flight
+    auto one_edge = [&](int64_t e, const int2 uv, T x0, T x1, T yu, T yv, T ze) {
+        T wu = t_exp(eta * (yu - sp));
+        T wv = t_exp(eta * (yv - sp));
+        if (P.rv.rdiv) { wu /= (T)P.rv.rdiv[uv.x]; wv /= (T)P.rv.rdiv[uv.y]; }
+        T wc = t_exp(-eta * (ze - sc));
+        if (C.rv.rdiv) wc /= (T)C.rv.rdiv[e];
+        const T h = wc * fc;
+        const T g0 = wu * fp, g1 = wv * fp;
+        const T d0 = (g0 < thr * h) ? cd * (T(1) - g0 / h) * x0 : T(0);
+        const T d1 = (g1 < thr * h) ? cd * (T(1) - g1 / h) * x1 : T(0);
+        if (sizeof(T) == 4) reinterpret_cast<float2 *>(p.d)[e] = make_float2((float)d0, (float)d1);
+        else { p.d[2 * e] = d0; p.d[2 * e + 1] = d1; }
+        npos += (d0 > T(0)) + (d1 > T(0));
+    };
+    auto load_x = [&](int64_t e, T &x0, T &x1) {
+        if (sizeof(T) == 4) {
+            float2 xx = reinterpret_cast<const float2 *>(p.x)[e];
+            x0 = xx.x; x1 = xx.y;
+            if (alpha_prev != T(0)) {
+                float2 dd = reinterpret_cast<const float2 *>(p.d)[e];
+                x0 += alpha_prev * dd.x; x1 += alpha_prev * dd.y;
+                reinterpret_cast<float2 *>(p.x)[e] = make_float2((float)x0, (float)x1);
             }
+        } else {
+            x0 = p.x[2 * e]; x1 = p.x[2 * e + 1];
+            if (alpha_prev != T(0)) {
+                x0 += alpha_prev * p.d[2 * e]; x1 += alpha_prev * p.d[2 * e + 1];
+                p.x[2 * e] = x0; p.x[2 * e + 1] = x1;
+            }
+        }
+    };
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; e + stride < E; e += 2 * stride) {
+        const int64_t f = e + stride;
+        T xa0, xa1, xb0, xb1;
+        load_x(e, xa0, xa1);
+        load_x(f, xb0, xb1);
+        if (!running) continue;
+        const int2 ua = ends[e], ub = ends[f];
+        const T ya = P.v[ua.x], yb = P.v[ua.y], yc = P.v[ub.x], yd = P.v[ub.y];
+        const T za = C.v[e], zb = C.v[f];
+        one_edge(e, ua, xa0, xa1, ya, yb, za);
+        one_edge(f, ub, xb0, xb1, yc, yd, zb);
+    }
+    for (; e < E; e += stride) {
+        T x0, x1;
+        load_x(e, x0, x1);
+        if (!running) continue;
+        const int2 uv = ends[e];
+        one_edge(e, uv, x0, x1, P.v[uv.x], P.v[uv.y], C.v[e]);
+    }
+    const double np = block_sum((double)npos, smd);
+    if (threadIdx.x == 0) {
+        double *rec = p.part_var + (size_t)blockIdx.x * REC;
+        rec[0] = np; rec[1] = 0.0; rec[2] = 0.0;
+    }
+    if (last_block_done(&st->counter[1])) {
+        double a0 = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a0 += p.part_var[(size_t)b * REC];
+        const double np_t = block_sum(a0, smd);
+        if (threadIdx.x == 0) {
+            st->pending = 0;
+            if (running) dir_finish(st, np_t, 0.0, 0.0);
             st->counter[1] = 0;
         }
     }
@@ -782,16 +826,169 @@ __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> 
     }
 }
 
-// a6 + a7: dv = A d on the first pass, then K candidates per row.
+template <class T>
+__device__ __forceinline__ void spmv_side(const Problem<T> &p, int s, const T *__restrict__ in, int to_v) {
+    const DevState *st = p.st;
+    const int bid = blockIdx.x, nbs = gridDim.x;
+    const Side<T> &sd = p.side[s];
+    const RowView &rv = sd.rv;
+    if (rv.kind == RK_DENSE1 || rv.kind == RK_NONE) return;
+    T *out = to_v ? sd.v : sd.dv;
+    const double scale = st->scale[s];
+    const int64_t m = sd.m;
+    const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nbs * blockDim.x;
+    if (rv.kind != RK_CSR) {
+        for (int64_t j0 = 4 * tid; j0 < m; j0 += 4 * nthr) {
+            const int nr = (int)min((int64_t)4, m - j0);
+            T dd[4];
+            if (rv.kind == RK_PAIRSUM && nr == 4 && sizeof(T) == 4) {
+                const float4 a = reinterpret_cast<const float4 *>(in)[j0 >> 1];
+                const float4 b = reinterpret_cast<const float4 *>(in)[(j0 >> 1) + 1];
+                dd[0] = a.x + a.y; dd[1] = a.z + a.w; dd[2] = b.x + b.y; dd[3] = b.z + b.w;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    dd[r] = T(0);
+                    if (r < nr) {
+                        const int64_t j = j0 + r;
+                        dd[r] = (rv.kind == RK_PAIRSUM) ? in[2 * j] + in[2 * j + 1] : row_gather(rv, j, 0, 1, in);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) dd[r] *= row_coef(sd, j0 + r < m ? j0 + r : j0, scale);
+            if (nr == 4 && sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(out + j0) = make_float4((float)dd[0], (float)dd[1], (float)dd[2], (float)dd[3]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r < nr) out[j0 + r] = dd[r];
+            }
+        }
+        return;
+    }
+    {   // segments of long rows: one warp each, partial sums to seg_part
+        const int lane = threadIdx.x & 31;
+        const int64_t w = tid >> 5, nw = nthr >> 5;
+        for (int64_t i = w; i < rv.n_seg; i += nw) {
+            const int j = rv.seg_row[i];
+            const int kb = rv.seg_beg[i];
+            const int ke = min(kb + SEG_LEN, rv.ptr[j + 1]);
+            T sum = strided_gather(rv.idx, rv.val, in, kb + lane, ke, 32);
+            sum = group_sum(sum, 32);
+            if (lane == 0) sd.seg_part[i] = sum;
+        }
+    }
+    {   // medium rows: MED_LANES lanes each
+        const int lane = threadIdx.x & (MED_LANES - 1);
+        const int64_t gid = tid / MED_LANES, ngroups = nthr / MED_LANES;
+        const int64_t wbase = gid - (threadIdx.x & 31) / MED_LANES;   // first group of this warp
+        for (int64_t b0 = wbase; b0 < rv.n_med; b0 += ngroups) {
+            const int64_t i = b0 + (threadIdx.x & 31) / MED_LANES;
+            T sum = T(0);
+            int64_t j = -1;
+            if (i < rv.n_med) {
+                j = rv.med_rows[i];
+                sum = strided_gather(rv.idx, rv.val, in, rv.ptr[j] + lane, rv.ptr[j + 1], MED_LANES);
+            }
+            sum = group_sum(sum, MED_LANES);
+            if (j >= 0 && lane == 0) out[j] = sum * row_coef(sd, j, scale);
+        }
+    }
+    for (int64_t i = tid; i < rv.n_short; i += nthr) {   // short rows: one thread each
+        const int64_t j = rv.short_rows[i];
+        out[j] = strided_gather(rv.idx, rv.val, in, rv.ptr[j], rv.ptr[j + 1], 1) * row_coef(sd, j, scale);
+    }
+}
+
+// Forward SpMV out = A in for both sides: dv = A d each iteration (dy = Pd,
+// dz = Cd; Alg. 2) and v = A x at a new x (y = Px, z = Cx).  No candidate work,
+// so it runs at high occupancy.  Every block works on both sides in turn (the
+// gathers of one side overlap the streaming of the other, and no block runs
+// out of work early).  CSR rows are binned by length at setup: rows longer
+// than MED_LEN are cut into SEG_LEN-entry segments, one warp per segment, so no
+// block holds a long tail; medium rows take MED_LANES lanes, short rows one
+// thread.  The pair rows of W and the edge rows of M^T are streamed four per
+// thread.  Every gather loop keeps four independent loads in flight.  Segment
+// partials are added per row in a fixed order by the last block, so the
+// result does not depend on scheduling.
+template <class T>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<T> p, const T *__restrict__ in, int to_v) {
+    DevState *st = p.st;
+    if (!to_v && st->status != ST_RUNNING) return;
+    spmv_side(p, 0, in, to_v);
+    spmv_side(p, 1, in, to_v);
+    if (p.side[0].rv.n_seg == 0 && p.side[1].rv.n_seg == 0) return;
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->counter[5], 1u) == (unsigned)(gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        const Side<T> &sd = p.side[s];
+        const RowView &rv = sd.rv;
+        if (rv.kind != RK_CSR) continue;
+        T *out = to_v ? sd.v : sd.dv;
+        const double scale = st->scale[s];
+        for (int i = threadIdx.x; i < rv.n_long; i += blockDim.x) {
+            const int j = rv.long_rows[i];
+            T sum = T(0);
+            for (int q = rv.long_seg[i]; q < rv.long_seg[i + 1]; ++q) sum += sd.seg_part[q];
+            out[j] = sum * row_coef(sd, j, scale);
+        }
+    }
+    if (threadIdx.x == 0) st->counter[5] = 0;
+}
+
+// Log-sum-exp reductions of y and z at a new x (a2, a3): a stream over both
+// sides, then the dense rows from k_x_prep's records and the stopping test.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb_var) {
+    DevState *st = p.st;
+    const int s = (blockIdx.x < gP) ? 0 : 1;
+    const int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
+    const int nbs = s == 0 ? gP : gridDim.x - gP;
+    const Side<T> &sd = p.side[s];
+    const T eta_sgn = (T)(st->eta * sd.sign);
+    Lse<T> acc{T(0), T(0)};
+    if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
+        for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < sd.m; j += (int64_t)nbs * blockDim.x)
+            lse_push(acc, sd.v[j], eta_sgn, sd.sign);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        T os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
+        lse_merge<T, T>(acc, os, oS, eta_sgn, sd.sign);
+    }
+    __shared__ double bs[BLOCK / 32], bS[BLOCK / 32];
+    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = (double)acc.s; bS[threadIdx.x >> 5] = (double)acc.S; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double eds = st->eta * sd.sign;
+        Lse<double> r{0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge<T, double>(r, bs[w], bS[w], eds, sd.sign);
+        double *rec = p.part_row + (size_t)blockIdx.x * REC;
+        rec[2 * s] = r.s; rec[2 * s + 1] = r.S;
+        rec[2 * (1 - s)] = 0.0; rec[2 * (1 - s) + 1] = 0.0;
+    }
+    if (last_block_done(&st->counter[0])) {
+        finalize_reductions(p, p.part_row, gridDim.x, nb_var, true, 0.0);
+        if (threadIdx.x == 0) st->counter[0] = 0;
+    }
+}
+
+// a7: K step candidates per constraint row over the stored (v, dv).
 // external = 1: evaluate st->alpha[0..K) and store psi/phi/zmin, no decision.
 template <class T>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int first, int external) {
-    __shared__ T sm[32];
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int external) {
     __shared__ CandSched<T> s_sc;
     DevState *st = p.st;
     if (st->status != ST_RUNNING) return;
     const bool searching = external || st->phase != PH_DONE;
-    if (!first && !searching) return;
+    if (!searching) return;
     const int K = st->K;
     int s = (blockIdx.x < gP) ? 0 : 1;
     int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
@@ -816,12 +1013,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
     const int64_t m = sd.m;
     const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)nbs * blockDim.x;
-    const bool csr_first = first && sd.rv.kind == RK_CSR;
-    if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) {
-        // single objective row: handled exactly by the decision step
-    } else if (!first && searching) {
-        // later passes: a pure stream over the stored (v, dv), four rows per thread,
-        // with the schedule in registers and the loop specialised per (mode, side)
+    if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
+        // a pure stream over the stored (v, dv), four rows per thread, with the
+        // schedule in registers and the loop specialised per (mode, side)
         const int md = sc.mode;
         if (sc.K == KMAX) {
             if (sd.sign > 0) {
@@ -837,115 +1031,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
             if (sd.sign > 0) cand_stream<T, 2, 1, 0>(acc, sc, sd, m, tid, nthr, eta, sh);
             else cand_stream<T, 2, -1, 0>(acc, sc, sd, m, tid, nthr, eta, sh);
         }
-    } else if (!csr_first) {
-        // first pass over implicit row kinds (pairs / edges): dv formed, stored and used
-        const RowView &rv = sd.rv;
-        const double scale = st->scale[s];
-        {
-        for (int64_t j0 = 4 * tid; j0 < m; j0 += 4 * nthr) {
-            T vv[4], dd[4];
-            const int nr = (int)min((int64_t)4, m - j0);
-            if (nr == 4 && sizeof(T) == 4) {
-                float4 a4 = *reinterpret_cast<const float4 *>(sd.v + j0);
-                vv[0] = a4.x; vv[1] = a4.y; vv[2] = a4.z; vv[3] = a4.w;
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) vv[r] = r < nr ? sd.v[j0 + r] : T(0);
-            }
-            if (!first) {
-                if (nr == 4 && sizeof(T) == 4) {
-                    float4 b4 = *reinterpret_cast<const float4 *>(sd.dv + j0);
-                    dd[0] = b4.x; dd[1] = b4.y; dd[2] = b4.z; dd[3] = b4.w;
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) dd[r] = r < nr ? sd.dv[j0 + r] : T(0);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    dd[r] = T(0);
-                    if (r < nr) {
-                        int64_t j = j0 + r;
-                        T sum = (rv.kind == RK_PAIRSUM) ? p.d[2 * j] + p.d[2 * j + 1] : row_gather(rv, j, 0, 1, p.d);
-                        dd[r] = sum * row_coef(sd, j, scale);
-                    }
-                }
-                if (nr == 4 && sizeof(T) == 4) {
-                    *reinterpret_cast<float4 *>(sd.dv + j0) = make_float4((float)dd[0], (float)dd[1], (float)dd[2], (float)dd[3]);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        if (r < nr) sd.dv[j0 + r] = dd[r];
-                }
-            }
-            if (searching) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (r < nr) cand_push(acc, sc, sd.sign, vv[r], dd[r], eta, sh);
-            }
-        }
-        }
-    } else {
-        // first pass over CSR rows, binned by length at setup: heavy rows one block
-        // each, medium rows MED_LANES lanes each (lane 0 evaluates the candidates),
-        // short rows one thread each (every lane evaluates its own row)
-        const RowView &rv = sd.rv;
-        const double scale = st->scale[s];
-        for (int h = bid; h < rv.n_heavy; h += nbs) {
-            int64_t j = rv.heavy[h];
-            T dvj = heavy_row_gather(rv, j, p.d, sm) * row_coef(sd, j, scale);
-            if (threadIdx.x == 0) {
-                sd.dv[j] = dvj;
-                if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
-            }
-        }
-        {
-            const int lane = threadIdx.x & (MED_LANES - 1);
-            const int64_t gid = tid / MED_LANES, ngroups = nthr / MED_LANES;
-            const int64_t wbase = gid - (threadIdx.x & 31) / MED_LANES;   // first group of this warp
-            for (int64_t b0 = wbase; b0 < rv.n_med; b0 += ngroups) {
-                int64_t i = b0 + (threadIdx.x & 31) / MED_LANES;
-                T sum = T(0);
-                int64_t j = -1;
-                if (i < rv.n_med) {
-                    j = rv.med_rows[i];
-                    int beg = rv.ptr[j], end = rv.ptr[j + 1];
-                    for (int k = beg + lane; k < end; k += MED_LANES) {
-                        T t = p.d[rv.idx[k]];
-                        if (rv.val) t *= (T)rv.val[k];
-                        sum += t;
-                    }
-                }
-                sum = group_sum(sum, MED_LANES);
-                if (j >= 0 && lane == 0) {
-                    T dvj = sum * row_coef(sd, j, scale);
-                    sd.dv[j] = dvj;
-                    if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
-                }
-            }
-        }
-        for (int64_t i = tid; i < rv.n_short; i += nthr) {
-            const int64_t j = rv.short_rows[i];
-            const int beg = rv.ptr[j], end = rv.ptr[j + 1];
-            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-            int k = beg;
-            for (; k + 4 <= end; k += 4) {
-                int i0 = rv.idx[k], i1 = rv.idx[k + 1], i2 = rv.idx[k + 2], i3 = rv.idx[k + 3];
-                T t0 = p.d[i0], t1 = p.d[i1], t2 = p.d[i2], t3 = p.d[i3];
-                if (rv.val) { t0 *= (T)rv.val[k]; t1 *= (T)rv.val[k + 1]; t2 *= (T)rv.val[k + 2]; t3 *= (T)rv.val[k + 3]; }
-                s0 += t0; s1 += t1; s2 += t2; s3 += t3;
-            }
-            for (; k < end; ++k) {
-                T t = p.d[rv.idx[k]];
-                if (rv.val) t *= (T)rv.val[k];
-                s0 += t;
-            }
-            T dvj = ((s0 + s1) + (s2 + s3)) * row_coef(sd, j, scale);
-            sd.dv[j] = dvj;
-            if (searching) cand_push(acc, sc, sd.sign, sd.v[j], dvj, eta, sh);
-        }
     }
-    if (!searching) return;   // standard step: dv written, nothing to evaluate
     // block merge: warp shuffles in T, then warps in FP64
     __shared__ double wm[BLOCK / 32][KMAX][4];
 #pragma unroll
@@ -1225,19 +1311,23 @@ static int grid_for(int64_t n, int cap) {
     return (int)g;
 }
 
-template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC) {
+// Blocks of a candidate pass are split between the two sides in proportion to
+// their work: the candidate arithmetic (K exp terms per row, weighed as 4
+// gathers each) plus, on the first pass, one unit per gathered entry of A d.
+template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC, bool first = true) {
     int total = p.grid_row;
-    auto work = [&](const Side<T> &s) -> double {   // gathers + rows
+    auto work = [&](const Side<T> &s) -> double {
         if (s.rv.kind == RK_DENSE1 || s.rv.kind == RK_NONE) return 0.0;
-        if (s.rv.kind == RK_CSR) return (double)s.rv.nnz + (double)s.m;
-        return 3.0 * (double)s.m;
+        double w = 4.0 * KMAX * (double)s.m;
+        if (first) w += (double)s.rv.nnz;
+        return w;
     };
     double wP = work(p.side[0]), wC = work(p.side[1]);
     auto need = [&](const Side<T> &s) -> int {
         if (s.rv.kind == RK_DENSE1 || s.rv.kind == RK_NONE) return 0;
         int64_t groups_per_block = BLOCK / s.rv.G;
         int64_t g = (s.m + groups_per_block - 1) / groups_per_block;
-        return (int)std::max<int64_t>(1, std::max<int64_t>(g, (int64_t)s.rv.n_heavy));
+        return (int)std::max<int64_t>(1, g);
     };
     int nP = need(p.side[0]), nC = need(p.side[1]);
     if (wP + wC <= 0.0) { *gP = 1; *gC = 0; return; }
@@ -1252,15 +1342,38 @@ template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC)
     if (*gP + *gC == 0) *gP = 1;
 }
 
+// grid of the forward SpMV: every block covers both sides; no more blocks than
+// the larger side has work items (a warp per segment, four rows per thread)
+template <class T> static int spmv_grid(const Problem<T> &p) {
+    auto need = [&](const Side<T> &sd) -> int64_t {
+        if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) return 0;
+        const int64_t items = sd.rv.kind == RK_CSR ? std::max<int64_t>(sd.m / 4, 32 * (int64_t)sd.rv.n_seg)
+                                                   : (sd.m + 3) / 4;
+        return (items + BLOCK - 1) / BLOCK;
+    };
+    const int64_t n = std::max(need(p.side[0]), need(p.side[1]));
+    return (int)std::max<int64_t>(0, std::min<int64_t>(n, p.grid_spmv));
+}
+
+template <class T> static cudaError_t rows_at_x(const Problem<T> &p, int nb_var, cudaStream_t s) {
+    const int gs = spmv_grid(p);
+    if (gs > 0) {
+        k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.x, 1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    int gP, gC;
+    split_rows(p, &gP, &gC, false);
+    k_rows_lse<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, nb_var);
+    return cudaGetLastError();
+}
+
 template <class T> cudaError_t launch_x_init(const Problem<T> &p, cudaStream_t s) {
     int g = grid_for(p.n, p.grid_var);
     k_x_prep<T><<<g, BLOCK, 0, s>>>(p, nullptr, 0, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int gP, gC;
-    split_rows(p, &gP, &gC);
-    k_rows_eval<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, g);
-    return cudaGetLastError();
+    return rows_at_x(p, g, s);
 }
 
 template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, int fp64, cudaStream_t s) {
@@ -1268,20 +1381,19 @@ template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, 
     k_x_prep<T><<<g, BLOCK, 0, s>>>(p, x, fp64, 1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int gP, gC;
-    split_rows(p, &gP, &gC);
-    k_rows_eval<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, g);
-    return cudaGetLastError();
+    return rows_at_x(p, g, s);
 }
 
 template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s) {
-    int gP, gC;
-    split_rows(p, &gP, &gC);
-    k_rows_eval<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, 0);
-    return cudaGetLastError();
+    return launch_x_set(p, p.x, sizeof(T) == 8 ? 1 : 0, s);
 }
 
 template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s) {
+    if (!keep_gh && p.side[0].cv.kind == CK_FIXED1 && p.side[1].cv.kind == CK_HALF1) {
+        int g = (int)std::max<int64_t>(1, std::min<int64_t>((p.n / 2 + BLOCK - 1) / BLOCK, p.grid_var));
+        k_dir_pairs<T><<<g, BLOCK, 0, s>>>(p);
+        return cudaGetLastError();
+    }
     int64_t per_block = BLOCK / p.G_var;
     int64_t need = std::max<int64_t>((p.n + per_block - 1) / per_block, p.n_heavy_var);
     int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, p.grid_var));
@@ -1289,10 +1401,17 @@ template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cuda
     return cudaGetLastError();
 }
 
-template <class T> cudaError_t launch_cand(const Problem<T> &p, int first, int external, cudaStream_t s) {
+template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s) {
+    const int gs = spmv_grid(p);
+    if (gs == 0) return cudaSuccess;
+    k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.d, 0);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s) {
     int gP, gC;
-    split_rows(p, &gP, &gC);
-    k_cand<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, first, external);
+    split_rows(p, &gP, &gC, false);
+    k_cand<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, external);
     return cudaGetLastError();
 }
 
@@ -1366,19 +1485,27 @@ template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_
     return 0;
 }
 
+template <class T> int spmv_blocks_per_sm() {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spmv<T>, BLOCK, 0);
+    return a > 0 ? a : 1;
+}
+
 #define MWU_INSTANTIATE(T)                                                                                     \
     template cudaError_t launch_x_init<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_x_set<T>(const Problem<T> &, const void *, int, cudaStream_t);                 \
     template cudaError_t launch_rows_eval<T>(const Problem<T> &, cudaStream_t);                                \
     template cudaError_t launch_dir<T>(const Problem<T> &, int, cudaStream_t);                                 \
-    template cudaError_t launch_cand<T>(const Problem<T> &, int, int, cudaStream_t);                           \
+    template cudaError_t launch_spmv<T>(const Problem<T> &, cudaStream_t);                                     \
+    template cudaError_t launch_cand<T>(const Problem<T> &, int, cudaStream_t);                                \
     template cudaError_t launch_update<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_flush<T>(const Problem<T> &, cudaStream_t);                                    \
     template cudaError_t launch_search_begin<T>(const Problem<T> &, cudaStream_t);                             \
     template cudaError_t launch_potential_grads<T>(const Problem<T> &, const float *, float *, float *,        \
                                                    float *, float *, cudaStream_t);                            \
     template cudaError_t launch_copy_vec<T>(const T *, void *, int64_t, int, cudaStream_t);                    \
-    template int sweep_blocks_per_sm<T>(int *, int *, int *);
+    template int sweep_blocks_per_sm<T>(int *, int *, int *);                                                  \
+    template int spmv_blocks_per_sm<T>();
 
 MWU_INSTANTIATE(float)
 MWU_INSTANTIATE(double)
