@@ -156,6 +156,7 @@ class SearchInfo:
     evals: int = 0          # number of f(alpha) evaluations
     passes: int = 0         # number of candidate sets evaluated
     early: bool = False     # returned by the early-exit rule
+    newton: int = 0         # Newton evaluations (f and f' at one alpha)
     candidates: list = field(default_factory=list)
 
 
@@ -282,6 +283,141 @@ def search_kary(evaluate, eps, K=8, b0=0, max_passes=64):
     return lb, info
 
 
+def dPsi(y, dy, alpha, eta):
+    """Psi'(alpha) = <dy, exp(eta (y + alpha dy))> / <1, exp(eta (y + alpha dy))> (Sec. 4.2, Newton's method)."""
+    y = np.asarray(y, dtype=np.float64)
+    dy = np.asarray(dy, dtype=np.float64)
+    return float(dy @ grad_smax(y + alpha * dy, eta))
+
+
+def dPhi(z, dz, alpha, eta):
+    """Phi'(alpha) = <dz, exp(-eta (z + alpha dz))> / <1, exp(-eta (z + alpha dz))> (Sec. 4.2, Newton's method)."""
+    z = np.asarray(z, dtype=np.float64)
+    dz = np.asarray(dz, dtype=np.float64)
+    return float(dz @ grad_smin(z + alpha * dz, eta))
+
+
+def make_newton_evaluator(y, dy, z, dz, eta):
+    """Single-candidate evaluator for Newton's method: (Psi, Phi, Psi', Phi') at alpha."""
+    y = np.asarray(y, dtype=np.float64)
+    dy = np.asarray(dy, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    dz = np.asarray(dz, dtype=np.float64)
+
+    def evaluate(alpha):
+        return (Psi(y, dy, alpha, eta), Phi(z, dz, alpha, eta), dPsi(y, dy, alpha, eta), dPhi(z, dz, alpha, eta))
+
+    return evaluate
+
+
+def newton_update(alpha, psi, phi, dpsi, dphi, lb, ub):
+    """One Newton step on g(alpha) = f(alpha) - 1 with f = Phi/Psi (Sec. 4.2).
+
+    alpha' = alpha - g/g' with g' = (Psi Phi' - Phi Psi') / Psi^2, i.e.
+    alpha' = alpha - (Phi - Psi) Psi / (Psi Phi' - Phi Psi').
+    Reading (safeguard; the paper gives none): [lb, ub] brackets the root by
+    Prop. 4.2 (f(lb) >= 1 > f(ub)).  A step that is undefined (Psi <= 0,
+    g' >= 0, not finite) or leaves the open bracket is replaced by the
+    midpoint (lb + ub)/2, or by 2 alpha while ub is still infinite.
+    """
+    den = psi * dphi - phi * dpsi
+    nxt = math.nan
+    if psi > 0.0 and den < 0.0 and math.isfinite(den):
+        nxt = alpha - (phi - psi) * psi / den
+    if not (math.isfinite(nxt) and lb < nxt < ub):
+        nxt = 0.5 * (lb + ub) if math.isfinite(ub) else 2.0 * alpha
+    return nxt
+
+
+def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, max_passes=64, tol=None):
+    """Step size by Newton's method on f(alpha) = 1 (Sec. 4.2), warm-started.
+
+    * Start: alpha_0 = the previous iteration's step size when given (warm
+      start); otherwise the exponential phase of the K-candidate search
+      (candidates 2^(b+k), early exit on min(z + alpha dz) >= 1) brackets the
+      root in [2^p, 2^(p+1)] and alpha_0 = 2^p.
+    * Newton: alpha_{k+1} = alpha_k - g(alpha_k)/g'(alpha_k), g = f - 1 (see
+      ``newton_update`` for the safeguard).  Reading (the paper gives no rule):
+      the iteration has converged at alpha_k once |alpha_{k+1} - alpha_k| <=
+      tol alpha_k (default tol = eps/20), or after ``max_newton`` evaluations.
+      A loose tol returns alpha_k up to a factor 1 + tol below the root and
+      costs MWU iterations; eps/20 keeps the iteration count of the bisection
+      at about three Newton evaluations per step.
+    * Backoff: the converged alpha_k may miss Eq. b4b_conv, so alpha_k (1 -
+      eps)^p is taken for the smallest p >= 0 with f >= 1.  Reading: a value
+      below 1 ends the backoff with 0 (alpha < 1 is INFEASIBLE in Alg. 2).
+    ``evaluate_nd(alpha)`` -> (Psi, Phi, Psi', Phi'); ``evaluate(alphas)`` ->
+    (f >= 1 flags, min(z + alpha dz)) as for the other searches.
+    Returns (alpha, info); info.evals counts f evaluations, info.newton the
+    Newton evaluations.
+    """
+    info = SearchInfo()
+    tol = eps / 20.0 if tol is None else tol
+    lb, ub = 0.0, math.inf
+    if alpha0 is None or not alpha0 >= 1.0:
+        b = 0
+        while True:
+            if info.passes >= max_passes:
+                return lb, info
+            cands = [2.0 ** (b + k) for k in range(K)]
+            ok, mins = evaluate(cands)
+            info.evals += K
+            info.passes += 1
+            info.candidates.append(cands)
+            p = _leading(ok)
+            for k in range(p):
+                if mins[k] >= 1.0:
+                    info.early = True
+                    return cands[k], info
+            if p > 0:
+                lb = max(lb, cands[p - 1])
+            if p < K:
+                ub = min(ub, cands[p])
+            if lb > 0.0 and ub < math.inf:
+                break
+            if lb == 0.0:
+                if b == 0:
+                    return 0.0, info
+                b = max(0, b - K)
+            else:
+                b += K
+        alpha = lb
+    else:
+        alpha = float(alpha0)
+    steps = 0
+    while True:
+        psi, phi, dpsi, dphi = evaluate_nd(alpha)
+        info.evals += 1
+        info.passes += 1
+        info.newton += 1
+        info.candidates.append([alpha])
+        steps += 1
+        ok = bang_for_buck_ok(psi, phi)
+        if ok:
+            lb = max(lb, alpha)
+        else:
+            ub = min(ub, alpha)
+        nxt = newton_update(alpha, psi, phi, dpsi, dphi, lb, ub)
+        if abs(nxt - alpha) <= tol * alpha or steps >= max_newton:
+            break
+        alpha = nxt
+    if ok:
+        return alpha, info
+    q = 1.0 - eps
+    p = 1
+    while p <= 64 * K:
+        a = alpha * q ** p
+        if a < 1.0:
+            return 0.0, info
+        okp, _ = evaluate([a])
+        info.evals += 1
+        info.candidates.append([a])
+        if okp[0]:
+            return a, info
+        p += 1
+    return 0.0, info
+
+
 # ----------------------------------------------------------------------------
 # Alg. 2: MWU with step-size search
 # ----------------------------------------------------------------------------
@@ -303,8 +439,8 @@ class MWUResult:
 
 
 def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_passes=64,
-        double_single=True, warm_start=False, x0=None, on_iter=None, stop_rule=0, grad_tol=0.0,
-        ratio_stop=0.0):
+        double_single=True, warm_start=False, x0=None, on_iter=None, stop_rule=0, grad_tol=0.0, max_newton=8,
+        newton_tol=None, ratio_stop=0.0):
     """MWU_STEPSIZE_SEARCH (Alg. 2) on explicit P (m_P x n) and C (m_C x n).
 
     Per iteration: test, g and h, d, max(d) = 0 -> INFEASIBLE, dy = Pd and
@@ -325,7 +461,10 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
     the outer search uses it to stop a probe whose certificate closes the
     bracket.
     ``max_iter`` (5000 in Sec. 6) ends it as MAX_ITER.  ``step`` is "kary" (K
-    candidates per pass), "binary" (Alg. 3) or "standard" (alpha = 1, Alg. 1).
+    candidates per pass), "binary" (Alg. 3), "newton" (Newton's method of
+    Sec. 4.2, warm-started from the previous alpha, at most ``max_newton``
+    Newton evaluations, relative tolerance ``newton_tol``) or "standard"
+    (alpha = 1, Alg. 1).
     ``grad_tol`` is the tolerance of the gradient test (see ``direction``).
     """
     P = sp.csr_matrix(P, dtype=np.float64)
@@ -371,6 +510,12 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
             passes += 1
         elif step == "binary":
             alpha, info = search_binary(ev, eps)
+            evals += info.evals
+            passes += info.passes
+        elif step == "newton":
+            evn = make_newton_evaluator(y, dy, z, dz, eta)
+            alpha, info = search_newton(evn, ev, eps, K=K, alpha0=alpha_prev, max_newton=max_newton,
+                                        max_passes=max_passes, tol=newton_tol)
             evals += info.evals
             passes += info.passes
         else:

@@ -241,6 +241,72 @@ def test_standard_step_admissible_on_feasible_probe():
     assert res.status in (mwu.FEASIBLE, mwu.MAX_ITER)
 
 
+def _root_of_b4b(o, y, dy, z, dz, eta):
+    """alpha* with Phi(alpha*) = Psi(alpha*), by Brent's method on a bracket found by doubling."""
+    from scipy.optimize import brentq
+    F = lambda a: o.Phi(z, dz, a, eta) - o.Psi(y, dy, a, eta)
+    lo = 1.0
+    while F(2 * lo) >= 0:
+        lo *= 2
+    return brentq(F, lo, 2 * lo, xtol=1e-15 * lo, rtol=1e-15)
+
+
+def check_newton(o=mwu, seed=3):
+    """Newton's method of Sec. 4.2: closed-form derivatives, the step, the search."""
+    P, C, x, eta, y, z, d, dy, dz = check_direction_invariants(o, seed)
+    ast = _root_of_b4b(o, y, dy, z, dz, eta)
+    assert ast > 4.0
+    # Psi', Phi' (closed forms) against central differences of Psi, Phi
+    for a in [0.3 * ast, ast, 2.0 * ast]:
+        h = 1e-5 * a
+        assert o.dPsi(y, dy, a, eta) == pytest.approx(
+            (o.Psi(y, dy, a + h, eta) - o.Psi(y, dy, a - h, eta)) / (2 * h), rel=1e-4)
+        assert o.dPhi(z, dz, a, eta) == pytest.approx(
+            (o.Phi(z, dz, a + h, eta) - o.Phi(z, dz, a - h, eta)) / (2 * h), rel=1e-4)
+    evn = o.make_newton_evaluator(y, dy, z, dz, eta)
+    # one step from each side of the root moves toward it (a contraction here)
+    a0 = 0.95 * ast
+    ps, ph, dps, dph = evn(a0)
+    assert ph >= ps
+    a1 = o.newton_update(a0, ps, ph, dps, dph, a0, math.inf)
+    assert a0 < a1 <= ast * (1 + 1e-12) and ast - a1 < 0.5 * (ast - a0)
+    a0 = 1.05 * ast
+    ps, ph, dps, dph = evn(a0)
+    assert ph < ps
+    a1 = o.newton_update(a0, ps, ph, dps, dph, 0.0, a0)
+    assert a1 < a0 and abs(a1 - ast) < 0.75 * (a0 - ast)
+    # the search: warm (near the root) and cold (exponential phase first)
+    ev = o.make_evaluator(y, dy, z, dz, eta)
+    for a0 in [0.95 * ast, 1.05 * ast, None]:
+        a, info = o.search_newton(evn, ev, EPS, K=8, alpha0=a0)
+        ok, _ = ev([a])
+        assert ok[0] and a <= ast * (1 + 1e-12) and a >= 0.99 * ast
+        if a0 is not None:
+            assert info.newton <= 4
+    return ast
+
+
+def test_newton_step_search():
+    for seed in [3, 5, 7]:
+        check_newton(mwu, seed)
+
+
+def test_newton_search_backoff_and_floor():
+    """The (1 - eps)^p backoff on a threshold f, and alpha < 1 -> 0."""
+    # f >= 1 iff alpha <= t, with Psi, Phi, and derivatives that make Newton
+    # converge at once to 1.3 t (g' undefined -> the safeguard doubles, then bisects)
+    for t in [3.0, 50.0, 1000.0]:
+        ev = _threshold_eval(t)
+        evn = lambda a: (1.0, 1.0 if a <= t else 0.5, 0.0, 0.0)
+        a, info = mwu.search_newton(evn, ev, EPS, K=8, alpha0=1.3 * t, max_newton=1)
+        p = math.ceil(math.log(t / (1.3 * t)) / math.log(1 - EPS) - 1e-12)
+        assert a == pytest.approx(1.3 * t * (1 - EPS) ** p, rel=1e-14) and a <= t
+    ev = _threshold_eval(0.5)
+    evn = lambda a: (1.0, 1.0 if a <= 0.5 else 0.5, 0.0, 0.0)
+    a, _ = mwu.search_newton(evn, ev, EPS, K=8, alpha0=4.0, max_newton=1)
+    assert a == 0.0
+
+
 # ----------------------------------------------------------------------------
 # whole solves against exact optima (Theorem 4.1 + the objective embedding)
 # ----------------------------------------------------------------------------
@@ -362,6 +428,8 @@ def test_densest_bruteforce_random():
         assert exact.lp_densest_opt(n, u, v) == pytest.approx(opt)
         r = mwu.solve_densest(n, u, v, EPS)
         _covering_within(r.objective, opt)
+        r = mwu.solve_densest(n, u, v, EPS, step="newton")
+        _covering_within(r.objective, opt)
 
 
 def test_fig1_example():
@@ -382,6 +450,8 @@ def test_matching_closed_forms(name, graph, opt):
     A = lp.incidence(n, u, v)
     assert exact.lp_packing_opt(A, np.ones(u.size)) == pytest.approx(opt)
     r = mwu.solve_packing(A, np.ones(u.size), EPS)
+    _packing_within(r.objective, opt)
+    r = mwu.solve_packing(A, np.ones(u.size), EPS, step="newton")
     _packing_within(r.objective, opt)
 
 
@@ -475,6 +545,14 @@ def _psi_dropped_shift(y, dy, alpha, eta):
     return mwu.smax(y + alpha * dy, eta)
 
 
+def _newton_wrong_sign(alpha, psi, phi, dpsi, dphi, lb, ub):
+    return mwu.newton_update(alpha, psi, -phi + 2 * psi, dpsi, -dphi + 2 * dpsi, lb, ub)
+
+
+def _dphi_unweighted(z, dz, alpha, eta):
+    return float(np.mean(dz))
+
+
 @pytest.mark.parametrize("mutant,check", [
     (_Mutant(smin=_smin_wrong_sign), check_smax_closed_forms),
     (_Mutant(smax=_smax_no_eta), check_smax_closed_forms),
@@ -482,6 +560,8 @@ def _psi_dropped_shift(y, dy, alpha, eta):
     (_Mutant(direction=_direction_no_x), check_direction_invariants),
     (_Mutant(gradients=_gradients_transposed_weight), check_direction_invariants),
     (_Mutant(Psi=_psi_dropped_shift), check_phi_psi),
+    (_Mutant(newton_update=_newton_wrong_sign), check_newton),
+    (_Mutant(dPhi=_dphi_unweighted), check_newton),
 ])
 def test_planted_mistake_is_caught(mutant, check):
     with pytest.raises(AssertionError):
