@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=18)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--step", default="kary", choices=["kary", "newton"],
+                    help="step-size search: K candidates per pass (Alg. 3 generalised) or Newton (Sec. 4.2)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -159,7 +161,8 @@ def run_ours(args):
     N, E = wl.graph.n, wl.graph.m
     kind, P, C, obj = lpspec.from_workload(wl)
     stream = torch.cuda.current_stream()
-    ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, timing=1)
+    step = M.STEP_NEWTON if args.step == "newton" else M.STEP_KARY
+    ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, timing=1, step=step)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -220,7 +223,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"densest-rmat{args.scale}", "lp": "densest subgraph (Charikar dual)",
-                   "vertices": N, "edges": E, "variables": 2 * E, "eps": wl.eps, "K": 8,
+                   "vertices": N, "edges": E, "variables": 2 * E, "eps": wl.eps, "K": 8, "step": args.step,
                    "precision": "f32 vectors, f64 reductions", "l2": "flushed (512 MB write) between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "time_to_approx_s": statistics.mean(step_ms) / 1e3,
@@ -239,7 +242,7 @@ def run_ours(args):
     M.mwu_destroy(ctx)
 
     if rank == 0 and not args.no_fp64:
-        ctx64 = M.mwu_create(kind, P, C, obj, eps=wl.eps, precision=M.PREC_FP64)
+        ctx64 = M.mwu_create(kind, P, C, obj, eps=wl.eps, precision=M.PREC_FP64, step=step)
         flush.zero_()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -264,7 +267,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             kd, Ph, Ch, oh = lpspec.densest_lp(N, edges_h)
-            cx = M.mwu_create(kd, Ph, Ch, oh, eps=wl.eps)
+            cx = M.mwu_create(kd, Ph, Ch, oh, eps=wl.eps, step=step)
             r = M.mwu_solve(cx)
             M.load().mwu_get_vector(cx, M.VEC_X, x_h.data_ptr(), 2 * E, 0)
             M.mwu_destroy(cx)

@@ -89,7 +89,11 @@ typedef struct {
 /* --------------------------------------------------------------- options */
 enum { MWU_STEP_KARY = 0,      /* K candidates per pass (Alg. 3 generalised; K = 1 is Alg. 3) */
        MWU_STEP_BINARY = 1,    /* Alg. 3 as printed: one candidate per pass                  */
-       MWU_STEP_STANDARD = 2 };/* alpha = 1 (Alg. 1)                                         */
+       MWU_STEP_STANDARD = 2,  /* alpha = 1 (Alg. 1)                                         */
+       MWU_STEP_NEWTON = 3 };  /* Newton's method on f(alpha) = 1 (Sec. 4.2): warm start from
+                                  the previous alpha (else the exponential phase), one
+                                  candidate and Psi', Phi' per pass, then the (1-eps)^p
+                                  backoff, K values per pass                                */
 enum { MWU_PREC_F32_R64 = 0,   /* FP32 vectors and per-element math, FP64 reductions         */
        MWU_PREC_FP64 = 1 };    /* everything FP64, one candidate per pass, host-driven search*/
 
@@ -99,7 +103,8 @@ typedef struct {
     double eta_factor;         /* eta = eta_factor ln(m_P+m_C)/eps; default 10 (Alg. 1)      */
     int32_t step;              /* MWU_STEP_*; default KARY                                    */
     int32_t K;                 /* candidates per pass, 1..8; default 8 (FP64 form forces 1)  */
-    int32_t max_passes;        /* candidate passes per iteration; default 6 (F32), 64 (FP64) */
+    int32_t max_passes;        /* candidate passes per iteration; default 6 (F32 K-candidate),
+                                  10 (F32 Newton), 64 (FP64 or K = 1)                       */
     int32_t warm_start;        /* start the exponential phase at floor(log2 alpha_prev)      */
     int32_t double_single;     /* c_d = 1/eta when one side is a single row (Sec. 2.2)       */
     int32_t precision;         /* MWU_PREC_*; default F32_R64                                 */
@@ -122,6 +127,9 @@ typedef struct {
                                   FP32), 0 for FP64 (the exact test of Alg. 2)             */
     void *stream;              /* cudaStream_t; NULL = a non-blocking stream the context
                                   creates and owns                                           */
+    int32_t max_newton;        /* Newton evaluations per step search; default 8              */
+    double newton_tol;         /* Newton has converged once |alpha' - alpha| <= newton_tol
+                                  alpha; <= 0 selects eps/20                                 */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
@@ -230,8 +238,15 @@ int mwu_direction(mwu_ctx *ctx, int64_t *n_positive);
 int mwu_eval_candidates(mwu_ctx *ctx, const double *alphas, int32_t K,
                         double *psi, double *phi, double *zmin);
 
-/* Run the configured step-size search (Alg. 3 / K-candidate form) on the
- * last direction without updating x.  *alpha < 1 means INFEASIBLE. */
+/* Newton quantities of the last direction at one step size (Sec. 4.2):
+ * out[0] = Psi(alpha), out[1] = Phi(alpha), out[2] = Psi'(alpha) =
+ * <dy, e^{eta(y + alpha dy)}>/<1, e^{eta(y + alpha dy)}>, out[3] = Phi'(alpha) =
+ * <dz, e^{-eta(z + alpha dz)}>/<1, e^{-eta(z + alpha dz)}>.  out: host array of
+ * 4 doubles.  Requires mwu_direction; MWU_ERR_NUMERIC on NaN/Inf. */
+int mwu_eval_newton(mwu_ctx *ctx, double alpha, double *out);
+
+/* Run the configured step-size search (Alg. 3 / K-candidate form / Newton)
+ * on the last direction without updating x.  *alpha < 1 means INFEASIBLE. */
 int mwu_search(mwu_ctx *ctx, double *alpha, int64_t *evals);
 
 /* ------------------------------------------------------- the whole solve */

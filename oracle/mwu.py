@@ -346,6 +346,10 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
     * Backoff: the converged alpha_k may miss Eq. b4b_conv, so alpha_k (1 -
       eps)^p is taken for the smallest p >= 0 with f >= 1.  Reading: a value
       below 1 ends the backoff with 0 (alpha < 1 is INFEASIBLE in Alg. 2).
+    * Budget: every Newton evaluation is one pass, the backoff takes K values
+      per pass, and ``max_passes`` bounds the passes of the whole search (a
+      spent budget ends Newton as converged, and the backoff with the largest
+      passing value seen).
     ``evaluate_nd(alpha)`` -> (Psi, Phi, Psi', Phi'); ``evaluate(alphas)`` ->
     (f >= 1 flags, min(z + alpha dz)) as for the other searches.
     Returns (alpha, info); info.evals counts f evaluations, info.newton the
@@ -374,6 +378,8 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
             if p < K:
                 ub = min(ub, cands[p])
             if lb > 0.0 and ub < math.inf:
+                if info.passes >= max_passes:
+                    return lb, info
                 break
             if lb == 0.0:
                 if b == 0:
@@ -398,15 +404,24 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
         else:
             ub = min(ub, alpha)
         nxt = newton_update(alpha, psi, phi, dpsi, dphi, lb, ub)
-        if abs(nxt - alpha) <= tol * alpha or steps >= max_newton:
+        if abs(nxt - alpha) <= tol * alpha or steps >= max_newton or info.passes >= max_passes:
             break
         alpha = nxt
     if ok:
         return alpha, info
+    # backoff alpha (1 - eps)^p, p = 1, 2, ... (the running product), K values
+    # per pass; when the pass budget is spent the largest passing value seen is
+    # returned (0 if there is none or it is below 1)
     q = 1.0 - eps
-    p = 1
-    while p <= 64 * K:
-        a = alpha * q ** p
+    a = alpha
+    p = 0
+    while True:
+        if p % K == 0:
+            if info.passes >= max_passes:
+                return (lb if lb >= 1.0 else 0.0), info
+            info.passes += 1
+        p += 1
+        a = a * q
         if a < 1.0:
             return 0.0, info
         okp, _ = evaluate([a])
@@ -414,8 +429,6 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
         info.candidates.append([a])
         if okp[0]:
             return a, info
-        p += 1
-    return 0.0, info
 
 
 # ----------------------------------------------------------------------------

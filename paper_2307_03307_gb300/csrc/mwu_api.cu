@@ -32,6 +32,7 @@ struct mwu_ctx {
     bool fp64 = false;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t body_stream = nullptr;      // captures the body of the device-side search loop
     Arena ar;
     std::string err;
     int64_t n = 0, mP = 0, mC = 0;
@@ -108,6 +109,8 @@ int mwu_default_options(mwu_options *o) {
     o->use_graph = 1;
     o->check_every = 8;
     o->group = 0;
+    o->max_newton = 8;
+    o->newton_tol = 0.0;   // 0 -> eps / 20
     o->timing = 0;
     o->stop_rule = 0;
     o->grad_tol = -1.0;   // precision default
@@ -364,14 +367,17 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     if (kind < MWU_PACKING || kind > MWU_DENSEST) return fail(nullptr, MWU_ERR_INVALID, "unknown problem kind");
     if (o.precision != MWU_PREC_F32_R64 && o.precision != MWU_PREC_FP64)
         return fail(nullptr, MWU_ERR_INVALID, "unknown precision");
-    if (o.step < MWU_STEP_KARY || o.step > MWU_STEP_STANDARD) return fail(nullptr, MWU_ERR_INVALID, "unknown step mode");
+    if (o.step < MWU_STEP_KARY || o.step > MWU_STEP_NEWTON) return fail(nullptr, MWU_ERR_INVALID, "unknown step mode");
+    if (o.max_newton < 0) return fail(nullptr, MWU_ERR_INVALID, "max_newton must be >= 0");
 
     mwu_ctx *c = new mwu_ctx();
     c->kind = kind;
     c->fp64 = o.precision == MWU_PREC_FP64;
     if (const char *tr = std::getenv("MWU_TRACE")) c->trace = tr[0] == '1';
     if (c->fp64 || o.step == MWU_STEP_BINARY) o.K = 1;
-    if (o.max_passes <= 0) o.max_passes = (c->fp64 || o.K == 1) ? 64 : 6;
+    if (o.max_passes <= 0) o.max_passes = (c->fp64 || o.K == 1) ? 64 : (o.step == MWU_STEP_NEWTON ? 10 : 6);
+    if (o.max_newton == 0) o.max_newton = 8;
+    if (!(o.newton_tol > 0.0)) o.newton_tol = o.eps / 20.0;
     if (o.outer_tol <= 0.0) o.outer_tol = o.eps;
     if (o.max_probes <= 0) o.max_probes = 64;
     if (o.check_every <= 0) o.check_every = 8;
@@ -505,6 +511,7 @@ void mwu_destroy(mwu_ctx *c) {
     if (c->st_host) cudaFreeHost(c->st_host);
     c->ar.free_all();
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->body_stream) cudaStreamDestroy(c->body_stream);
     delete c;
 }
 
@@ -567,7 +574,11 @@ int mwu_set_target(mwu_ctx *c, double target) {
     h.K = o.K;
     h.max_passes = o.max_passes;
     h.warm_start = o.warm_start;
-    h.step_mode = o.step == MWU_STEP_STANDARD ? 2 : (o.step == MWU_STEP_BINARY ? 1 : 0);
+    h.step_mode = o.step == MWU_STEP_STANDARD ? 2 : (o.step == MWU_STEP_BINARY ? 1 : (o.step == MWU_STEP_NEWTON ? 3 : 0));
+    h.max_newton = o.max_newton;
+    h.newton_tol = o.newton_tol;
+    h.kpass = o.K;
+    h.deriv = 0;
     h.stop_rule = o.stop_rule;
     h.grad_tol = o.grad_tol;
     h.ratio_stop = o.stop_rule == 1 ? 1.0 + o.eps : 0.0;
@@ -612,18 +623,63 @@ int mwu_set_x(mwu_ctx *c, const void *x, int32_t x_is_fp64) {
 static int kernels_per_iteration(const mwu_ctx *c) { return 3 + c->opt.max_passes; }
 constexpr int EV_PER_IT = 6;
 
-static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev) {
+// The passes after the first one.  Captured (graph): a conditional WHILE node
+// whose body is one candidate pass; every pass sets the loop condition, so
+// the loop runs exactly the passes the search needs.  Eager: max_passes - 1
+// launches that return at once when the search has ended.
+template <class Prob>
+static cudaError_t enqueue_search_rest(mwu_ctx *c, Prob &p, bool loop, cudaGraphConditionalHandle h) {
+    cudaError_t e;
+    if (!loop) {
+        for (int k = 1; k < c->opt.max_passes; ++k)
+            if ((e = launch_cand(p, 0, c->stream)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess) return e;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return e;
+    if (!c->body_stream && (e = cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamBeginCaptureToGraph(c->body_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return e;
+    cudaError_t e1 = launch_cand(p, 0, c->body_stream, 1, h);
+    cudaGraph_t body = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->body_stream, &body);
+    return e1 != cudaSuccess ? e1 : e2;
+}
+
+static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev, bool loop = false) {
     return with_prob(c, [&](auto &p) -> cudaError_t {
         cudaError_t e;
+        cudaGraphConditionalHandle h = 0;
+        if (loop) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            if ((e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess)
+                return e;
+            if ((e = cudaGraphConditionalHandleCreate(&h, g, 0u, 0u)) != cudaSuccess) return e;
+        }
         if (ev && (e = cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_dir(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_spmv(p, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = launch_cand(p, 0, c->stream)) != cudaSuccess) return e;
+        if ((e = launch_cand(p, 0, c->stream, loop ? 1 : 0, h)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[3], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        for (int k = 1; k < c->opt.max_passes; ++k)
-            if ((e = launch_cand(p, 0, c->stream)) != cudaSuccess) return e;
+        if ((e = enqueue_search_rest(c, p, loop, h)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[4], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_update(p, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[5], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
@@ -647,7 +703,7 @@ static int capture(mwu_ctx *c, int iters, std::vector<cudaEvent_t> &ev, cudaGrap
     TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < iters && e == cudaSuccess; ++k)
-        e = enqueue_iteration(c, c->opt.timing ? &ev[EV_PER_IT * k] : nullptr);
+        e = enqueue_iteration(c, c->opt.timing ? &ev[EV_PER_IT * k] : nullptr, true);
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail_cuda(c, e, "capture iteration"); }
     if (e2 != cudaSuccess) return fail_cuda(c, e2, "end capture");
@@ -736,8 +792,10 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             bool chunk = n_iters - done >= c->opt.check_every;
             int n = chunk ? c->opt.check_every : 1;
             TRY_CUDA(c, cudaGraphLaunch(chunk ? c->gexec_chunk : c->gexec_one, c->stream));
-            c->launches += (int64_t)n * kpi;
             if ((rc = pull_state(c)) != MWU_OK) return rc;
+            // 4 kernels per captured iteration plus the loop bodies (passes after the first)
+            c->launches += (int64_t)n * 4 +
+                           std::max<int64_t>(0, (c->st_host->total_passes - passes0) - (c->st_host->iter - iter0));
             if (c->opt.timing &&
                 (rc = accumulate_timing(c, chunk ? c->ev : c->ev_one, c->st_host->iter - iter0)) != MWU_OK)
                 return rc;
@@ -791,6 +849,8 @@ int mwu_eval_candidates(mwu_ctx *c, const double *alphas, int32_t K, double *psi
     DevState saved = *c->st_host;
     DevState &h = *c->st_host;
     h.K = K;
+    h.kpass = K;
+    h.deriv = 0;
     for (int k = 0; k < K; ++k) h.alpha[k] = alphas[k];
     if ((rc = push_state(c)) != MWU_OK) return rc;
     TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, c->stream); }));
@@ -803,6 +863,31 @@ int mwu_eval_candidates(mwu_ctx *c, const double *alphas, int32_t K, double *psi
     int bad = h.status == ST_NUMERIC;
     // restore the search state of the direction
     saved.psi[0] = h.psi[0];
+    *c->st_host = saved;
+    if ((rc = push_state(c)) != MWU_OK) return rc;
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    return bad ? fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a candidate") : MWU_OK;
+}
+
+int mwu_eval_newton(mwu_ctx *c, double alpha, double *out) {
+    if (!c || !out || !(alpha >= 0.0)) return MWU_ERR_INVALID;
+    if (!c->have_direction) return fail(c, MWU_ERR_STATE, "call mwu_direction first");
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    DevState saved = *c->st_host;
+    DevState &h = *c->st_host;
+    h.K = 1;
+    h.kpass = 1;
+    h.deriv = 1;
+    h.alpha[0] = alpha;
+    if ((rc = push_state(c)) != MWU_OK) return rc;
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, c->stream); }));
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    out[0] = h.psi[0];
+    out[1] = h.phi[0];
+    out[2] = h.dpsi;
+    out[3] = h.dphi;
+    int bad = h.status == ST_NUMERIC;
     *c->st_host = saved;
     if ((rc = push_state(c)) != MWU_OK) return rc;
     TRY_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -19,7 +19,7 @@ namespace mwu {
 
 constexpr int KMAX = 8;           // candidates per pass (compile-time bound)
 constexpr int BLOCK = 256;        // threads per block of the sweep kernels
-constexpr int REC = 64;           // doubles per per-block partial record
+constexpr int REC = 72;           // doubles per per-block partial record
 constexpr int GRP = 16;           // blocks per group of the two-level completion
 constexpr int GRP_MAX = 128;      // groups (grids up to 2048 blocks)
 
@@ -97,14 +97,14 @@ enum : int32_t { RS_NONE = 0, RS_COVERED = 1, RS_PACKING = 2, RS_DZERO = 3, RS_A
                  RS_RATIO = 6 };
 
 // Search phases.
-enum : int32_t { PH_EXP = 0, PH_REFINE = 1, PH_DONE = 2 };
+enum : int32_t { PH_EXP = 0, PH_REFINE = 1, PH_DONE = 2, PH_NEWTON = 3, PH_BACKOFF = 4 };
 
 struct DevState {
     // problem scalars
     double eta, eps, c_d, target;
     double scale[2];            // side factors: 1/M (objective row), 1/D (O), else 1
     int32_t max_iter, K, max_passes, warm_start;
-    int32_t step_mode;          // 0 kary, 1 binary (K=1 semantics), 2 standard
+    int32_t step_mode;          // 0 kary, 1 binary (K=1 semantics), 2 standard, 3 newton
     int32_t stop_rule;          // 1: stop FEASIBLE once ymax <= (1+eps) zmin
     double grad_tol;            // gradient test: d_i > 0 iff g_i < (1 - grad_tol) h_i
     double ratio_stop;          // > 0: stop FEASIBLE once ymax <= ratio_stop * zmin
@@ -116,6 +116,13 @@ struct DevState {
     long long n_pos;
     // search
     int32_t phase, b, passes, early;
+    int32_t kpass;              // candidates of the next pass (1 for a Newton pass)
+    int32_t deriv;              // external pass: also return Psi'(alpha_0), Phi'(alpha_0)
+    int32_t max_newton, newton_steps;
+    double newton_tol;
+    double bo_cur;              // backoff: last value alpha (1 - eps)^p handed out
+    double dpsi, dphi;          // Psi'(alpha_0), Phi'(alpha_0) of the last Newton pass
+    int32_t loop_guard;         // passes run by the device-side search loop of this iteration
     double lb, ub;
     double alpha[KMAX];
     double psi[KMAX], phi[KMAX], zmink[KMAX];
@@ -158,7 +165,11 @@ template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, 
 template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s);             // a1-a3 at a new x
 template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s);      // a4-a5 (+ fused x update)
 template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s);                  // a6: dy = Pd, dz = Cd
-template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s);    // a7: one candidate pass
+// cond_on: the kernel sets `cond` (the while-loop handle of a captured
+// iteration graph) to 1 while the step search must continue, else 0
+template <class T>
+cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s, int cond_on = 0,
+                        cudaGraphConditionalHandle cond = 0);    // a7: one candidate pass
 template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s);                // a8
 template <class T> cudaError_t launch_flush(const Problem<T> &p, cudaStream_t s);                 // pending x update
 template <class T> cudaError_t launch_search_begin(const Problem<T> &p, cudaStream_t s);

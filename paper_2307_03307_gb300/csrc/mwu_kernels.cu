@@ -390,10 +390,18 @@ __device__ void dir_finish(DevState *st, double np_t, double dd0, double dd1) {
     st->passes = 0;
     st->early = 0;
     st->alpha_acc = 0.0;
+    st->kpass = st->K;
+    st->newton_steps = 0;
+    st->loop_guard = 0;
     int b0 = 0;
-    if (st->warm_start && st->alpha_prev >= 1.0) b0 = (int)floor(log2(st->alpha_prev));
+    if (st->warm_start && st->alpha_prev >= 1.0 && st->step_mode != 3) b0 = (int)floor(log2(st->alpha_prev));
     st->b = b0;
     for (int k = 0; k < st->K; ++k) st->alpha[k] = ldexp(1.0, b0 + k);
+    if (st->step_mode == 3 && st->alpha_prev >= 1.0) {   // Newton, warm start (Sec. 4.2)
+        st->phase = PH_NEWTON;
+        st->kpass = 1;
+        st->alpha[0] = st->alpha_prev;
+    }
     if (st->step_mode == 2) {   // standard step alpha = 1 (Alg. 1)
         st->phase = PH_DONE;
         st->alpha_acc = 1.0;
@@ -600,6 +608,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
 template <class T> struct CandAcc {
     T mx[KMAX], R[KMAX], Tt[KMAX], zm[KMAX];
     T mxmin;   // min_k mx[k] (covering side), maintained on rescale
+    T D;       // Newton pass: sum dv e^{x_0 - mx_0}, scaled like R[0]
 };
 
 template <class T>
@@ -610,12 +619,14 @@ __device__ __forceinline__ void cand_init(CandAcc<T> &c, int sgn) {
         c.R[k] = T(0); c.Tt[k] = T(0); c.zm[k] = t_inf<T>();
     }
     c.mxmin = sgn > 0 ? T(0) : -t_inf<T>();
+    c.D = T(0);
 }
 
 // Candidate schedule of one pass (identical for every row).
 //   mode 0: alpha_{k+1} = 2 alpha_k          (exponential phase of the search)
 //   mode 1: alpha_{k+1} = alpha_k + delta    (refinement on [lb, ub])
-//   mode 2: arbitrary alphas                 (mwu_eval_candidates)
+//   mode 2: arbitrary alphas                 (mwu_eval_candidates, the backoff)
+//   mode 3: one alpha, with the sums of Psi'(alpha), Phi'(alpha) (Newton)
 // ca[k] = alpha_k eta, al[k] = alpha_k, cd = delta eta, all in T.
 template <class T> struct CandSched {
     int K, mode;
@@ -688,12 +699,14 @@ __device__ __forceinline__ void cand_push_m(CandAcc<T> &c, const T *ca, const T 
                     T f = fast_exp(c.mx[k] - x);
                     c.R[k] *= f;
                     if (SGN > 0) c.Tt[k] *= f;
+                    if (MODE == 3 && k == 0) c.D *= f;
                     c.mx[k] = x;
                     moved = true;
                 }
             }
             const T t = fast_exp(x - c.mx[k]);
             c.R[k] += t;
+            if (MODE == 3 && k == 0) c.D += dv * t;
             if (SGN > 0) c.Tt[k] += t * u;
             else {
                 c.Tt[k] += A * u;
@@ -715,10 +728,12 @@ __device__ __forceinline__ void cand_push(CandAcc<T> &c, const CandSched<T> &sc,
     if (sgn > 0) {
         if (sc.mode == 0) cand_push_m<T, 0, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
         else if (sc.mode == 1) cand_push_m<T, 1, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
+        else if (sc.mode == 3) cand_push_m<T, 3, 1, 1>(c, sc.ca, sc.al, sc.cd, 1, v, dv, eta, s);
         else cand_push_m<T, 2, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
     } else {
         if (sc.mode == 0) cand_push_m<T, 0, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
         else if (sc.mode == 1) cand_push_m<T, 1, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
+        else if (sc.mode == 3) cand_push_m<T, 3, -1, 1>(c, sc.ca, sc.al, sc.cd, 1, v, dv, eta, s);
         else cand_push_m<T, 2, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
     }
 }
@@ -745,11 +760,94 @@ __device__ __forceinline__ void cand_merge1(U &mx, U &R, U &Tt, U &zm, U bmx, U 
     }
 }
 
+// cand_merge1 for candidate 0, whose Newton sum D scales like R
+template <class T, class U>
+__device__ __forceinline__ void cand_merge1d(U &mx, U &R, U &Tt, U &zm, U &D, U bmx, U bR, U bT, U bzm, U bD,
+                                             int sgn) {
+    if (bR == U(0)) { cand_merge1<T, U>(mx, R, Tt, zm, bmx, bR, bT, bzm, sgn); return; }
+    if (R == U(0)) { D = bD; cand_merge1<T, U>(mx, R, Tt, zm, bmx, bR, bT, bzm, sgn); return; }
+    const U m = fmax(mx, bmx);
+    D = D * (U)t_exp((T)(mx - m)) + bD * (U)t_exp((T)(bmx - m));
+    cand_merge1<T, U>(mx, R, Tt, zm, bmx, bR, bT, bzm, sgn);
+}
+
 // The search step after a pass (runs on one thread).  Mirrors the K-candidate
 // search of the oracle: prefix of passing candidates, early exit on
 // min(z + alpha dz) >= 1 in the exponential phase, refinement on [lb, ub].
+__device__ void search_finish(DevState *st, double acc) {
+    st->phase = PH_DONE;
+    st->last_passes = st->passes;
+    if (acc >= 1.0) st->alpha_acc = acc;
+    else {
+        st->alpha_acc = 0.0;
+        st->status = ST_INFEASIBLE;
+        st->reason = RS_ALPHA;
+    }
+}
+
+// First backoff pass after Newton converged at alpha (f(alpha) < 1): the
+// values alpha (1 - eps)^p, p = 1..K, as a running product.
+__device__ void backoff_next(DevState *st) {
+    const double q = 1.0 - st->eps;
+    st->kpass = st->K;
+    for (int k = 0; k < st->K; ++k) {
+        st->bo_cur = st->bo_cur * q;
+        st->alpha[k] = st->bo_cur;
+    }
+}
+
+__device__ void newton_start_backoff(DevState *st, double alpha) {
+    if (st->passes >= st->max_passes) { search_finish(st, st->lb >= 1.0 ? st->lb : 0.0); return; }
+    st->phase = PH_BACKOFF;
+    st->bo_cur = alpha;
+    backoff_next(st);
+}
+
+// After a Newton pass at alpha = alpha[0] (Sec. 4.2): Newton's update of
+// g = f - 1 with the bracket safeguard, the convergence test, and the start
+// of the (1 - eps)^p backoff when the converged alpha misses Eq. b4b_conv.
+// The same steps as the oracle's search_newton.
+__device__ void newton_decide(DevState *st, double psi, double phi, double dpsi, double dphi) {
+    st->passes += 1;
+    st->evals += 1;
+    st->total_passes += 1;
+    st->newton_steps += 1;
+    const double a = st->alpha[0];
+    const bool ok = phi >= psi;
+    if (ok) st->lb = fmax(st->lb, a);
+    else st->ub = fmin(st->ub, a);
+    const double lb = st->lb, ub = st->ub;
+    const double den = psi * dphi - phi * dpsi;
+    double nxt = (double)NAN;
+    if (psi > 0.0 && den < 0.0 && isfinite(den)) nxt = a - (phi - psi) * psi / den;
+    if (!(isfinite(nxt) && lb < nxt && nxt < ub)) nxt = isfinite(ub) ? 0.5 * (lb + ub) : 2.0 * a;
+    if (fabs(nxt - a) <= st->newton_tol * a || st->newton_steps >= st->max_newton || st->passes >= st->max_passes) {
+        if (ok) search_finish(st, a);
+        else newton_start_backoff(st, a);
+        return;
+    }
+    st->alpha[0] = nxt;
+    st->kpass = 1;
+}
+
+// After a backoff pass: the first passing value in order; a value below 1
+// ends the search with 0 (alpha < 1 is INFEASIBLE); a spent budget returns
+// the largest passing value seen.
+__device__ void backoff_decide(DevState *st, const int *ok) {
+    const int K = st->kpass;
+    st->passes += 1;
+    st->evals += K;
+    st->total_passes += 1;
+    for (int k = 0; k < K; ++k) {
+        if (st->alpha[k] < 1.0) { search_finish(st, 0.0); return; }
+        if (ok[k]) { search_finish(st, st->alpha[k]); return; }
+    }
+    if (st->passes >= st->max_passes) { search_finish(st, st->lb >= 1.0 ? st->lb : 0.0); return; }
+    backoff_next(st);
+}
+
 __device__ void search_decide(DevState *st, const int *ok, const double *zmin_k) {
-    int K = st->K;
+    int K = st->kpass;
     int p = 0;
     while (p < K && ok[p]) ++p;
     st->passes += 1;
@@ -767,8 +865,19 @@ __device__ void search_decide(DevState *st, const int *ok, const double *zmin_k)
         if (!done) {
             if (p > 0) st->lb = fmax(st->lb, al[p - 1]);
             if (p < K) st->ub = fmin(st->ub, al[p]);
-            if (st->lb > 0.0 && st->ub < (double)INFINITY) st->phase = PH_REFINE;
-            else if (st->lb == 0.0) {
+            if (st->lb > 0.0 && st->ub < (double)INFINITY) {
+                if (st->step_mode == 3) {   // Newton from the bracket's lower end
+                    if (st->passes >= st->max_passes) {
+                        search_finish(st, st->lb);
+                        return;
+                    }
+                    st->phase = PH_NEWTON;
+                    st->kpass = 1;
+                    al[0] = st->lb;
+                    return;
+                }
+                st->phase = PH_REFINE;
+            } else if (st->lb == 0.0) {
                 if (st->b == 0) { acc = 0.0; done = true; }
                 else st->b = max(0, st->b - K);
             } else st->b += K;
@@ -777,14 +886,7 @@ __device__ void search_decide(DevState *st, const int *ok, const double *zmin_k)
     if (!done && st->phase == PH_REFINE && (st->ub - st->lb) <= st->eps * st->lb) { acc = st->lb; done = true; }
     if (!done && st->passes >= st->max_passes) { acc = st->lb; done = true; }
     if (done) {
-        st->phase = PH_DONE;
-        st->last_passes = st->passes;
-        if (acc >= 1.0) st->alpha_acc = acc;
-        else {
-            st->alpha_acc = 0.0;
-            st->status = ST_INFEASIBLE;
-            st->reason = RS_ALPHA;
-        }
+        search_finish(st, acc);
         return;
     }
     // next candidate set
@@ -983,13 +1085,18 @@ __global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb
 // a7: K step candidates per constraint row over the stored (v, dv).
 // external = 1: evaluate st->alpha[0..K) and store psi/phi/zmin, no decision.
 template <class T>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int external) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int external, int cond_on,
+                                                                  cudaGraphConditionalHandle cond) {
     __shared__ CandSched<T> s_sc;
     DevState *st = p.st;
-    if (st->status != ST_RUNNING) return;
     const bool searching = external || st->phase != PH_DONE;
-    if (!searching) return;
-    const int K = st->K;
+    if (st->status != ST_RUNNING || !searching) {
+        // nothing to search: end the device-side loop (one setter per launch)
+        if (cond_on && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    const int K = external ? st->K : st->kpass;
+    const bool newton = external ? (st->deriv != 0 && K == 1) : st->phase == PH_NEWTON;
     int s = (blockIdx.x < gP) ? 0 : 1;
     int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
     int nbs = s == 0 ? gP : gridDim.x - gP;
@@ -998,7 +1105,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
     const T sh = (T)st->s[s];
     if (threadIdx.x == 0) {
         s_sc.K = K;
-        s_sc.mode = external ? 2 : (st->phase == PH_EXP ? 0 : 1);
+        s_sc.mode = newton ? 3 : external ? 2 : (st->phase == PH_EXP ? 0 : st->phase == PH_REFINE ? 1 : 2);
         s_sc.cd = (T)((st->ub - st->lb) / (K + 1) * st->eta);
     }
     if (threadIdx.x < KMAX) {
@@ -1017,7 +1124,10 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
         // a pure stream over the stored (v, dv), four rows per thread, with the
         // schedule in registers and the loop specialised per (mode, side)
         const int md = sc.mode;
-        if (sc.K == KMAX) {
+        if (md == 3) {
+            if (sd.sign > 0) cand_stream<T, 3, 1, 1>(acc, sc, sd, m, tid, nthr, eta, sh);
+            else cand_stream<T, 3, -1, 1>(acc, sc, sd, m, tid, nthr, eta, sh);
+        } else if (sc.K == KMAX) {
             if (sd.sign > 0) {
                 if (md == 0) cand_stream<T, 0, 1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
                 else if (md == 1) cand_stream<T, 1, 1, KMAX>(acc, sc, sd, m, tid, nthr, eta, sh);
@@ -1032,29 +1142,41 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
             else cand_stream<T, 2, -1, 0>(acc, sc, sd, m, tid, nthr, eta, sh);
         }
     }
-    // block merge: warp shuffles in T, then warps in FP64
-    __shared__ double wm[BLOCK / 32][KMAX][4];
+    // block merge in T: warp shuffles, then one 8-lane shuffle tree per
+    // candidate over the block's 8 warps (only the pass's K candidates); the
+    // cross-block levels below run in FP64
+    static_assert(BLOCK / 32 == 8 && KMAX == 8, "block merge layout: 8 warps x 8 candidates");
+    __shared__ T wm[BLOCK / 32][KMAX][5];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        T mx = acc.mx[k], R = acc.R[k], Tt = acc.Tt[k], zm = acc.zm[k];
-        for (int off = 16; off > 0; off >>= 1) {
-            T omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off);
-            cand_merge1<T, T>(mx, R, Tt, zm, omx, oR, oT, oz, sd.sign);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            wm[threadIdx.x >> 5][k][0] = mx; wm[threadIdx.x >> 5][k][1] = R;
-            wm[threadIdx.x >> 5][k][2] = Tt; wm[threadIdx.x >> 5][k][3] = zm;
+        if (k < K) {
+            T mx = acc.mx[k], R = acc.R[k], Tt = acc.Tt[k], zm = acc.zm[k], D = k == 0 ? acc.D : T(0);
+            for (int off = 16; off > 0; off >>= 1) {
+                T omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off);
+                T oD = shfl_x(D, off);
+                cand_merge1d<T, T>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sd.sign);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                T *o = wm[threadIdx.x >> 5][k];
+                o[0] = mx; o[1] = R; o[2] = Tt; o[3] = zm; o[4] = D;
+            }
         }
     }
     __syncthreads();
-    if (threadIdx.x < KMAX) {
-        int k = threadIdx.x;
-        double mx = sd.sign > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            cand_merge1<T, double>(mx, R, Tt, zm, wm[w][k][0], wm[w][k][1], wm[w][k][2], wm[w][k][3], sd.sign);
-        double *rec = p.part_row + (size_t)blockIdx.x * REC;
-        rec[k * 4 + 0] = mx; rec[k * 4 + 1] = R; rec[k * 4 + 2] = Tt; rec[k * 4 + 3] = zm;
-        rec[32] = s;
+    if (threadIdx.x < 64) {
+        const int k = threadIdx.x >> 3, w = threadIdx.x & 7;
+        const T *o = wm[w][k < K ? k : 0];
+        T mx = o[0], R = o[1], Tt = o[2], zm = o[3], D = o[4];
+        for (int off = 4; off > 0; off >>= 1) {
+            T omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off);
+            T oD = shfl_x(D, off);
+            cand_merge1d<T, T>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sd.sign);
+        }
+        if (w == 0 && k < K) {
+            double *rec = p.part_row + (size_t)blockIdx.x * REC;
+            rec[k * 4 + 0] = mx; rec[k * 4 + 1] = R; rec[k * 4 + 2] = Tt; rec[k * 4 + 3] = zm;
+            if (k == 0) { rec[32] = s; rec[33] = D; }
+        }
     }
     // two-level completion: the last block of each group of GRP blocks merges the
     // group's records (one per lane), the last group merges the group records, so
@@ -1075,20 +1197,23 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
         const int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
         const int ss = q / KMAX, k = q % KMAX;
         const int sg = p.side[ss].sign;
-        double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
+        double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
         const int b = grp * GRP + ln;
-        if (ln < gsz && (b < gP ? 0 : 1) == ss) {
-            const double *rec = p.part_row + (size_t)b * REC + k * 4;
-            cand_merge1<T, double>(mx, R, Tt, zm, rec[0], rec[1], rec[2], rec[3], sg);
+        if (k < K && ln < gsz && (b < gP ? 0 : 1) == ss) {
+            const double *rb = p.part_row + (size_t)b * REC;
+            const double *rec = rb + k * 4;
+            cand_merge1d<T, double>(mx, R, Tt, zm, D, rec[0], rec[1], rec[2], rec[3], k == 0 ? rb[33] : 0.0, sg);
         }
         for (int off = 8; off > 0; off >>= 1) {
             double omx = __shfl_xor_sync(0xffffffffu, mx, off), oR = __shfl_xor_sync(0xffffffffu, R, off);
             double oT = __shfl_xor_sync(0xffffffffu, Tt, off), oz = __shfl_xor_sync(0xffffffffu, zm, off);
-            cand_merge1<T, double>(mx, R, Tt, zm, omx, oR, oT, oz, sg);
+            double oD = __shfl_xor_sync(0xffffffffu, D, off);
+            cand_merge1d<T, double>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sg);
         }
         if (ln == 0) {
             double *g = grec + (size_t)grp * REC + ss * 32 + k * 4;
             g[0] = mx; g[1] = R; g[2] = Tt; g[3] = zm;
+            if (k == 0) grec[(size_t)grp * REC + 64 + ss] = D;
         }
     }
     if (threadIdx.x == 0) st->grp_counter[0][grp] = 0;
@@ -1104,15 +1229,17 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
             const int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
             const int ss = q / KMAX, k = q % KMAX;
             const int sg = p.side[ss].sign;
-            double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY;
-            for (int gg = ln; gg < ngrp; gg += 16) {
+            double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
+            for (int gg = ln; gg < ngrp && k < K; gg += 16) {
                 const double *rec = grec + (size_t)gg * REC + ss * 32 + k * 4;
-                cand_merge1<T, double>(mx, R, Tt, zm, rec[0], rec[1], rec[2], rec[3], sg);
+                const double bD = k == 0 ? grec[(size_t)gg * REC + 64 + ss] : 0.0;
+                cand_merge1d<T, double>(mx, R, Tt, zm, D, rec[0], rec[1], rec[2], rec[3], bD, sg);
             }
             for (int off = 8; off > 0; off >>= 1) {
                 double omx = __shfl_xor_sync(0xffffffffu, mx, off), oR = __shfl_xor_sync(0xffffffffu, R, off);
                 double oT = __shfl_xor_sync(0xffffffffu, Tt, off), oz = __shfl_xor_sync(0xffffffffu, zm, off);
-                cand_merge1<T, double>(mx, R, Tt, zm, omx, oR, oT, oz, sg);
+                double oD = __shfl_xor_sync(0xffffffffu, D, off);
+                cand_merge1d<T, double>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sg);
             }
             if (ln == 0) {
                 // Psi_k (packing side) or Phi_k (covering side) from the merged sums.  The
@@ -1137,6 +1264,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
                                       : -(mx + (double)t_log((T)R) - lS0) / eta_d;
                 }
                 fin[ss][k][0] = val;
+                // Newton: Psi' = D/R (packing side), Phi' = D/R (covering side); both
+                // sums carry the same shift, so the ratio needs no rescale
+                fin[ss][k][1] = (q.rv.kind == RK_DENSE1) ? st->dense_dv[ss] : (R > 0.0 ? D / R : 0.0);
                 fin[ss][k][3] = (q.rv.kind == RK_DENSE1) ? st->dense_v[ss] + a * st->dense_dv[ss] : zm;
             }
         }
@@ -1155,11 +1285,30 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
                 ok[k] = val[1] >= val[0];
                 st->okk[k] = ok[k];
             }
+            if (newton) {
+                st->dpsi = fin[0][0][1];
+                st->dphi = fin[1][0][1];
+                if (!isfinite(st->dpsi) || !isfinite(st->dphi)) bad = true;
+            }
             if (bad) {
                 st->status = ST_NUMERIC;
                 st->numeric_bad = 2;
             } else if (!external) {
-                search_decide(st, ok, zmk);
+                if (newton) newton_decide(st, fin[0][0][0], fin[1][0][0], st->dpsi, st->dphi);
+                else if (st->phase == PH_BACKOFF) backoff_decide(st, ok);
+                else search_decide(st, ok, zmk);
+            }
+            if (cond_on) {
+                // continue the loop while the search runs; the decide rules end every
+                // search within max_passes passes, and the guard ends the loop (with an
+                // error status) should that ever fail
+                unsigned v = (st->status == ST_RUNNING && st->phase != PH_DONE) ? 1u : 0u;
+                if (v && ++st->loop_guard > st->max_passes + 2) {
+                    st->status = ST_NUMERIC;
+                    st->numeric_bad = 3;
+                    v = 0u;
+                }
+                cudaGraphSetConditional(cond, v);
             }
             st->counter[2] = 0;
         }
@@ -1408,10 +1557,12 @@ template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s) {
+template <class T>
+cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s, int cond_on,
+                        cudaGraphConditionalHandle cond) {
     int gP, gC;
     split_rows(p, &gP, &gC, false);
-    k_cand<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, external);
+    k_cand<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, external, cond_on, cond);
     return cudaGetLastError();
 }
 
@@ -1497,7 +1648,7 @@ template <class T> int spmv_blocks_per_sm() {
     template cudaError_t launch_rows_eval<T>(const Problem<T> &, cudaStream_t);                                \
     template cudaError_t launch_dir<T>(const Problem<T> &, int, cudaStream_t);                                 \
     template cudaError_t launch_spmv<T>(const Problem<T> &, cudaStream_t);                                     \
-    template cudaError_t launch_cand<T>(const Problem<T> &, int, cudaStream_t);                                \
+    template cudaError_t launch_cand<T>(const Problem<T> &, int, cudaStream_t, int, cudaGraphConditionalHandle); \
     template cudaError_t launch_update<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_flush<T>(const Problem<T> &, cudaStream_t);                                    \
     template cudaError_t launch_search_begin<T>(const Problem<T> &, cudaStream_t);                             \

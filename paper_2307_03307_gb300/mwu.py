@@ -22,7 +22,7 @@ INFEASIBLE, MAX_ITER, RUNNING = 1, 2, 3
 ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6
 PACKING, COVERING, MIXED, DENSEST = 0, 1, 2, 3
 MAT_CSR, MAT_INCIDENCE, MAT_INCIDENCE_T, MAT_PAIR, MAT_INTERWEAVE, MAT_NONE = 0, 1, 2, 3, 4, 5
-STEP_KARY, STEP_BINARY, STEP_STANDARD = 0, 1, 2
+STEP_KARY, STEP_BINARY, STEP_STANDARD, STEP_NEWTON = 0, 1, 2, 3
 PREC_F32_R64, PREC_FP64 = 0, 1
 VEC_X, VEC_Y, VEC_Z, VEC_D, VEC_DY, VEC_DZ, VEC_G, VEC_H = range(8)
 REASONS = {0: "none", 1: "covered", 2: "packing", 3: "d=0", 4: "alpha<1", 5: "max_iter", 6: "ratio"}
@@ -41,7 +41,8 @@ class mwu_options(C.Structure):
                 ("warm_start", C.c_int32), ("double_single", C.c_int32), ("precision", C.c_int32),
                 ("outer_tol", C.c_double), ("max_probes", C.c_int32), ("use_graph", C.c_int32),
                 ("check_every", C.c_int32), ("group", C.c_int32), ("timing", C.c_int32),
-                ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p)]
+                ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p),
+                ("max_newton", C.c_int32), ("newton_tol", C.c_double)]
 
 
 class mwu_iter_stats(C.Structure):
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH):
         "mwu_iterate": (C.c_int, [V, I32, P(mwu_iter_stats)]),
         "mwu_direction": (C.c_int, [V, P(I64)]),
         "mwu_eval_candidates": (C.c_int, [V, P(D), I32, P(D), P(D), P(D)]),
+        "mwu_eval_newton": (C.c_int, [V, D, P(D)]),
         "mwu_search": (C.c_int, [V, P(D), P(I64)]),
         "mwu_solve": (C.c_int, [V, D, D, P(mwu_result)]),
         "mwu_get_vector": (C.c_int, [V, I32, V, I64, I32]),
@@ -123,7 +125,8 @@ def load(path: str = LIB_PATH):
 def exported_symbols():
     """Names of the C entry points this binding expects the library to export."""
     return ["mwu_default_options", "mwu_create", "mwu_destroy", "mwu_last_error", "mwu_set_target",
-            "mwu_set_x", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_search", "mwu_solve",
+            "mwu_set_x", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_eval_newton", "mwu_search",
+            "mwu_solve",
             "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_potential", "mwu_candidates_static",
             "mwu_create_batch", "mwu_solve_batch"]
 
@@ -246,6 +249,13 @@ def mwu_eval_candidates(ctx, alphas):
     psi, phi, zm = (C.c_double * K)(), (C.c_double * K)(), (C.c_double * K)()
     _check(ctx, load().mwu_eval_candidates(ctx, a, K, psi, phi, zm))
     return list(psi), list(phi), list(zm)
+
+
+def mwu_eval_newton(ctx, alpha):
+    """(Psi, Phi, Psi', Phi') of the last direction at one step size."""
+    out = (C.c_double * 4)()
+    _check(ctx, load().mwu_eval_newton(ctx, float(alpha), out))
+    return tuple(out)
 
 
 def mwu_search(ctx):

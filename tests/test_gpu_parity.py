@@ -63,6 +63,111 @@ def vec(M, ctx, which, n):
     return M.mwu_get_vector(ctx, which, n, fp64=True).numpy()
 
 
+GRAD_TOL = {"f32": 2.0 ** -16, "fp64": 0.0}
+
+
+class Chain:
+    """The oracle's own chain of one MWU iteration from a host-seeded x.
+
+    Nothing here comes from the GPU: x is drawn on the host from the oracle's
+    x_init, rounded to the form's precision and handed to both sides; every
+    later oracle quantity follows from it by the oracle's functions alone.
+    """
+
+    def __init__(self, wl, prec, T, seed=7):
+        P, C, _ = H.oracle_matrices(wl, T)
+        self.P, self.C = P, C
+        self.mP, self.mC = P.shape[0], C.shape[0]
+        self.n = H.n_vars(wl)
+        self.eta = om.eta_of(self.mP + self.mC, wl.eps)
+        self.c_d = om.step_coefficient(self.mP, self.mC, self.eta)
+        rng = np.random.default_rng(seed)
+        dt = np.float32 if prec == "f32" else np.float64
+        x = om.x_init(P, wl.eps) * rng.uniform(1.0, 40.0, self.n)
+        # keep the probe running: max(Px) and min(Cx) below 1
+        f = 0.8 / max(float((P @ x).max()), float((C @ x).min()))
+        self.x = (x * min(1.0, f)).astype(dt)
+        xo = self.x.astype(np.float64)
+        self.xo = xo
+        self.y, self.z = P @ xo, C @ xo
+        self.g, self.h = om.gradients(P, C, self.y, self.z, self.eta)
+        self.d = om.direction(self.g, self.h, xo, self.c_d, GRAD_TOL[prec])
+        self.dy, self.dz = P @ self.d, C @ self.d
+        self.evaluate = om.make_evaluator(self.y, self.dy, self.z, self.dz, self.eta)
+        self.evaluate_nd = om.make_newton_evaluator(self.y, self.dy, self.z, self.dz, self.eta)
+
+
+def _softmax_l1(e_logit, eta):
+    """Bound on ||softmax(eta u') - softmax(eta u)||_1 when ||u' - u||_inf <= e_logit."""
+    return math.expm1(2.0 * eta * e_logit)
+
+
+def run_direction_checks(M, ctx, wl, prec, ch):
+    """a1-a6 on the GPU from the chain's x against the chain, with error bounds
+    propagated from the measured error of each step's inputs."""
+    rel = H.REL[prec]
+    eta = ch.eta
+    M.mwu_set_x(ctx, torch.from_numpy(ch.x).cuda())
+    # a1: y = Px, z = Cx
+    y = vec(M, ctx, M.VEC_Y, ch.mP)
+    z = vec(M, ctx, M.VEC_Z, ch.mC)
+    H.assert_rel(y, ch.y, rel, what="y=Px")
+    H.assert_rel(z, ch.z, rel, what="z=Cx")
+    ey = float(np.abs(y - ch.y).max())
+    ez = float(np.abs(z - ch.z).max())
+    # a2, a3: shifts and shifted sums; each weight e^{eta(v - s)} moves by a
+    # factor of at most e^{2 eta e_v} (v and its shift both move by <= e_v)
+    sc = M.mwu_get_scalars(ctx)
+    s_p, S_p = om.lse_shift_sum(ch.y, eta, +1)
+    s_c, S_c = om.lse_shift_sum(ch.z, eta, -1)
+    assert abs(sc["s_p"] - s_p) <= ey and abs(sc["s_c"] - s_c) <= ez
+    tw_p = rel + 1.1 * math.expm1(2 * eta * ey)
+    tw_c = rel + 1.1 * math.expm1(2 * eta * ez)
+    H.assert_rel([sc["S_p"]], [S_p], tw_p, what="S_p")
+    H.assert_rel([sc["S_c"]], [S_c], tw_c, what="S_c")
+    # a4: normalised weights move by twice that; g, h are positive sums of them
+    rc, npos = M.mwu_direction(ctx)
+    assert rc == M.OK
+    g = vec(M, ctx, M.VEC_G, ch.n)
+    h = vec(M, ctx, M.VEC_H, ch.n)
+    d = vec(M, ctx, M.VEC_D, ch.n)
+    tg, th = rel + 2.2 * math.expm1(2 * eta * ey), rel + 2.2 * math.expm1(2 * eta * ez)
+    H.assert_rel(g, ch.g, tg, what="g=P^T w_p", floor=H.UNDERFLOW[prec])
+    H.assert_rel(h, ch.h, th, what="h=C^T w_c", floor=H.UNDERFLOW[prec])
+    # a5: d_i = c_d max(0, 1 - g_i/h_i) x_i; g/h moves by <= (tg + th) r, and a
+    # gradient test decided differently costs at most c_d x (grad_tol + that)
+    go, ho, xo = ch.g, ch.h, ch.xo
+    r = np.where(ho > 0, go / np.where(ho > 0, ho, 1), 0.0)
+    tiny = (ho <= H.UNDERFLOW[prec] * ho.max()) & (go <= H.UNDERFLOW[prec] * max(go.max(), 1e-300))
+    bd = ch.c_d * xo * (1.1 * (tg + th) * r + GRAD_TOL[prec]) + rel * np.abs(ch.d) + 1e-300
+    bad = (np.abs(d - ch.d) > bd) & ~tiny
+    assert not bad.any(), f"d: {int(bad.sum())} entries outside the propagated bound"
+    assert npos == int((d > 0).sum())
+    assert np.dot(ch.h, d) >= np.dot(ch.g, d) * (1 - 10 * (tg + th))   # Lagrangian condition on the GPU's d
+    # a6: dy = Pd, dz = Cd
+    dy = vec(M, ctx, M.VEC_DY, ch.mP)
+    dz = vec(M, ctx, M.VEC_DZ, ch.mC)
+    bd_t = np.where(tiny, ch.c_d * xo, bd)
+    bdy = ch.P @ bd_t + rel * (ch.P @ np.abs(ch.d)) + 1e-300
+    bdz = ch.C @ bd_t + rel * (ch.C @ np.abs(ch.d)) + 1e-300
+    assert (np.abs(dy - ch.dy) <= bdy).all(), "dy=Pd outside the propagated bound"
+    assert (np.abs(dz - ch.dz) <= bdz).all(), "dz=Cd outside the propagated bound"
+    edy = float(np.abs(dy - ch.dy).max())
+    edz = float(np.abs(dz - ch.dz).max())
+    return dict(ey=ey, ez=ez, edy=edy, edz=edz, d=d, y=y, z=z, dy=dy, dz=dz)
+
+
+def cand_bounds(ch, e, a, prec):
+    """|Psi' - Psi| and |Phi' - Phi| at alpha = a: smax and smin are 1-Lipschitz
+    in the max norm, plus the GPU's own evaluation error of the difference."""
+    rel = H.REL[prec]
+    fl = 1e-14 * (1 + abs(om.smax(ch.y, ch.eta)) + abs(om.smin(ch.z, ch.eta)))
+    own = fl + (1e-8 / ch.eta if prec == "f32" else 0.0)
+    bpsi = 1.05 * (2 * e["ey"] + a * e["edy"]) + own
+    bphi = 1.05 * (2 * e["ez"] + a * e["edz"]) + own
+    return bpsi, bphi
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kind", KINDS)
 def test_iteration_steps_match_oracle(M, wls, kind, prec):
@@ -72,99 +177,99 @@ def test_iteration_steps_match_oracle(M, wls, kind, prec):
     try:
         T = probe_target(wl)
         M.mwu_set_target(ctx, T)
-        P, C, c = H.oracle_matrices(wl, T)
-        n = H.n_vars(wl)
+        ch = Chain(wl, prec, T)
         sc = M.mwu_get_scalars(ctx)
-        mP, mC = P.shape[0], C.shape[0]
-        eta = om.eta_of(mP + mC, wl.eps)
-        assert sc["eta"] == pytest.approx(eta, rel=1e-15)
-        assert sc["c_d"] == pytest.approx(om.step_coefficient(mP, mC, eta), rel=1e-15)
+        assert sc["eta"] == pytest.approx(ch.eta, rel=1e-15)
+        assert sc["c_d"] == pytest.approx(ch.c_d, rel=1e-15)
         # a0: initial x
-        x0 = vec(M, ctx, M.VEC_X, n)
-        H.assert_rel(x0, om.x_init(P, wl.eps), 1e-7 if prec == "f32" else 1e-15, what="x0")
-        # a state away from x0 so that the weights are not uniform
-        rng = np.random.default_rng(7)
-        dt = np.float32 if prec == "f32" else np.float64
-        x = x0 * rng.uniform(1.0, 40.0, n)
-        # keep the probe running: max(Px) and min(Cx) below 1
-        f = 0.8 / max(float((P @ x).max()), float((C @ x).min()))
-        x = (x * min(1.0, f)).astype(dt)
-        M.mwu_set_x(ctx, torch.from_numpy(x).cuda())
-        xo = x.astype(np.float64)
-        # a1: y = Px, z = Cx
-        y = vec(M, ctx, M.VEC_Y, mP)
-        z = vec(M, ctx, M.VEC_Z, mC)
-        H.assert_rel(y, P @ xo, rel, what="y=Px")
-        H.assert_rel(z, C @ xo, rel, what="z=Cx")
-        # a2, a3: shifted LSE of the same y, z
-        sc = M.mwu_get_scalars(ctx)
-        s_p, S_p = om.lse_shift_sum(y, eta, +1)
-        s_c, S_c = om.lse_shift_sum(z, eta, -1)
-        assert sc["s_p"] == s_p and sc["s_c"] == s_c
-        H.assert_rel([sc["S_p"], sc["S_c"]], [S_p, S_c], rel, what="S")
-        # a4, a5: gradients and direction
-        rc, npos = M.mwu_direction(ctx)
-        assert rc == M.OK
-        g = vec(M, ctx, M.VEC_G, n)
-        h = vec(M, ctx, M.VEC_H, n)
-        d = vec(M, ctx, M.VEC_D, n)
-        go, ho = om.gradients(P, C, y, z, eta)
-        H.assert_rel(g, go, rel, what="g=P^T w_p", floor=H.UNDERFLOW[prec])
-        H.assert_rel(h, ho, rel, what="h=C^T w_c", floor=H.UNDERFLOW[prec])
-        c_d = sc["c_d"]
-        do = om.direction(go, ho, xo, c_d)
-        r = np.where(ho > 0, go / np.where(ho > 0, ho, 1), np.inf)
-        band = np.abs(1.0 - r) < 10 * rel
-        # variables whose g and h are both below the representable range carry no decision
-        tiny = (ho <= H.UNDERFLOW[prec] * ho.max()) & (go <= H.UNDERFLOW[prec] * max(go.max(), 1e-300))
-        band |= tiny
-        flips = (d > 0) != (do > 0)
-        assert not (flips & ~band).any(), "gradient test differs outside the rounding band"
-        agree = ~flips
-        tol = c_d * xo * (4 * rel * np.minimum(r, 1e6)) + rel * np.abs(do) + 1e-300
-        assert (np.abs(d - do)[agree] <= tol[agree]).all(), "d magnitude"
-        assert npos == int((d > 0).sum())
-        assert np.dot(ho, d) >= np.dot(go, d) * (1 - 10 * rel)   # Lagrangian condition on the GPU's d
-        # a6: dy = Pd, dz = Cd on the same d
-        dy = vec(M, ctx, M.VEC_DY, mP)
-        dz = vec(M, ctx, M.VEC_DZ, mC)
-        H.assert_rel(dy, P @ d, rel, abs_=1e-300, what="dy=Pd")
-        H.assert_rel(dz, C @ d, rel, abs_=1e-300, what="dz=Cd")
-        # a7: candidates on the same y, dy, z, dz
+        x0 = vec(M, ctx, M.VEC_X, ch.n)
+        H.assert_rel(x0, om.x_init(ch.P, wl.eps), 1e-7 if prec == "f32" else 1e-15, what="x0")
+        e = run_direction_checks(M, ctx, wl, prec, ch)
+        # a7: candidates
         alphas = [1.0, 2.0, 4.0, 16.0, 128.0, 1000.0, 3.0e4, 1.5]
         psi, phi, zmn = M.mwu_eval_candidates(ctx, alphas)
         for k, a in enumerate(alphas):
-            pw = om.Psi(y, dy, a, eta)
-            pf = om.Phi(z, dz, a, eta)
-            # the oracle's own FP64 cancellation error in a difference of two LSEs
-            fl = 1e-14 * (1 + abs(om.smax(y, eta)) + abs(om.smin(z, eta)))
-            H.assert_rel([psi[k]], [pw], rel, abs_=fl + (1e-8 / eta if prec == "f32" else 0), what=f"Psi({a})")
-            H.assert_rel([phi[k]], [pf], rel, abs_=fl + (1e-8 / eta if prec == "f32" else 0), what=f"Phi({a})")
-            H.assert_rel([zmn[k]], [float((z + a * dz).min())], rel, what=f"min z({a})")
-        # the step-size search on the same vectors
+            bpsi, bphi = cand_bounds(ch, e, a, prec)
+            H.assert_rel([psi[k]], [om.Psi(ch.y, ch.dy, a, ch.eta)], rel, abs_=bpsi, what=f"Psi({a})")
+            H.assert_rel([phi[k]], [om.Phi(ch.z, ch.dz, a, ch.eta)], rel, abs_=bphi, what=f"Phi({a})")
+            H.assert_rel([zmn[k]], [float((ch.z + a * ch.dz).min())], rel,
+                         abs_=1.05 * (e["ez"] + a * e["edz"]), what=f"min z({a})")
+        # the K-candidate search
         rc, alpha, ev = M.mwu_search(ctx)
-        evaluate = om.make_evaluator(y, dy, z, dz, eta)
         K = 1 if prec == "fp64" else 8
-        ao, info = om.search_kary(evaluate, wl.eps, K=K, max_passes=6 if K == 8 else 64)
-        if alpha != ao:
-            # only a decision inside the rounding band may differ: check f at both
-            for a in (alpha, ao):
-                if a >= 1:
-                    f = om.Phi(z, dz, a, eta) / om.Psi(y, dy, a, eta)
-                    assert abs(f - 1) < 1e-3 or (a == alpha and f >= 1 - 1e-4), (alpha, ao, f)
-        # a8: one full iteration from the same x reproduces x + alpha d, y + alpha dy, z + alpha dz
-        M.mwu_set_x(ctx, torch.from_numpy(x).cuda())
+        ao, info = om.search_kary(ch.evaluate, wl.eps, K=K, max_passes=6 if K == 8 else 64)
+        check_step_decision(ch, e, prec, alpha, ao)
+        # a8: one full iteration from the same x
+        M.mwu_set_x(ctx, torch.from_numpy(ch.x).cuda())
         rc, st = M.mwu_iterate(ctx, 1)
-        a1 = st["alpha"]
-        if st["iters"] == 1:
-            x1 = vec(M, ctx, M.VEC_X, n)
-            y1 = vec(M, ctx, M.VEC_Y, mP)
-            z1 = vec(M, ctx, M.VEC_Z, mC)
-            H.assert_rel(x1, xo + a1 * d, 4 * rel, abs_=1e-300, what="x update")
-            if mP > 1:
-                H.assert_rel(y1, y + a1 * dy, 4 * rel, what="y update")
-            if mC > 1:
-                H.assert_rel(z1, z + a1 * dz, 4 * rel, what="z update")
+        if st["iters"] == 1 and st["alpha"] == ao:
+            bd = np.abs(e["d"] - ch.d)
+            x1 = vec(M, ctx, M.VEC_X, ch.n)
+            H.assert_rel(x1, ch.xo + ao * ch.d, 4 * rel, abs_=1.05 * ao * bd + 1e-300, what="x update")
+            if ch.mP > 1:
+                y1 = vec(M, ctx, M.VEC_Y, ch.mP)
+                H.assert_rel(y1, ch.y + ao * ch.dy, 4 * rel, abs_=1.05 * (e["ey"] + ao * e["edy"]), what="y update")
+            if ch.mC > 1:
+                z1 = vec(M, ctx, M.VEC_Z, ch.mC)
+                H.assert_rel(z1, ch.z + ao * ch.dz, 4 * rel, abs_=1.05 * (e["ez"] + ao * e["edz"]), what="z update")
+    finally:
+        M.mwu_destroy(ctx)
+
+
+def check_step_decision(ch, e, prec, alpha, ao, rel_gap=0.0):
+    """The GPU's step equals the oracle's, or both lie where f = Phi/Psi is
+    within the propagated evaluation error of 1 (a decision in the rounding band)."""
+    if alpha == ao or (rel_gap > 0 and ao > 0 and abs(alpha / ao - 1) <= rel_gap):
+        return
+    for a in (alpha, ao):
+        if a >= 1:
+            ps = om.Psi(ch.y, ch.dy, a, ch.eta)
+            ph = om.Phi(ch.z, ch.dz, a, ch.eta)
+            bpsi, bphi = cand_bounds(ch, e, a, prec)
+            band = (bpsi + bphi) / ps + 10 * H.REL[prec]
+            f = ph / ps
+            assert f >= 1 - band, (alpha, ao, f, band)
+            if rel_gap == 0:
+                assert abs(f - 1) <= band or a == alpha, (alpha, ao, f, band)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kind", KINDS)
+def test_newton_search_matches_oracle(M, wls, kind, prec):
+    """Newton's method (Sec. 4.2): Psi', Phi' and the search from a cold start."""
+    wl = wls[kind]
+    rel = H.REL[prec]
+    ctx = make_ctx(M, wl, prec, step=M.STEP_NEWTON)
+    try:
+        T = probe_target(wl)
+        M.mwu_set_target(ctx, T)
+        ch = Chain(wl, prec, T)
+        e = run_direction_checks(M, ctx, wl, prec, ch)
+        for a in [1.0, 7.0, 150.0, 4000.0]:
+            psi, phi, dpsi, dphi = M.mwu_eval_newton(ctx, a)
+            bpsi, bphi = cand_bounds(ch, e, a, prec)
+            H.assert_rel([psi], [om.Psi(ch.y, ch.dy, a, ch.eta)], rel, abs_=bpsi, what=f"Psi({a})")
+            H.assert_rel([phi], [om.Phi(ch.z, ch.dz, a, ch.eta)], rel, abs_=bphi, what=f"Phi({a})")
+            # Psi' = <dy, softmax(eta (y + a dy))>: the weights move by the
+            # softmax bound of the logits' error, dy by its own error
+            wp = _softmax_l1(e["ey"] + a * e["edy"], ch.eta)
+            wc = _softmax_l1(e["ez"] + a * e["edz"], ch.eta)
+            H.assert_rel([dpsi], [om.dPsi(ch.y, ch.dy, a, ch.eta)], 4 * rel,
+                         abs_=1.1 * (e["edy"] + np.abs(ch.dy).max() * wp) + 1e-300, what=f"Psi'({a})")
+            H.assert_rel([dphi], [om.dPhi(ch.z, ch.dz, a, ch.eta)], 4 * rel,
+                         abs_=1.1 * (e["edz"] + np.abs(ch.dz).max() * wc) + 1e-300, what=f"Phi'({a})")
+        rc, alpha, ev = M.mwu_search(ctx)
+        K = 1 if prec == "fp64" else 8
+        ao, info = om.search_newton(ch.evaluate_nd, ch.evaluate, wl.eps, K=K, alpha0=None,
+                                    max_passes=10 if K == 8 else 64)
+        # Newton iterates are continuous in Psi, Phi: the two searches may end a
+        # Newton tolerance apart; decisions must otherwise be valid
+        check_step_decision(ch, e, prec, alpha, ao, rel_gap=2 * wl.eps / 20 + 1e-3)
+        ok, _ = ch.evaluate([alpha])
+        if alpha >= 1 and not ok[0]:
+            bpsi, bphi = cand_bounds(ch, e, alpha, prec)
+            ps = om.Psi(ch.y, ch.dy, alpha, ch.eta)
+            assert om.Phi(ch.z, ch.dz, alpha, ch.eta) >= ps - bpsi - bphi
     finally:
         M.mwu_destroy(ctx)
 
@@ -200,11 +305,12 @@ def certificate_from_x(wl, x):
         return om.certified_densest(olp.pair_matrix(g.n, u, v), olp.interweave(g.m), x)
 
 
+@pytest.mark.parametrize("step", ["kary", "newton"])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kind", KINDS)
-def test_solve_matches_oracle_and_exact(M, wls, kind, prec):
+def test_solve_matches_oracle_and_exact(M, wls, kind, prec, step):
     wl = wls[kind]
-    ctx = make_ctx(M, wl, prec)
+    ctx = make_ctx(M, wl, prec, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY)
     try:
         res = M.mwu_solve(ctx)
         x = vec(M, ctx, M.VEC_X, H.n_vars(wl))
@@ -219,7 +325,7 @@ def test_solve_matches_oracle_and_exact(M, wls, kind, prec):
         assert opt / tol2 <= cert <= opt * (1 + 1e-9)
     else:
         assert opt * (1 - 1e-9) <= cert <= opt * tol2
-    ores = H.oracle_solve(wl)
+    ores = H.oracle_solve(wl, step=step)
     ratio = cert / ores.objective
     assert 1 / (1 + wl.eps) <= ratio <= 1 + wl.eps, (cert, ores.objective)
 
