@@ -166,8 +166,7 @@ typedef struct {
 typedef struct {
     double dir_ms;             /* gradient + direction kernel (with the deferred x update)   */
     double spmv_ms;            /* forward SpMV dy = Pd, dz = Cd                              */
-    double cand_first_ms;      /* first candidate pass                                       */
-    double cand_rest_ms;       /* further candidate passes (exit at once when done)          */
+    double cand_ms;            /* step-size search: all candidate passes of the iteration    */
     double update_ms;          /* y, z update with the next iteration's reductions           */
     int64_t iters;             /* iterations timed                                           */
     int64_t cand_passes;       /* candidate passes that evaluated candidates                 */

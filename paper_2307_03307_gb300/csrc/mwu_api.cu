@@ -339,12 +339,16 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.grid_row = std::max(2, c->n_sms * row_bps);
     p.grid_upd = std::max(2, c->n_sms * std::min(upd_bps, row_bps));
     p.grid_spmv = std::max(2, c->n_sms * std::min(8, spmv_blocks_per_sm<T>()));
-    size_t recs = (size_t)std::max(p.grid_var, std::max(p.grid_row, p.grid_upd)) + 8;
+    p.grid_newton = std::max(2, c->n_sms * std::min(8, newton_blocks_per_sm<T>()));
+    p.cond_on = 0;
+    p.cond = 0;
+    size_t recs = (size_t)std::max(std::max(p.grid_var, p.grid_newton), std::max(p.grid_row, p.grid_upd)) + 8;
     p.part_var = c->ar.alloc<double>((int64_t)(recs * REC));
     p.part_row = c->ar.alloc<double>((int64_t)(recs * REC));
     p.part_grp = c->ar.alloc<double>((int64_t)2 * GRP_MAX * REC);
     if (!p.part_var || !p.part_row || !p.part_grp) return fail(c, MWU_ERR_OOM, "allocating partial buffers");
-    if (std::max(p.grid_row, p.grid_upd) > GRP * GRP_MAX) return fail(c, MWU_ERR_INVALID, "grid too large for the group tickets");
+    if (std::max(std::max(p.grid_row, p.grid_newton), p.grid_upd) > GRP * GRP_MAX)
+        return fail(c, MWU_ERR_INVALID, "grid too large for the group tickets");
     p.G_var = G_var;
     p.heavy_var = heavy_var;
     p.n_heavy_var = n_heavy_var;
@@ -621,18 +625,22 @@ int mwu_set_x(mwu_ctx *c, const void *x, int32_t x_is_fp64) {
 // kernels of one iteration; ev (6 events or nullptr) brackets the kernel classes.  The
 // events are recorded as external event nodes when the sequence is captured.
 static int kernels_per_iteration(const mwu_ctx *c) { return 3 + c->opt.max_passes; }
-constexpr int EV_PER_IT = 6;
+constexpr int EV_PER_IT = 5;
 
-// The passes after the first one.  Captured (graph): a conditional WHILE node
-// whose body is one candidate pass; every pass sets the loop condition, so
-// the loop runs exactly the passes the search needs.  Eager: max_passes - 1
-// launches that return at once when the search has ended.
+// The step-size search of one iteration.  Captured (graph): a conditional WHILE
+// node, opened by the direction kernel, whose body is one Newton pass kernel
+// and one K-candidate pass kernel (each returns at once outside its phases);
+// every body turn ends by setting the loop condition, so the loop runs the
+// passes the search needs.  Eager: max_passes turns of the same kernels,
+// which return at once once the search has ended.
 template <class Prob>
-static cudaError_t enqueue_search_rest(mwu_ctx *c, Prob &p, bool loop, cudaGraphConditionalHandle h) {
+static cudaError_t enqueue_search(mwu_ctx *c, Prob &p, bool loop) {
     cudaError_t e;
     if (!loop) {
-        for (int k = 1; k < c->opt.max_passes; ++k)
+        for (int k = 0; k < c->opt.max_passes; ++k) {
+            if (c->opt.step == MWU_STEP_NEWTON && (e = launch_cand_newton(p, c->stream)) != cudaSuccess) return e;
             if ((e = launch_cand(p, 0, c->stream)) != cudaSuccess) return e;
+        }
         return cudaSuccess;
     }
     cudaStreamCaptureStatus cs;
@@ -642,7 +650,7 @@ static cudaError_t enqueue_search_rest(mwu_ctx *c, Prob &p, bool loop, cudaGraph
     if ((e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess) return e;
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
+    np.conditional.handle = p.cond;
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     cudaGraphNode_t node;
@@ -655,34 +663,34 @@ static cudaError_t enqueue_search_rest(mwu_ctx *c, Prob &p, bool loop, cudaGraph
     if ((e = cudaStreamBeginCaptureToGraph(c->body_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed)) != cudaSuccess)
         return e;
-    cudaError_t e1 = launch_cand(p, 0, c->body_stream, 1, h);
+    cudaError_t e1 = launch_cand_newton(p, c->body_stream);
+    if (e1 == cudaSuccess) e1 = launch_cand(p, 0, c->body_stream);
     cudaGraph_t body = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->body_stream, &body);
     return e1 != cudaSuccess ? e1 : e2;
 }
 
 static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev, bool loop = false) {
-    return with_prob(c, [&](auto &p) -> cudaError_t {
+    return with_prob(c, [&](auto &p0) -> cudaError_t {
         cudaError_t e;
-        cudaGraphConditionalHandle h = 0;
+        auto p = p0;   // this iteration's copy: carries the handle of its search loop
         if (loop) {
             cudaStreamCaptureStatus cs;
             cudaGraph_t g = nullptr;
             if ((e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess)
                 return e;
-            if ((e = cudaGraphConditionalHandleCreate(&h, g, 0u, 0u)) != cudaSuccess) return e;
+            if ((e = cudaGraphConditionalHandleCreate(&p.cond, g, 0u, 0u)) != cudaSuccess) return e;
+            p.cond_on = 1;
         }
         if (ev && (e = cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_dir(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_spmv(p, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = launch_cand(p, 0, c->stream, loop ? 1 : 0, h)) != cudaSuccess) return e;
+        if ((e = enqueue_search(c, p, loop)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[3], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = enqueue_search_rest(c, p, loop, h)) != cudaSuccess) return e;
-        if (ev && (e = cudaEventRecordWithFlags(ev[4], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_update(p, c->stream)) != cudaSuccess) return e;
-        if (ev && (e = cudaEventRecordWithFlags(ev[5], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[4], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         return cudaSuccess;
     });
 }
@@ -728,9 +736,8 @@ static int accumulate_timing(mwu_ctx *c, const std::vector<cudaEvent_t> &ev, int
             TRY_CUDA(c, cudaEventElapsedTime(&t[j], ev[EV_PER_IT * k + j], ev[EV_PER_IT * k + j + 1]));
         c->tim.dir_ms += t[0];
         c->tim.spmv_ms += t[1];
-        c->tim.cand_first_ms += t[2];
-        c->tim.cand_rest_ms += t[3];
-        c->tim.update_ms += t[4];
+        c->tim.cand_ms += t[2];
+        c->tim.update_ms += t[3];
         c->tim.iters += 1;
     }
     return MWU_OK;
@@ -772,7 +779,6 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_spmv(p, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[2], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
-            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[3], c->stream));
             c->launches += 3;
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             int guard = 0;
@@ -781,9 +787,9 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
                 c->launches += 1;
                 if ((rc = pull_state(c)) != MWU_OK) return rc;
             }
-            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[4], c->stream));
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[3], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_update(p, c->stream); }));
-            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[5], c->stream));
+            if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[4], c->stream));
             c->launches += 1;
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             if (c->opt.timing && (rc = accumulate_timing(c, ev, c->st_host->iter - iter0)) != MWU_OK) return rc;

@@ -152,6 +152,11 @@ struct Problem {
     int32_t grid_var, grid_row;   // grid sizes (blocks): variable kernels, candidate passes
     int32_t grid_upd;             // grid of the update kernel
     int32_t grid_spmv;            // grid of the forward SpMV (its own occupancy)
+    int32_t grid_newton;          // grid of the one-candidate Newton pass (its own occupancy)
+    // a captured iteration: the handle of its step-search WHILE loop, which the
+    // direction kernel opens and every candidate pass sets (0 = not captured)
+    int32_t cond_on;
+    cudaGraphConditionalHandle cond;
     int32_t G_var;      // lanes per variable for CSR column views
     int32_t heavy_var_len;
     int32_t n_heavy_var;
@@ -165,11 +170,9 @@ template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, 
 template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s);             // a1-a3 at a new x
 template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s);      // a4-a5 (+ fused x update)
 template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s);                  // a6: dy = Pd, dz = Cd
-// cond_on: the kernel sets `cond` (the while-loop handle of a captured
-// iteration graph) to 1 while the step search must continue, else 0
-template <class T>
-cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s, int cond_on = 0,
-                        cudaGraphConditionalHandle cond = 0);    // a7: one candidate pass
+template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s);
+// one-candidate Newton pass (captured iterations): returns at once unless the search is in its Newton phase
+template <class T> cudaError_t launch_cand_newton(const Problem<T> &p, cudaStream_t s);    // a7: one candidate pass
 template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s);                // a8
 template <class T> cudaError_t launch_flush(const Problem<T> &p, cudaStream_t s);                 // pending x update
 template <class T> cudaError_t launch_search_begin(const Problem<T> &p, cudaStream_t s);
@@ -183,5 +186,6 @@ void set_global_error(const char *msg);
 // Kernel occupancy helper (blocks per SM of the heaviest sweep kernel).
 template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_bps);
 template <class T> int spmv_blocks_per_sm();
+template <class T> int newton_blocks_per_sm();
 
 }  // namespace mwu

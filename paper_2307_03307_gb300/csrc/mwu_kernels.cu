@@ -102,6 +102,104 @@ template <class T, class U> __device__ __forceinline__ void lse_merge(Lse<U> &a,
     a.s = s;
 }
 
+// ---------------------------------------------------------------- record merges
+// Per-block records of shifted sums (log-sum-exp sums of Sec. 2.2, candidate
+// sums of Sec. 4.1) are merged by one warp per quantity in the last block: the
+// common shift M = max_i m_i first, then each sum scaled by e^{c (m_i - M)}
+// (or added as it is), accumulated per lane in compensated FP32 (Kahan) and
+// combined across the 32 lanes in FP64.  GB300 issues FP64 at a small fraction
+// of the FP32 rate, so FP64 is kept to the five steps of the lane tree.  The
+// records hold T values (FP32 in the fast form, FP64 in the plain form).
+template <class T> __host__ __device__ constexpr int rec_len() { return REC * (int)(sizeof(double) / sizeof(T)); }
+template <class T> __device__ __forceinline__ T *rec_of(const double *part, int b) {
+    return reinterpret_cast<T *>(const_cast<double *>(part)) + (size_t)b * rec_len<T>();
+}
+
+template <class T> __device__ __forceinline__ void kahan_add(T &sum, T &comp, T x) {
+    const T y = x - comp;
+    const T t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// Merges, for each quantity q < nq, the block records b in [b0, b1) given by
+// range(q, b0, b1).  get(q, b, m, r, v) reads record b's shift m, its NV sums r
+// and (HASMIN) a value v whose minimum is wanted; bit j of scaled(q) marks the
+// sums that carry the factor e^{c (m - M)}; records with r[0] = 0 are empty.
+// The 8 warps share the quantities (several warps per quantity when nq < 8),
+// each lane takes a strided subset of records with the loads unrolled, and
+// emit(q, M, tot, vmin) runs once per quantity with the FP64 totals.  Every
+// thread of the block must call it (it synchronises).
+template <class T, int NV, bool HASMIN, class Range, class Scaled, class Get, class Emit>
+__device__ void block_merge_shifted(int nq, T c, Range range, Scaled scaled, Get get, Emit emit) {
+    constexpr int NW = BLOCK / 32;
+    __shared__ T sm_M[NW], sm_min[NW];
+    __shared__ double sm_S[NW][NV];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r0 = 0; r0 < nq; r0 += NW) {
+        const int nr = min(NW, nq - r0);
+        const int nwc = NW / nr;                       // warps per quantity in this round
+        const int qi = w / nwc, sub = w % nwc;
+        const bool act = qi < nr;
+        const int q = r0 + qi;
+        int b0 = 0, b1 = 0;
+        if (act) range(q, b0, b1);
+        const int first = b0 + sub * 32 + lane, stride = 32 * nwc;
+        T M = -t_inf<T>(), vmin = t_inf<T>();
+#pragma unroll 4
+        for (int b = first; b < b1; b += stride) {
+            T m, r[NV], v;
+            get(q, b, m, r, v);
+            if (r[0] != T(0)) M = fmax(M, m);
+            if (HASMIN) vmin = fmin(vmin, v);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            M = fmax(M, shfl_x(M, off));
+            if (HASMIN) vmin = fmin(vmin, shfl_x(vmin, off));
+        }
+        if (lane == 0) { sm_M[w] = M; sm_min[w] = vmin; }
+        __syncthreads();
+        if (act) {
+            M = sm_M[qi * nwc];
+            vmin = sm_min[qi * nwc];
+            for (int j = 1; j < nwc; ++j) {
+                M = fmax(M, sm_M[qi * nwc + j]);
+                vmin = fmin(vmin, sm_min[qi * nwc + j]);
+            }
+        }
+        T sum[NV], comp[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) { sum[j] = T(0); comp[j] = T(0); }
+        const unsigned sc = act ? scaled(q) : 0u;
+#pragma unroll 4
+        for (int b = first; b < b1; b += stride) {
+            T m, r[NV], v;
+            get(q, b, m, r, v);
+            const T f = (r[0] != T(0)) ? t_exp(c * (m - M)) : T(0);
+#pragma unroll
+            for (int j = 0; j < NV; ++j) kahan_add(sum[j], comp[j], ((sc >> j) & 1u) ? r[j] * f : r[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double t = (double)sum[j] - (double)comp[j];
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == 0) sm_S[w][j] = t;
+        }
+        __syncthreads();
+        if (act && sub == 0 && lane == 0) {
+            double tot[NV];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                tot[j] = 0.0;
+                for (int i = 0; i < nwc; ++i) tot[j] += sm_S[qi * nwc + i][j];
+            }
+            emit(q, M, tot, vmin);
+        }
+        __syncthreads();
+    }
+}
+
+
 // ---------------------------------------------------------------- last block
 __device__ __forceinline__ bool last_block_done(unsigned int *counter) {
     __shared__ bool am_last;
@@ -294,23 +392,28 @@ __global__ void __launch_bounds__(BLOCK) k_x_prep(Problem<T> p, const void *xin,
 // Merge per-block LSE records of the row kernels plus dense-row values and set
 // s, S, ymax, zmin and the stop status (Alg. 2 loop test, see the oracle).
 template <class T>
-__device__ void finalize_reductions(Problem<T> &p, const double *recs, int nb_row, int nb_var, bool dense_from_var,
-                                    double alpha) {
+__device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_var, bool dense_from_var, double alpha) {
+    // LSE block records (float view of part_row): [0] shift s_b, [1] S_b;
+    // side 0 in blocks [0, gP), side 1 in [gP, nb_row).  Warp s merges side s
+    // on the sign-adjusted shift sg * s_b.
     static_assert(BLOCK == 256, "merge layout assumes 256 threads");
     DevState *st = p.st;
-    __shared__ double sh_s[2][BLOCK], sh_S[2][BLOCK];
+    __shared__ double sh_fin[2][2];
     __shared__ double sh_d[32];
-    // each thread merges a strided subset of the block records ...
-    for (int s = 0; s < 2; ++s) {
-        Lse<double> a{0.0, 0.0};
-        double eta_sgn = st->eta * (double)p.side[s].sign;
-        for (int b = threadIdx.x; b < nb_row; b += blockDim.x) {
-            const double *r = recs + (size_t)b * REC;
-            lse_merge<T, double>(a, r[2 * s], r[2 * s + 1], eta_sgn, p.side[s].sign);
-        }
-        sh_s[s][threadIdx.x] = a.s;
-        sh_S[s][threadIdx.x] = a.S;
-    }
+    block_merge_shifted<T, 1, false>(
+        2, (T)st->eta,
+        [&](int q, int &b0, int &b1) { b0 = q == 0 ? 0 : gP; b1 = q == 0 ? gP : nb_row; },
+        [&](int) { return 1u; },
+        [&](int q, int b, T &m, T (&r)[1], T &v) {
+            const T *o = rec_of<T>(p.part_row, b);
+            m = p.side[q].sign > 0 ? o[0] : -o[0];   // sign-adjusted shift: the merge takes the max
+            r[0] = o[1];
+            v = T(0);
+        },
+        [&](int q, T M, const double (&tot)[1], T) {
+            sh_fin[q][0] = p.side[q].sign > 0 ? (double)M : -(double)M;
+            sh_fin[q][1] = tot[0];
+        });
     double dense[2] = {0.0, 0.0};
     if (dense_from_var) {
         double d0 = 0.0, d1 = 0.0;
@@ -322,19 +425,6 @@ __device__ void finalize_reductions(Problem<T> &p, const double *recs, int nb_ro
         dense[1] = block_sum(d1, sh_d);
     }
     __syncthreads();
-    // ... then a tree over the threads (fixed order)
-    for (int half = BLOCK / 2; half > 0; half >>= 1) {
-        if (threadIdx.x < half) {
-            for (int s = 0; s < 2; ++s) {
-                Lse<double> a{sh_s[s][threadIdx.x], sh_S[s][threadIdx.x]};
-                lse_merge<T, double>(a, sh_s[s][threadIdx.x + half], sh_S[s][threadIdx.x + half],
-                                     st->eta * (double)p.side[s].sign, p.side[s].sign);
-                sh_s[s][threadIdx.x] = a.s;
-                sh_S[s][threadIdx.x] = a.S;
-            }
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
         bool bad = false;
         for (int s = 0; s < 2; ++s) {
@@ -345,8 +435,8 @@ __device__ void finalize_reductions(Problem<T> &p, const double *recs, int nb_ro
                 st->s[s] = st->dense_v[s];
                 st->S[s] = 1.0;
             } else {
-                st->s[s] = sh_s[s][0];
-                st->S[s] = sh_S[s][0];
+                st->s[s] = sh_fin[s][0];
+                st->S[s] = sh_fin[s][1];
             }
             if (!isfinite(st->s[s]) || !isfinite(st->S[s]) || !(st->S[s] > 0.0)) bad = true;
         }
@@ -369,6 +459,38 @@ __device__ void finalize_reductions(Problem<T> &p, const double *recs, int nb_ro
             }
         }
     }
+}
+
+// End of a block's LSE accumulation: warps in T, then an 8-lane tree over the
+// warps in T, then one float record [shift, S] per block.
+template <class T>
+__device__ void lse_block_record(const Problem<T> &p, Lse<T> acc, T eta_sgn, int sgn) {
+    for (int off = 16; off > 0; off >>= 1) {
+        T os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
+        lse_merge<T, T>(acc, os, oS, eta_sgn, sgn);
+    }
+    __shared__ T ws[BLOCK / 32], wS[BLOCK / 32];
+    if ((threadIdx.x & 31) == 0) { ws[threadIdx.x >> 5] = acc.s; wS[threadIdx.x >> 5] = acc.S; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        Lse<T> q{ws[threadIdx.x & 7], wS[threadIdx.x & 7]};
+        for (int off = 4; off > 0; off >>= 1) {
+            T os = shfl_x(q.s, off), oS = shfl_x(q.S, off);
+            lse_merge<T, T>(q, os, oS, eta_sgn, sgn);
+        }
+        if (threadIdx.x == 0) {
+            T *rec = rec_of<T>(p.part_row, blockIdx.x);
+            rec[0] = q.s;
+            rec[1] = q.S;
+        }
+    }
+}
+
+// Condition of the step-search loop of a captured iteration: 1 while the
+// search of this iteration has passes left.  Each kernel that sets it does so
+// from one thread, once per launch.
+__device__ __forceinline__ unsigned search_continues(const DevState *st) {
+    return (st->status == ST_RUNNING && st->phase != PH_DONE) ? 1u : 0u;
 }
 
 // ============================================================ gradient + direction
@@ -506,6 +628,7 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
             }
             if (running) dir_finish(st, np_t, dd[0], dd[1]);
             st->counter[1] = 0;
+            if (p.cond_on) cudaGraphSetConditional(p.cond, search_continues(st));
         }
     }
 }
@@ -599,6 +722,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
             st->pending = 0;
             if (running) dir_finish(st, np_t, 0.0, 0.0);
             st->counter[1] = 0;
+            if (p.cond_on) cudaGraphSetConditional(p.cond, search_continues(st));
         }
     }
 }
@@ -898,6 +1022,73 @@ __device__ void search_decide(DevState *st, const int *ok, const double *zmin_k)
     }
 }
 
+// End of one turn of the search loop (k_cand is the last kernel of a turn):
+// continue while the search runs.  The decide rules end every search within
+// max_passes passes; the guard ends the loop with an error status should that
+// ever fail.
+__device__ void loop_turn_end(DevState *st, cudaGraphConditionalHandle cond) {
+    unsigned v = search_continues(st);
+    if (v && ++st->loop_guard > st->max_passes + 2) {
+        st->status = ST_NUMERIC;
+        st->numeric_bad = 3;
+        v = 0u;
+    }
+    cudaGraphSetConditional(cond, v);
+}
+
+// Psi (packing side, sg = +1) or Phi (covering side, sg = -1) at alpha from the
+// merged shifted sums R (of e^{x - mx}) and Tt of one candidate.  The
+// transcendentals run in T precision (FP32 for the fast form, whose FP64 units
+// are scarce), the sums and the final combination in FP64.
+template <class T>
+__device__ double side_value(const Side<T> &q, int sg, const DevState *st, int ss, double a, double mx, double R,
+                             double Tt) {
+    const double eta_d = st->eta, S0 = st->S[ss];
+    const double lS0 = (double)t_log((T)S0);
+    if (q.rv.kind == RK_DENSE1) return a * st->dense_dv[ss];   // single row: smax / smin exact
+    if (sg > 0) {
+        // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p)
+        const double lq = mx + (double)t_log((T)Tt) - lS0;
+        return (lq < 0.0) ? (double)t_log1p((T)exp_T<T>(lq)) / eta_d : (mx + (double)t_log((T)R) - lS0) / eta_d;
+    }
+    // Phi = -(1/eta) ln(R_true / S_c) = -(1/eta) ln(1 - T_true / S_c)
+    const double qv = Tt / S0;
+    return (qv <= 0.5) ? -(double)t_log1p((T)(-qv)) / eta_d : -(mx + (double)t_log((T)R) - lS0) / eta_d;
+}
+
+// Last block of a candidate pass: merges the (side, k) quantities, k < K,
+// over the block records ([4k + 0..3] = mx, R, Tt, zm of candidate k, [32] =
+// the Newton sum D of candidate 0; side 0 in blocks [0, gP), side 1 after) and
+// writes Psi_k / Phi_k, the derivative of candidate 0 and min(z + alpha_k dz)
+// to fin.
+template <class T>
+__device__ void cand_finish_merge(const Problem<T> &p, int gP, int K, double (*fin)[KMAX][4]) {
+    const DevState *st = p.st;
+    block_merge_shifted<T, 3, true>(
+        2 * K, T(1),
+        [&](int q, int &b0, int &b1) { b0 = q < K ? 0 : gP; b1 = q < K ? gP : (int)gridDim.x; },
+        [&](int q) { return 1u | (p.side[q < K ? 0 : 1].sign > 0 ? 2u : 0u) | 4u; },   // covering T is unshifted
+        [&](int q, int b, T &m, T (&r)[3], T &v) {
+            const int k = q % K;
+            const T *o = rec_of<T>(p.part_row, b);
+            m = o[4 * k + 0];
+            r[0] = o[4 * k + 1];
+            r[1] = o[4 * k + 2];
+            r[2] = k == 0 ? o[32] : T(0);
+            v = o[4 * k + 3];
+        },
+        [&](int q, T M, const double (&tot)[3], T zm) {
+            const int ss = q < K ? 0 : 1, k = q % K;
+            const Side<T> &sd = p.side[ss];
+            const double a = st->alpha[k];
+            fin[ss][k][0] = side_value(sd, sd.sign, st, ss, a, (double)M, tot[0], tot[1]);
+            // Newton: Psi' = D/R (packing side), Phi' = D/R (covering side); both
+            // sums carry the same shift, so the ratio needs no rescale
+            fin[ss][k][1] = (sd.rv.kind == RK_DENSE1) ? st->dense_dv[ss] : (tot[0] > 0.0 ? tot[2] / tot[0] : 0.0);
+            fin[ss][k][3] = (sd.rv.kind == RK_DENSE1) ? st->dense_v[ss] + a * st->dense_dv[ss] : (double)zm;
+        });
+}
+
 // Later candidate passes: stream the stored (v, dv) of one side.
 template <class T, int MODE, int SGN, int KC>
 __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> &sc, const Side<T> &sd, int64_t m,
@@ -1061,23 +1252,9 @@ __global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb
         for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < sd.m; j += (int64_t)nbs * blockDim.x)
             lse_push(acc, sd.v[j], eta_sgn, sd.sign);
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        T os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
-        lse_merge<T, T>(acc, os, oS, eta_sgn, sd.sign);
-    }
-    __shared__ double bs[BLOCK / 32], bS[BLOCK / 32];
-    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = (double)acc.s; bS[threadIdx.x >> 5] = (double)acc.S; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double eds = st->eta * sd.sign;
-        Lse<double> r{0.0, 0.0};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge<T, double>(r, bs[w], bS[w], eds, sd.sign);
-        double *rec = p.part_row + (size_t)blockIdx.x * REC;
-        rec[2 * s] = r.s; rec[2 * s + 1] = r.S;
-        rec[2 * (1 - s)] = 0.0; rec[2 * (1 - s) + 1] = 0.0;
-    }
+    lse_block_record(p, acc, eta_sgn, sd.sign);
     if (last_block_done(&st->counter[0])) {
-        finalize_reductions(p, p.part_row, gridDim.x, nb_var, true, 0.0);
+        finalize_reductions(p, gP, gridDim.x, nb_var, true, 0.0);
         if (threadIdx.x == 0) st->counter[0] = 0;
     }
 }
@@ -1085,14 +1262,14 @@ __global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb
 // a7: K step candidates per constraint row over the stored (v, dv).
 // external = 1: evaluate st->alpha[0..K) and store psi/phi/zmin, no decision.
 template <class T>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int external, int cond_on,
-                                                                  cudaGraphConditionalHandle cond) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int external) {
     __shared__ CandSched<T> s_sc;
     DevState *st = p.st;
-    const bool searching = external || st->phase != PH_DONE;
+    // in a captured iteration the Newton passes belong to k_cand_newton, which
+    // runs just before this kernel in each turn of the search loop
+    const bool searching = external || (st->phase != PH_DONE && !(p.cond_on && st->phase == PH_NEWTON));
     if (st->status != ST_RUNNING || !searching) {
-        // nothing to search: end the device-side loop (one setter per launch)
-        if (cond_on && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) loop_turn_end(st, p.cond);
         return;
     }
     const int K = external ? st->K : st->kpass;
@@ -1173,103 +1350,16 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
             cand_merge1d<T, T>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sd.sign);
         }
         if (w == 0 && k < K) {
-            double *rec = p.part_row + (size_t)blockIdx.x * REC;
-            rec[k * 4 + 0] = mx; rec[k * 4 + 1] = R; rec[k * 4 + 2] = Tt; rec[k * 4 + 3] = zm;
-            if (k == 0) { rec[32] = s; rec[33] = D; }
+            T *rec = rec_of<T>(p.part_row, blockIdx.x);
+            rec[4 * k + 0] = mx; rec[4 * k + 1] = R; rec[4 * k + 2] = Tt; rec[4 * k + 3] = zm;
+            if (k == 0) rec[32] = D;
         }
     }
-    // two-level completion: the last block of each group of GRP blocks merges the
-    // group's records (one per lane), the last group merges the group records, so
-    // the FP64 merge work is spread over the SMs instead of one block
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    const int grp = blockIdx.x / GRP, ngrp = (gridDim.x + GRP - 1) / GRP;
-    const int gsz = min(GRP, (int)gridDim.x - grp * GRP);
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->grp_counter[0][grp], 1u) == (unsigned)(gsz - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    static_assert(BLOCK == 16 * 2 * KMAX, "merge layout assumes 256 threads and KMAX = 8");
-    static_assert(GRP == 16, "one record per lane of a 16-lane group");
-    double *grec = p.part_grp;   // row 0 of the group records
-    {
-        const int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
-        const int ss = q / KMAX, k = q % KMAX;
-        const int sg = p.side[ss].sign;
-        double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
-        const int b = grp * GRP + ln;
-        if (k < K && ln < gsz && (b < gP ? 0 : 1) == ss) {
-            const double *rb = p.part_row + (size_t)b * REC;
-            const double *rec = rb + k * 4;
-            cand_merge1d<T, double>(mx, R, Tt, zm, D, rec[0], rec[1], rec[2], rec[3], k == 0 ? rb[33] : 0.0, sg);
-        }
-        for (int off = 8; off > 0; off >>= 1) {
-            double omx = __shfl_xor_sync(0xffffffffu, mx, off), oR = __shfl_xor_sync(0xffffffffu, R, off);
-            double oT = __shfl_xor_sync(0xffffffffu, Tt, off), oz = __shfl_xor_sync(0xffffffffu, zm, off);
-            double oD = __shfl_xor_sync(0xffffffffu, D, off);
-            cand_merge1d<T, double>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sg);
-        }
-        if (ln == 0) {
-            double *g = grec + (size_t)grp * REC + ss * 32 + k * 4;
-            g[0] = mx; g[1] = R; g[2] = Tt; g[3] = zm;
-            if (k == 0) grec[(size_t)grp * REC + 64 + ss] = D;
-        }
-    }
-    if (threadIdx.x == 0) st->grp_counter[0][grp] = 0;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->counter[2], 1u) == (unsigned)(ngrp - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    // one completion level: the last block merges all block records
+    if (!last_block_done(&st->counter[2])) return;
     {
         __shared__ double fin[2][KMAX][4];
-        {
-            const int q = threadIdx.x >> 4, ln = threadIdx.x & 15;
-            const int ss = q / KMAX, k = q % KMAX;
-            const int sg = p.side[ss].sign;
-            double mx = sg > 0 ? 0.0 : -(double)INFINITY, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
-            for (int gg = ln; gg < ngrp && k < K; gg += 16) {
-                const double *rec = grec + (size_t)gg * REC + ss * 32 + k * 4;
-                const double bD = k == 0 ? grec[(size_t)gg * REC + 64 + ss] : 0.0;
-                cand_merge1d<T, double>(mx, R, Tt, zm, D, rec[0], rec[1], rec[2], rec[3], bD, sg);
-            }
-            for (int off = 8; off > 0; off >>= 1) {
-                double omx = __shfl_xor_sync(0xffffffffu, mx, off), oR = __shfl_xor_sync(0xffffffffu, R, off);
-                double oT = __shfl_xor_sync(0xffffffffu, Tt, off), oz = __shfl_xor_sync(0xffffffffu, zm, off);
-                double oD = __shfl_xor_sync(0xffffffffu, D, off);
-                cand_merge1d<T, double>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sg);
-            }
-            if (ln == 0) {
-                // Psi_k (packing side) or Phi_k (covering side) from the merged sums.  The
-                // transcendentals run in T precision (FP32 for the fast form, whose FP64 units
-                // are scarce), the sums and the final combination in FP64.
-                const Side<T> &q = p.side[ss];
-                double a = k < K ? st->alpha[k] : 0.0;
-                double val;
-                double eta_d = st->eta, S0 = st->S[ss];
-                double lS0 = (double)t_log((T)S0);
-                if (q.rv.kind == RK_DENSE1) {
-                    val = a * st->dense_dv[ss];          // single row: smax / smin exact
-                } else if (sg > 0) {
-                    // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p)
-                    double lq = mx + (double)t_log((T)Tt) - lS0;
-                    val = (lq < 0.0) ? (double)t_log1p((T)exp_T<T>(lq)) / eta_d
-                                     : (mx + (double)t_log((T)R) - lS0) / eta_d;
-                } else {
-                    // Phi = -(1/eta) ln(R_true / S_c) = -(1/eta) ln(1 - T_true / S_c)
-                    double qv = Tt / S0;
-                    val = (qv <= 0.5) ? -(double)t_log1p((T)(-qv)) / eta_d
-                                      : -(mx + (double)t_log((T)R) - lS0) / eta_d;
-                }
-                fin[ss][k][0] = val;
-                // Newton: Psi' = D/R (packing side), Phi' = D/R (covering side); both
-                // sums carry the same shift, so the ratio needs no rescale
-                fin[ss][k][1] = (q.rv.kind == RK_DENSE1) ? st->dense_dv[ss] : (R > 0.0 ? D / R : 0.0);
-                fin[ss][k][3] = (q.rv.kind == RK_DENSE1) ? st->dense_v[ss] + a * st->dense_dv[ss] : zm;
-            }
-        }
+        cand_finish_merge(p, gP, K, fin);
         __syncthreads();
         if (threadIdx.x == 0) {
             int ok[KMAX];
@@ -1298,20 +1388,84 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
                 else if (st->phase == PH_BACKOFF) backoff_decide(st, ok);
                 else search_decide(st, ok, zmk);
             }
-            if (cond_on) {
-                // continue the loop while the search runs; the decide rules end every
-                // search within max_passes passes, and the guard ends the loop (with an
-                // error status) should that ever fail
-                unsigned v = (st->status == ST_RUNNING && st->phase != PH_DONE) ? 1u : 0u;
-                if (v && ++st->loop_guard > st->max_passes + 2) {
-                    st->status = ST_NUMERIC;
-                    st->numeric_bad = 3;
-                    v = 0u;
-                }
-                cudaGraphSetConditional(cond, v);
-            }
+            if (p.cond_on) loop_turn_end(st, p.cond);
             st->counter[2] = 0;
         }
+    }
+}
+
+// ============================================================ Newton pass
+// One-candidate pass of Newton's method (Sec. 4.2) in a captured iteration:
+// Psi, Phi and the sums of Psi', Phi' at alpha_0, then newton_decide.  Per row
+// it is the K-candidate pass in its Newton mode, with one accumulator set and
+// small records, so it runs at higher occupancy than k_cand.
+template <class T>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(Problem<T> p, int gP) {
+    DevState *st = p.st;
+    if (st->status != ST_RUNNING || st->phase != PH_NEWTON) return;   // k_cand follows and ends the loop turn
+    const int s = (blockIdx.x < gP) ? 0 : 1;
+    const int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
+    const int nbs = s == 0 ? gP : gridDim.x - gP;
+    const Side<T> &sd = p.side[s];
+    const T eta = (T)st->eta;
+    const T sh = (T)st->s[s];
+    CandSched<T> sc;
+    sc.K = 1;
+    sc.mode = 3;
+    sc.ca[0] = (T)(st->alpha[0] * st->eta);
+    sc.al[0] = (T)st->alpha[0];
+    sc.cd = T(0);
+    CandAcc<T> acc;
+    cand_init(acc, sd.sign);
+    const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nbs * blockDim.x;
+    if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
+        if (sd.sign > 0) cand_stream<T, 3, 1, 1>(acc, sc, sd, sd.m, tid, nthr, eta, sh);
+        else cand_stream<T, 3, -1, 1>(acc, sc, sd, sd.m, tid, nthr, eta, sh);
+    }
+    // block merge in T, float record in the k_cand layout (candidate 0)
+    T mx = acc.mx[0], R = acc.R[0], Tt = acc.Tt[0], zm = acc.zm[0], D = acc.D;
+    for (int off = 16; off > 0; off >>= 1) {
+        T omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off), oD = shfl_x(D, off);
+        cand_merge1d<T, T>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sd.sign);
+    }
+    __shared__ T wm[BLOCK / 32][5];
+    if ((threadIdx.x & 31) == 0) {
+        T *o = wm[threadIdx.x >> 5];
+        o[0] = mx; o[1] = R; o[2] = Tt; o[3] = zm; o[4] = D;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const T *o = wm[threadIdx.x & 7];
+        mx = o[0]; R = o[1]; Tt = o[2]; zm = o[3]; D = o[4];
+        for (int off = 4; off > 0; off >>= 1) {
+            T omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off), oD = shfl_x(D, off);
+            cand_merge1d<T, T>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, sd.sign);
+        }
+        if (threadIdx.x == 0) {
+            T *rec = rec_of<T>(p.part_row, blockIdx.x);
+            rec[0] = mx; rec[1] = R; rec[2] = Tt; rec[3] = zm; rec[32] = D;
+        }
+    }
+    if (!last_block_done(&st->counter[2])) return;
+    __shared__ double fin[2][KMAX][4];
+    cand_finish_merge(p, gP, 1, fin);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double psi = fin[0][0][0], phi = fin[1][0][0];
+        st->psi[0] = psi;
+        st->phi[0] = phi;
+        st->zmink[0] = fin[1][0][3];
+        st->okk[0] = phi >= psi;
+        st->dpsi = fin[0][0][1];
+        st->dphi = fin[1][0][1];
+        if (!isfinite(psi) || !isfinite(phi) || !isfinite(st->dpsi) || !isfinite(st->dphi)) {
+            st->status = ST_NUMERIC;
+            st->numeric_bad = 2;
+        } else {
+            newton_decide(st, psi, phi, st->dpsi, st->dphi);
+        }
+        st->counter[2] = 0;
     }
 }
 
@@ -1354,67 +1508,19 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
             }
         }
     }
-    // warp merge in T (FP32 for the fast form), warps and blocks in FP64
-    __shared__ double bs[BLOCK / 32], bS[BLOCK / 32];
-    const double eds = st->eta * sd.sign;
-    for (int off = 16; off > 0; off >>= 1) {
-        T os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
-        lse_merge<T, T>(acc, os, oS, eta_sgn, sd.sign);
-    }
-    if ((threadIdx.x & 31) == 0) { bs[threadIdx.x >> 5] = (double)acc.s; bS[threadIdx.x >> 5] = (double)acc.S; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Lse<double> q{0.0, 0.0};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge<T, double>(q, bs[w], bS[w], eds, sd.sign);
-        double *rec = p.part_row + (size_t)blockIdx.x * REC;
-        rec[2 * s] = q.s; rec[2 * s + 1] = q.S;
-        rec[2 * (1 - s)] = 0.0; rec[2 * (1 - s) + 1] = 0.0;
-    }
-    // two-level completion (see k_cand): group merge, then the last group finalises
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    const int grp = blockIdx.x / GRP, ngrp = (gridDim.x + GRP - 1) / GRP;
-    const int gsz = min(GRP, (int)gridDim.x - grp * GRP);
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->grp_counter[1][grp], 1u) == (unsigned)(gsz - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double *grec = p.part_grp + (size_t)GRP_MAX * REC;   // row 1 of the group records
-    if (threadIdx.x < 32) {
-        const int ss = threadIdx.x >> 4, ln = threadIdx.x & 15;
-        const int sg = p.side[ss].sign;
-        Lse<double> q{0.0, 0.0};
-        if (ln < gsz) {
-            const double *rec = p.part_row + (size_t)(grp * GRP + ln) * REC;
-            q.s = rec[2 * ss];
-            q.S = rec[2 * ss + 1];
+    // block record in T, then one completion level: the last block merges the
+    // records of both sides (warp per side) and runs the stopping test
+    lse_block_record(p, acc, eta_sgn, sd.sign);
+    if (last_block_done(&st->counter[3])) {
+        if (threadIdx.x == 0) {
+            st->iter += 1;
+            st->pending = 1;
+            st->alpha_prev = alpha;
         }
-        const double e2 = st->eta * sg;
-        for (int off = 8; off > 0; off >>= 1) {
-            double os = __shfl_xor_sync(0xffffffffu, q.s, off), oS = __shfl_xor_sync(0xffffffffu, q.S, off);
-            lse_merge<T, double>(q, os, oS, e2, sg);
-        }
-        if (ln == 0) {
-            grec[(size_t)grp * REC + 2 * ss] = q.s;
-            grec[(size_t)grp * REC + 2 * ss + 1] = q.S;
-        }
+        __syncthreads();
+        finalize_reductions(p, gP, gridDim.x, 0, false, alpha);
+        if (threadIdx.x == 0) st->counter[3] = 0;
     }
-    if (threadIdx.x == 0) st->grp_counter[1][grp] = 0;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->counter[3], 1u) == (unsigned)(ngrp - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) {
-        st->iter += 1;
-        st->pending = 1;
-        st->alpha_prev = alpha;
-    }
-    __syncthreads();
-    finalize_reductions(p, grec, ngrp, 0, false, alpha);
-    if (threadIdx.x == 0) st->counter[3] = 0;
 }
 
 // apply a pending x += alpha d
@@ -1463,8 +1569,8 @@ static int grid_for(int64_t n, int cap) {
 // Blocks of a candidate pass are split between the two sides in proportion to
 // their work: the candidate arithmetic (K exp terms per row, weighed as 4
 // gathers each) plus, on the first pass, one unit per gathered entry of A d.
-template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC, bool first = true) {
-    int total = p.grid_row;
+template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC, bool first = true, int total = 0) {
+    if (total <= 0) total = p.grid_row;
     auto work = [&](const Side<T> &s) -> double {
         if (s.rv.kind == RK_DENSE1 || s.rv.kind == RK_NONE) return 0.0;
         double w = 4.0 * KMAX * (double)s.m;
@@ -1557,12 +1663,17 @@ template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s, int cond_on,
-                        cudaGraphConditionalHandle cond) {
+template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s) {
     int gP, gC;
     split_rows(p, &gP, &gC, false);
-    k_cand<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, external, cond_on, cond);
+    k_cand<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, external);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_cand_newton(const Problem<T> &p, cudaStream_t s) {
+    int gP, gC;
+    split_rows(p, &gP, &gC, false, p.grid_newton);
+    k_cand_newton<T><<<gP + gC, BLOCK, 0, s>>>(p, gP);
     return cudaGetLastError();
 }
 
@@ -1636,6 +1747,12 @@ template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_
     return 0;
 }
 
+template <class T> int newton_blocks_per_sm() {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cand_newton<T>, BLOCK, 0);
+    return a > 0 ? a : 1;
+}
+
 template <class T> int spmv_blocks_per_sm() {
     int a = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spmv<T>, BLOCK, 0);
@@ -1648,7 +1765,9 @@ template <class T> int spmv_blocks_per_sm() {
     template cudaError_t launch_rows_eval<T>(const Problem<T> &, cudaStream_t);                                \
     template cudaError_t launch_dir<T>(const Problem<T> &, int, cudaStream_t);                                 \
     template cudaError_t launch_spmv<T>(const Problem<T> &, cudaStream_t);                                     \
-    template cudaError_t launch_cand<T>(const Problem<T> &, int, cudaStream_t, int, cudaGraphConditionalHandle); \
+    template cudaError_t launch_cand<T>(const Problem<T> &, int, cudaStream_t);                                \
+    template cudaError_t launch_cand_newton<T>(const Problem<T> &, cudaStream_t);                              \
+    template int newton_blocks_per_sm<T>();                                                                     \
     template cudaError_t launch_update<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_flush<T>(const Problem<T> &, cudaStream_t);                                    \
     template cudaError_t launch_search_begin<T>(const Problem<T> &, cudaStream_t);                             \
