@@ -327,6 +327,13 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
  * otherwise host arrays of `count` entries. */
 int mwu_solve_batch(mwu_ctx *ctx, double *objective, int64_t *iters, mwu_result *total);
 
+/* ------------------------------------------------------------ diagnostics */
+/* u[i] = 1 - e^{-b[i]} for b[i] >= 0, by the same device function the
+ * candidate passes use (FP32).  b, u: device arrays of n floats; stream:
+ * cudaStream_t or NULL; the call waits for the result.  MWU_ERR_INVALID on
+ * NULL arrays or n < 0, MWU_ERR_CUDA on a launch error. */
+int mwu_diag_one_minus_exp_neg(const float *b, float *u, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -685,7 +685,7 @@ static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev, bool loop = fa
         if (ev && (e = cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_dir(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = launch_spmv(p, c->stream)) != cudaSuccess) return e;
+        if ((e = launch_spmv(p, c->stream, dir_fuses_dz(p, 0))) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = enqueue_search(c, p, loop)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[3], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
@@ -776,7 +776,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[0], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 0, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[1], c->stream));
-            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_spmv(p, c->stream); }));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_spmv(p, c->stream, dir_fuses_dz(p, 0)); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[2], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
             c->launches += 3;

@@ -169,7 +169,13 @@ template <class T> cudaError_t launch_x_init(const Problem<T> &p, cudaStream_t s
 template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, int fp64, cudaStream_t s);
 template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s);             // a1-a3 at a new x
 template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s);      // a4-a5 (+ fused x update)
-template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s);                  // a6: dy = Pd, dz = Cd
+// a6: dy = Pd, dz = Cd; skip_c: dz was already written by the direction kernel
+template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s, int skip_c = 0);
+// true when launch_dir(p, keep_gh) runs the edge-pair direction kernel, which also writes dz = Wd
+template <class T> bool dir_fuses_dz(const Problem<T> &p, int keep_gh) {
+    return !keep_gh && p.side[0].cv.kind == CK_FIXED1 && p.side[1].cv.kind == CK_HALF1 &&
+           p.side[1].rv.kind == RK_PAIRSUM;
+}
 template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s);
 // one-candidate Newton pass (captured iterations): returns at once unless the search is in its Newton phase
 template <class T> cudaError_t launch_cand_newton(const Problem<T> &p, cudaStream_t s);    // a7: one candidate pass

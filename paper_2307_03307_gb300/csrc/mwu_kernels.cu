@@ -29,8 +29,25 @@ namespace mwu {
 // ---------------------------------------------------------------- math
 __device__ __forceinline__ float t_exp(float x) { return expf(x); }
 __device__ __forceinline__ double t_exp(double x) { return exp(x); }
-__device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
-__device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
+
+// u = 1 - e^{-b} for b >= 0 (the candidate factor of the T sums).  FP32: the
+// Taylor series b - b^2/2! + ... - b^8/8! in Horner form for b <= 1/4, whose
+// truncation error is below b^9/9! < 1e-10 b; 1 - e^{-b} from the fast
+// exponential above, where u >= 0.22 keeps the cancellation below 2^-21
+// relative.  FP64: -expm1(-b).
+__device__ __forceinline__ float one_minus_exp_neg(float b) {
+    b = fmaxf(b, 0.0f);
+    float t = 1.0f - b * (1.0f / 8.0f);
+    t = 1.0f - b * (1.0f / 7.0f) * t;
+    t = 1.0f - b * (1.0f / 6.0f) * t;
+    t = 1.0f - b * (1.0f / 5.0f) * t;
+    t = 1.0f - b * (1.0f / 4.0f) * t;
+    t = 1.0f - b * (1.0f / 3.0f) * t;
+    t = 1.0f - b * 0.5f * t;
+    const float series = b * t;
+    return b <= 0.25f ? series : 1.0f - __expf(-b);
+}
+__device__ __forceinline__ double one_minus_exp_neg(double b) { return -expm1(-b); }
 template <class T> __device__ __forceinline__ T exp_T(double x) { return t_exp((T)x); }
 __device__ __forceinline__ float t_log(float x) { return logf(x); }
 __device__ __forceinline__ double t_log(double x) { return log(x); }
@@ -656,19 +673,25 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
     const int64_t E = p.n >> 1;
     const int2 *ends = reinterpret_cast<const int2 *>(P.cv.idx);
     long long npos = 0;
-    // one edge per lane and iteration, two iterations' loads in flight
+    // Per slot the test and the step need only r = g/h = (fp/fc) w_p[u] / w_c[e]
+    // = (fp/fc) exp(eta (y_u - s_p) + eta (z_e - s_c)) (times rdiv_e / rdiv_u
+    // with bounds): one exponential per slot and no division.
+    const T kgh = fp / fc;
+    const double scale_c = st->scale[1];
     auto one_edge = [&](int64_t e, const int2 uv, T x0, T x1, T yu, T yv, T ze) {
-        T wu = t_exp(eta * (yu - sp));
-        T wv = t_exp(eta * (yv - sp));
-        if (P.rv.rdiv) { wu /= (T)P.rv.rdiv[uv.x]; wv /= (T)P.rv.rdiv[uv.y]; }
-        T wc = t_exp(-eta * (ze - sc));
-        if (C.rv.rdiv) wc /= (T)C.rv.rdiv[e];
-        const T h = wc * fc;
-        const T g0 = wu * fp, g1 = wv * fp;
-        const T d0 = (g0 < thr * h) ? cd * (T(1) - g0 / h) * x0 : T(0);
-        const T d1 = (g1 < thr * h) ? cd * (T(1) - g1 / h) * x1 : T(0);
+        const T bz = eta * (ze - sc);
+        T r0 = kgh * t_exp(eta * (yu - sp) + bz);
+        T r1 = kgh * t_exp(eta * (yv - sp) + bz);
+        if (P.rv.rdiv || C.rv.rdiv) {
+            const T re = C.rv.rdiv ? (T)C.rv.rdiv[e] : T(1);
+            r0 *= re / (P.rv.rdiv ? (T)P.rv.rdiv[uv.x] : T(1));
+            r1 *= re / (P.rv.rdiv ? (T)P.rv.rdiv[uv.y] : T(1));
+        }
+        const T d0 = (r0 < thr) ? cd * (T(1) - r0) * x0 : T(0);
+        const T d1 = (r1 < thr) ? cd * (T(1) - r1) * x1 : T(0);
         if (sizeof(T) == 4) reinterpret_cast<float2 *>(p.d)[e] = make_float2((float)d0, (float)d1);
         else { p.d[2 * e] = d0; p.d[2 * e + 1] = d1; }
+        C.dv[e] = (d0 + d1) * row_coef(C, e, scale_c);   // a6 for W: dz_e = d_{2e} + d_{2e+1}
         npos += (d0 > T(0)) + (d1 > T(0));
     };
     auto load_x = [&](int64_t e, T &x0, T &x1) {
@@ -688,19 +711,24 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
             }
         }
     };
+    // four edges per lane and iteration: the streamed loads of all four are
+    // issued before the dependent gathers of y
+    constexpr int U = 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (; e + stride < E; e += 2 * stride) {
-        const int64_t f = e + stride;
-        T xa0, xa1, xb0, xb1;
-        load_x(e, xa0, xa1);
-        load_x(f, xb0, xb1);
+    for (; e + (U - 1) * stride < E; e += U * stride) {
+        T x0[U], x1[U], z[U];
+        int2 uv[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) load_x(e + j * stride, x0[j], x1[j]);
         if (!running) continue;
-        const int2 ua = ends[e], ub = ends[f];
-        const T ya = P.v[ua.x], yb = P.v[ua.y], yc = P.v[ub.x], yd = P.v[ub.y];
-        const T za = C.v[e], zb = C.v[f];
-        one_edge(e, ua, xa0, xa1, ya, yb, za);
-        one_edge(f, ub, xb0, xb1, yc, yd, zb);
+#pragma unroll
+        for (int j = 0; j < U; ++j) { uv[j] = ends[e + j * stride]; z[j] = C.v[e + j * stride]; }
+        T yu[U], yv[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) { yu[j] = P.v[uv[j].x]; yv[j] = P.v[uv[j].y]; }
+#pragma unroll
+        for (int j = 0; j < U; ++j) one_edge(e + j * stride, uv[j], x0[j], x1[j], yu[j], yv[j], z[j]);
     }
     for (; e < E; e += stride) {
         T x0, x1;
@@ -799,9 +827,9 @@ __device__ __forceinline__ void cand_push_m(CandAcc<T> &c, const T *ca, const T 
         }
     }
     T b = ca[0] * dv;
-    T u = -t_expm1(-b);
+    T u = one_minus_exp_neg(b);
     T ud = T(0);
-    if (MODE == 1) ud = -t_expm1(-cd * dv);
+    if (MODE == 1) ud = one_minus_exp_neg(cd * dv);
     T A = T(0);
     if (SGN < 0) A = fast_exp(a);
     // rescale only when some lane of the warp meets a new maximum
@@ -814,7 +842,7 @@ __device__ __forceinline__ void cand_push_m(CandAcc<T> &c, const T *ca, const T 
                 b = ca[k] * dv;
                 if (MODE == 0) u = u * (T(2) - u);
                 else if (MODE == 1) u = u + ud * (T(1) - u);
-                else u = -t_expm1(-b);
+                else u = one_minus_exp_neg(b);
             }
             const T x = SGN > 0 ? a + b : a - b;
             const bool up = x > c.mx[k];
@@ -1207,11 +1235,12 @@ __device__ __forceinline__ void spmv_side(const Problem<T> &p, int s, const T *_
 // partials are added per row in a fixed order by the last block, so the
 // result does not depend on scheduling.
 template <class T>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<T> p, const T *__restrict__ in, int to_v) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<T> p, const T *__restrict__ in, int to_v,
+                                                                         int skip_c) {
     DevState *st = p.st;
     if (!to_v && st->status != ST_RUNNING) return;
     spmv_side(p, 0, in, to_v);
-    spmv_side(p, 1, in, to_v);
+    if (!skip_c) spmv_side(p, 1, in, to_v);
     if (p.side[0].rv.n_seg == 0 && p.side[1].rv.n_seg == 0) return;
     __shared__ bool s_last;
     __threadfence();
@@ -1613,7 +1642,7 @@ template <class T> static int spmv_grid(const Problem<T> &p) {
 template <class T> static cudaError_t rows_at_x(const Problem<T> &p, int nb_var, cudaStream_t s) {
     const int gs = spmv_grid(p);
     if (gs > 0) {
-        k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.x, 1);
+        k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.x, 1, 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1644,7 +1673,7 @@ template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_
 }
 
 template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s) {
-    if (!keep_gh && p.side[0].cv.kind == CK_FIXED1 && p.side[1].cv.kind == CK_HALF1) {
+    if (dir_fuses_dz(p, keep_gh)) {
         int g = (int)std::max<int64_t>(1, std::min<int64_t>((p.n / 2 + BLOCK - 1) / BLOCK, p.grid_var));
         k_dir_pairs<T><<<g, BLOCK, 0, s>>>(p);
         return cudaGetLastError();
@@ -1656,10 +1685,10 @@ template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cuda
     return cudaGetLastError();
 }
 
-template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s) {
+template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s, int skip_c) {
     const int gs = spmv_grid(p);
     if (gs == 0) return cudaSuccess;
-    k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.d, 0);
+    k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.d, 0, skip_c);
     return cudaGetLastError();
 }
 
@@ -1764,7 +1793,7 @@ template <class T> int spmv_blocks_per_sm() {
     template cudaError_t launch_x_set<T>(const Problem<T> &, const void *, int, cudaStream_t);                 \
     template cudaError_t launch_rows_eval<T>(const Problem<T> &, cudaStream_t);                                \
     template cudaError_t launch_dir<T>(const Problem<T> &, int, cudaStream_t);                                 \
-    template cudaError_t launch_spmv<T>(const Problem<T> &, cudaStream_t);                                     \
+    template cudaError_t launch_spmv<T>(const Problem<T> &, cudaStream_t, int);                                \
     template cudaError_t launch_cand<T>(const Problem<T> &, int, cudaStream_t);                                \
     template cudaError_t launch_cand_newton<T>(const Problem<T> &, cudaStream_t);                              \
     template int newton_blocks_per_sm<T>();                                                                     \
@@ -1938,4 +1967,21 @@ extern "C" int mwu_candidates_static(const float *v, const float *dv, int64_t m,
         if (vmin) vmin[k] = out[k][1];
     }
     return MWU_OK;
+}
+
+// ---------------------------------------------------------------- diagnostics
+namespace mwu {
+__global__ void k_diag_ome(const float *b, float *u, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = one_minus_exp_neg(b[i]);
+}
+}   // namespace mwu
+
+extern "C" int mwu_diag_one_minus_exp_neg(const float *b, float *u, int64_t n, void *stream) {
+    if (!b || !u || n < 0) return MWU_ERR_INVALID;
+    if (n == 0) return MWU_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mwu::k_diag_ome<<<grid, 256, 0, (cudaStream_t)stream>>>(b, u, n);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? MWU_OK : MWU_ERR_CUDA;
 }

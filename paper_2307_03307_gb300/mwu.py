@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "mwu_potential": (C.c_int, [V, V, P(D), V, V, V]),
         "mwu_candidates_static": (C.c_int, [V, V, I64, I32, D, D, D, P(D), I32, P(D), P(D), V]),
         "mwu_create_batch": (C.c_int, [I32, P(mwu_matrix), P(mwu_options), P(V)]),
+        "mwu_diag_one_minus_exp_neg": (C.c_int, [V, V, I64, V]),
         "mwu_solve_batch": (C.c_int, [V, P(D), P(I64), P(mwu_result)]),
     }
     for name, (res, args) in sig.items():
@@ -128,7 +129,7 @@ def exported_symbols():
             "mwu_set_x", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_eval_newton", "mwu_search",
             "mwu_solve",
             "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_potential", "mwu_candidates_static",
-            "mwu_create_batch", "mwu_solve_batch"]
+            "mwu_create_batch", "mwu_solve_batch", "mwu_diag_one_minus_exp_neg"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -256,6 +257,16 @@ def mwu_eval_newton(ctx, alpha):
     out = (C.c_double * 4)()
     _check(ctx, load().mwu_eval_newton(ctx, float(alpha), out))
     return tuple(out)
+
+
+def mwu_diag_one_minus_exp_neg(b, stream=None):
+    """1 - exp(-b) on the device by the library's candidate-pass function (b: CUDA float32 tensor)."""
+    import torch
+    u = torch.empty_like(b)
+    if stream is None:
+        stream = _current_stream()
+    _check(None, load().mwu_diag_one_minus_exp_neg(_ptr(b), _ptr(u), b.numel(), stream))
+    return u
 
 
 def mwu_search(ctx):

@@ -398,3 +398,18 @@ def test_host_and_device_inputs_agree(M, wls):
         finally:
             M.mwu_destroy(ctx)
     assert np.array_equal(xs[0], xs[1])
+
+
+def test_one_minus_exp_neg_against_cuda_expm1(M):
+    """The candidate passes' own 1 - e^{-b} (Taylor series below 1/4, the fast
+    exponential above) against FP64 expm1 and CUDA's FP32 expm1f (via torch):
+    relative error below 2^-20 over b in [0, 100]."""
+    b = torch.cat([torch.zeros(1), torch.logspace(-12, 2, 200001), torch.linspace(0.2, 0.3, 100001)]).float().cuda()
+    u = M.mwu_diag_one_minus_exp_neg(b)
+    want = -torch.expm1(-b.double())
+    rel = ((u.double() - want).abs() / want.clamp_min(1e-300))[1:]
+    assert float(u[0]) == 0.0
+    assert float(rel.max()) < 2.0 ** -20, float(rel.max())
+    f32 = -torch.expm1(-b)
+    rel32 = ((u - f32).abs() / f32.clamp_min(1e-38))[1:]
+    assert float(rel32.max()) < 2.0 ** -20
