@@ -3,8 +3,9 @@
 
 Workload (default): the densest-subgraph LP (Charikar dual, W z >= 1, O z <= D)
 on a synthetic R-MAT graph of scale 18, edge factor 16, (a,b,c) = (.57,.19,.19),
-seed 2, eps = 0.1, FP32 vectors with FP64 reductions, K = 8 candidates per
-pass.  One step is one complete solve (search on D, every probe's MWU
+seed 2, eps = 0.1, FP32 vectors with FP64 reductions, Newton's step-size
+search of Sec. 4.2 (--step kary: K = 8 candidates per pass).  One step is one
+complete solve (search on D, every probe's MWU
 iterations with their step-size searches) to a (1+0.1)-relative certified
 objective, with the problem already resident in HBM.
 
@@ -44,8 +45,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=18)
     ap.add_argument("--seed", type=int, default=2)
-    ap.add_argument("--step", default="kary", choices=["kary", "newton"],
+    ap.add_argument("--step", default="newton", choices=["kary", "newton"],
                     help="step-size search: K candidates per pass (Alg. 3 generalised) or Newton (Sec. 4.2)")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every kernel from the host instead of replaying captured iterations (for "
+                         "profilers that cannot see the kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -124,18 +128,19 @@ def measured_peaks():
 def algorithmic_bytes(N, E):
     """Algorithmic bytes per launch of each kernel class on the densest-subgraph LP.
 
-    FP32 values and int32 indices, every referenced array element counted once:
-      dir        x read + write, d_old read (deferred update), d write, endpoint
-                 index per slot (2E slots), z (one per edge), y (one per vertex)
-      spmv       dy = (O/D) d: rowptr, slot index and d per slot, dy written;
-                 dz = W d: dz written (d counted once)
-      cand       y, dy, z, dz read (one candidate pass)
+    FP32 values and int32 indices, every referenced array element counted once
+    (n = 2E variable slots):
+      dir        x read + written, d of the previous step read (deferred update),
+                 d written, endpoint pair per edge, z per edge, y per vertex,
+                 dz = W d written (fused)
+      spmv       dy = (O/D) d: rowptr, slot index and d per slot, dy written
+      cand       y, dy, z, dz read (one candidate pass, Newton or K-candidate)
       update     y, z read + written, dy, dz read
     """
     n = 2 * E
     return {
-        "dir": 4 * (4 * n) + 4 * n + 4 * E + 4 * N,
-        "spmv": 4 * (N + 1) + 4 * n + 4 * n + 4 * N + 4 * E,
+        "dir": 8 * n + 4 * n + 4 * n + 8 * E + 4 * E + 4 * N + 4 * E,
+        "spmv": 4 * (N + 1) + 4 * n + 4 * n + 4 * N,
         "cand": 8 * N + 8 * E,
         "update": 12 * N + 12 * E,
     }
@@ -161,7 +166,8 @@ def run_ours(args):
     kind, P, C, obj = lpspec.from_workload(wl)
     stream = torch.cuda.current_stream()
     step = M.STEP_NEWTON if args.step == "newton" else M.STEP_KARY
-    ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, timing=1, step=step)
+    ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, timing=0 if args.eager else 1, step=step,
+                       use_graph=0 if args.eager else 1)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -204,12 +210,13 @@ def run_ours(args):
     # roofline of the dominant kernel class (device time from the events captured in the graph)
     ab = algorithmic_bytes(N, E)
     per_class_ms = {"dir": tim["dir_ms"], "spmv": tim["spmv_ms"], "cand": tim["cand_ms"], "update": tim["update_ms"]}
+    timed_classes = sum(per_class_ms.values()) > 0.0     # no event times in --eager runs
     dom = max(per_class_ms, key=lambda k: per_class_ms[k])
     nit = max(1, tim["iters"])
     # launches per iteration: one per class, the candidate passes as counted by the library
     per_launch = {"dir": nit, "spmv": nit, "cand": max(1, tim["cand_passes"]), "update": nit}
     avg_ms = per_class_ms[dom] / per_launch[dom]
-    achieved = ab[dom] / (avg_ms / 1e3) / 1e9
+    achieved = ab[dom] / (avg_ms / 1e3) / 1e9 if timed_classes else None
     peak, peak_src = measured_peaks()
     traffic = None
     try:
@@ -234,7 +241,8 @@ def run_ours(args):
         "clocks": clk,
         "roofline": {"bound": "hbm", "kernel": {"dir": "k_dir_pairs", "spmv": "k_spmv",
                                                  "cand": "k_cand / k_cand_newton (one pass)", "update": "k_update"}[dom],
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved is not None else None,
                      "traffic": traffic, "algorithmic_bytes_per_launch": ab[dom], "avg_launch_ms": avg_ms,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6800 GB/s",
                      "per_class_ms_per_iter": {k: v / nit for k, v in per_class_ms.items()},
@@ -280,7 +288,7 @@ def run_ours(args):
                        "seconds_per_step": statistics.mean(e2e_s)}
 
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(wl, args.cpu_seconds)
+        line["cpu_baseline"] = oracle_sample(wl, args.cpu_seconds, args.step)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -288,7 +296,7 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(wl, seconds):
+def oracle_sample(wl, seconds, step):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload:
     MWU iterations of one probe (D = 1.5 |E|/|V|) run until `seconds` elapse."""
     import numpy as np
@@ -311,13 +319,13 @@ def oracle_sample(wl, seconds):
             raise Stop()
 
     try:
-        om.mwu((O / D).tocsr(), Wm, wl.eps, on_iter=on_iter)
+        om.mwu((O / D).tocsr(), Wm, wl.eps, on_iter=on_iter, step=step)
     except Stop:
         pass
     dt = time.perf_counter() - t0
     its = max(count[0], 1)
     return {"value": g.m * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{its} MWU iterations (K=8 search) of one densest probe D=1.5|E|/|V| on the same graph, "
+            "sample": f"{its} MWU iterations ({step} search) of one densest probe D=1.5|E|/|V| on the same graph, "
                       f"{dt:.1f} s, numpy/scipy single thread",
             "host_cpus": os.cpu_count()}
 
@@ -341,7 +349,7 @@ def run_reference(args):
     times = []
 
     def one_iter():
-        r = om.mwu(P, Wm, wl.eps, max_iter=1, x0=state["x"])
+        r = om.mwu(P, Wm, wl.eps, max_iter=1, x0=state["x"], step=args.step)
         state["x"] = r.x
         return r.iters
 
@@ -356,9 +364,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"densest-rmat{args.scale}", "vertices": g.n, "edges": g.m, "eps": wl.eps},
+            "config": {"workload": f"densest-rmat{args.scale}", "vertices": g.n, "edges": g.m, "eps": wl.eps,
+                       "step": args.step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one MWU iteration (K=8 search) per step of a densest probe at D=1.5|E|/|V|"},
+                             "sample": f"one MWU iteration ({args.step} search, cold start) per step of a densest "
+                                       "probe at D=1.5|E|/|V|"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

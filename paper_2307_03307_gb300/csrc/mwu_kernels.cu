@@ -348,9 +348,37 @@ __device__ T heavy_col_gather(const ColView &cv, int64_t i, const F &w, T *smem)
 // (A x)_j = coef_j * sum_k val_jk x_k with coef_j = scale / rdiv_j; the scale
 // (1/M of the objective row, 1/D of O) lives in device state so that a captured
 // iteration stays valid when the probe target changes.
-template <class T> __device__ __forceinline__ T row_coef(const Side<T> &sd, int64_t j, double scale) {
-    T c = (T)scale;
-    if (sd.rv.rdiv) c /= (T)sd.rv.rdiv[j];
+// (scale arrives in T: GB300 runs double-to-float conversions on its FP64
+// pipe, so the callers convert once per thread, not once per element)
+template <class T> __device__ __forceinline__ T row_coef(const Side<T> &sd, int64_t j, T scale) {
+    return sd.rv.rdiv ? scale / (T)sd.rv.rdiv[j] : scale;
+}
+
+// T copies of the device-state scalars of the sweep kernels, made once per
+// block by one thread: GB300 runs FP64 arithmetic and double/float
+// conversions on a narrow pipe, so no thread repeats them.  Every thread of
+// the block must call it (it synchronises).
+template <class T> struct SweepConsts {
+    T eta, s0, s1, fp, fc, kgh, cd, thr, scale0, scale1, alpha_prev, alpha_acc;
+};
+template <class T> __device__ __forceinline__ SweepConsts<T> sweep_consts(const DevState *st) {
+    __shared__ SweepConsts<T> c;
+    if (threadIdx.x == 0) {
+        const double fp = st->scale[0] / st->S[0], fc = st->scale[1] / st->S[1];
+        c.eta = (T)st->eta;
+        c.s0 = (T)st->s[0];
+        c.s1 = (T)st->s[1];
+        c.fp = (T)fp;
+        c.fc = (T)fc;
+        c.kgh = (T)(fp / fc);
+        c.cd = (T)st->c_d;
+        c.thr = (T)(1.0 - st->grad_tol);   // gradient test threshold on g/h
+        c.scale0 = (T)st->scale[0];
+        c.scale1 = (T)st->scale[1];
+        c.alpha_prev = st->pending ? (T)st->alpha_acc : T(0);
+        c.alpha_acc = (T)st->alpha_acc;
+    }
+    __syncthreads();
     return c;
 }
 
@@ -362,9 +390,19 @@ __global__ void __launch_bounds__(BLOCK) k_x_prep(Problem<T> p, const void *xin,
     const Side<T> &P = p.side[0];
     const double eps = p.st->eps;
     double dot[2] = {0.0, 0.0};
+    // implicit column views without bounds (and a dense row without weights)
+    // have every column norm equal to the side's scale: x0 is one value,
+    // computed once per thread
+    const ColView &cv0 = P.cv;
+    const bool uniform = !cv0.rdiv && (cv0.kind == CK_FIXED1 || cv0.kind == CK_FIXED2 || cv0.kind == CK_HALF1 ||
+                                       (cv0.kind == CK_DENSE1 && !cv0.cvec));
+    const double s0 = p.st->scale[0] > 0.0 ? p.st->scale[0] : 1.0;
+    const T x_uniform = (T)(eps / ((double)p.n * s0));
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
         T xi;
-        if (mode == 0) {
+        if (mode == 0 && uniform) {
+            xi = x_uniform;
+        } else if (mode == 0) {
             double cm = 0.0;
             const ColView &cv = P.cv;
             switch (cv.kind) {
@@ -556,17 +594,15 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
     DevState *st = p.st;
     if (!potential_mode && st->status != ST_RUNNING && !st->pending) return;
     const bool running = potential_mode || st->status == ST_RUNNING;
-    const T alpha_prev = st->pending ? (T)st->alpha_acc : T(0);
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const T alpha_prev = K0.alpha_prev;
     const Side<T> &P = p.side[0];
     const Side<T> &C = p.side[1];
-    WeightFn<T> wp{P.v, P.rv.rdiv, (T)st->eta, (T)st->s[0]};
-    WeightFn<T> wc{C.v, C.rv.rdiv, (T)(-st->eta), (T)st->s[1]};
-    const T fp = (T)(st->scale[0] / st->S[0]);
-    const T fc = (T)(st->scale[1] / st->S[1]);
-    const T cd = (T)st->c_d;
-    const T thr = (T)(1.0 - st->grad_tol);   // gradient test threshold on g/h
-    long long npos = 0;
-    double dense_dot[2] = {0.0, 0.0};
+    WeightFn<T> wp{P.v, P.rv.rdiv, K0.eta, K0.s0};
+    WeightFn<T> wc{C.v, C.rv.rdiv, -K0.eta, K0.s1};
+    const T fp = K0.fp, fc = K0.fc, cd = K0.cd, thr = K0.thr;
+    int npos = 0;   // positives of this thread
+    T dense_dot[2] = {T(0), T(0)}, dense_cmp[2] = {T(0), T(0)};   // compensated per thread
 
     auto finish = [&](int64_t i, T sg, T sh) {
         T xi = p.x[i];
@@ -588,7 +624,7 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
         npos += (di > T(0));
         for (int s = 0; s < 2; ++s)
             if (p.side[s].cv.kind == CK_DENSE1)
-                dense_dot[s] += (double)((p.side[s].cv.cvec ? (T)p.side[s].cv.cvec[i] : T(1)) * di);
+                kahan_add(dense_dot[s], dense_cmp[s], (p.side[s].cv.cvec ? (T)p.side[s].cv.cvec[i] : T(1)) * di);
     };
 
     // heavy variables (long CSR columns): whole block
@@ -625,8 +661,8 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
     if (potential_mode) return;
     // block partials: n_pos, dense dots
     double np = block_sum((double)npos, smd);
-    double d0 = block_sum(dense_dot[0], smd);
-    double d1 = block_sum(dense_dot[1], smd);
+    double d0 = block_sum((double)dense_dot[0] - (double)dense_cmp[0], smd);
+    double d1 = block_sum((double)dense_dot[1] - (double)dense_cmp[1], smd);
     if (threadIdx.x == 0) {
         double *rec = p.part_var + (size_t)blockIdx.x * REC;
         rec[0] = np; rec[1] = d0; rec[2] = d1;
@@ -662,22 +698,19 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
     DevState *st = p.st;
     if (st->status != ST_RUNNING && !st->pending) return;
     const bool running = st->status == ST_RUNNING;
-    const T alpha_prev = st->pending ? (T)st->alpha_acc : T(0);
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const T alpha_prev = K0.alpha_prev;
     const Side<T> &P = p.side[0];
     const Side<T> &C = p.side[1];
-    const T eta = (T)st->eta, sp = (T)st->s[0], sc = (T)st->s[1];
-    const T fp = (T)(st->scale[0] / st->S[0]);
-    const T fc = (T)(st->scale[1] / st->S[1]);
-    const T cd = (T)st->c_d;
-    const T thr = (T)(1.0 - st->grad_tol);
+    const T eta = K0.eta, sp = K0.s0, sc = K0.s1, cd = K0.cd, thr = K0.thr;
     const int64_t E = p.n >> 1;
     const int2 *ends = reinterpret_cast<const int2 *>(P.cv.idx);
-    long long npos = 0;
+    int npos = 0;   // positives of this thread
     // Per slot the test and the step need only r = g/h = (fp/fc) w_p[u] / w_c[e]
     // = (fp/fc) exp(eta (y_u - s_p) + eta (z_e - s_c)) (times rdiv_e / rdiv_u
     // with bounds): one exponential per slot and no division.
-    const T kgh = fp / fc;
-    const double scale_c = st->scale[1];
+    const T kgh = K0.kgh;
+    const T scale_c = K0.scale1;
     auto one_edge = [&](int64_t e, const int2 uv, T x0, T x1, T yu, T yv, T ze) {
         const T bz = eta * (ze - sc);
         T r0 = kgh * t_exp(eta * (yu - sp) + bz);
@@ -1148,14 +1181,12 @@ __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> 
 }
 
 template <class T>
-__device__ __forceinline__ void spmv_side(const Problem<T> &p, int s, const T *__restrict__ in, int to_v) {
-    const DevState *st = p.st;
+__device__ __forceinline__ void spmv_side(const Problem<T> &p, int s, const T *__restrict__ in, int to_v, T scale) {
     const int bid = blockIdx.x, nbs = gridDim.x;
     const Side<T> &sd = p.side[s];
     const RowView &rv = sd.rv;
     if (rv.kind == RK_DENSE1 || rv.kind == RK_NONE) return;
     T *out = to_v ? sd.v : sd.dv;
-    const double scale = st->scale[s];
     const int64_t m = sd.m;
     const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)nbs * blockDim.x;
@@ -1239,8 +1270,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<
                                                                          int skip_c) {
     DevState *st = p.st;
     if (!to_v && st->status != ST_RUNNING) return;
-    spmv_side(p, 0, in, to_v);
-    if (!skip_c) spmv_side(p, 1, in, to_v);
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    spmv_side(p, 0, in, to_v, K0.scale0);
+    if (!skip_c) spmv_side(p, 1, in, to_v, K0.scale1);
     if (p.side[0].rv.n_seg == 0 && p.side[1].rv.n_seg == 0) return;
     __shared__ bool s_last;
     __threadfence();
@@ -1255,7 +1287,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<
         const RowView &rv = sd.rv;
         if (rv.kind != RK_CSR) continue;
         T *out = to_v ? sd.v : sd.dv;
-        const double scale = st->scale[s];
+        const T scale = (T)st->scale[s];
         for (int i = threadIdx.x; i < rv.n_long; i += blockDim.x) {
             const int j = rv.long_rows[i];
             T sum = T(0);
@@ -1275,7 +1307,8 @@ __global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb
     const int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
     const int nbs = s == 0 ? gP : gridDim.x - gP;
     const Side<T> &sd = p.side[s];
-    const T eta_sgn = (T)(st->eta * sd.sign);
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const T eta_sgn = sd.sign > 0 ? K0.eta : -K0.eta;
     Lse<T> acc{T(0), T(0)};
     if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
         for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < sd.m; j += (int64_t)nbs * blockDim.x)
@@ -1307,12 +1340,14 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
     int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
     int nbs = s == 0 ? gP : gridDim.x - gP;
     const Side<T> &sd = p.side[s];
-    const T eta = (T)st->eta;
-    const T sh = (T)st->s[s];
+    __shared__ T s_eta, s_sh[2];
     if (threadIdx.x == 0) {
         s_sc.K = K;
         s_sc.mode = newton ? 3 : external ? 2 : (st->phase == PH_EXP ? 0 : st->phase == PH_REFINE ? 1 : 2);
         s_sc.cd = (T)((st->ub - st->lb) / (K + 1) * st->eta);
+        s_eta = (T)st->eta;
+        s_sh[0] = (T)st->s[0];
+        s_sh[1] = (T)st->s[1];
     }
     if (threadIdx.x < KMAX) {
         double a = threadIdx.x < K ? st->alpha[threadIdx.x] : 0.0;
@@ -1320,6 +1355,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
         s_sc.al[threadIdx.x] = (T)a;
     }
     __syncthreads();
+    const T eta = s_eta;
+    const T sh = s_sh[s];
     const CandSched<T> &sc = s_sc;
     CandAcc<T> acc;
     cand_init(acc, sd.sign);
@@ -1436,13 +1473,22 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(P
     const int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
     const int nbs = s == 0 ? gP : gridDim.x - gP;
     const Side<T> &sd = p.side[s];
-    const T eta = (T)st->eta;
-    const T sh = (T)st->s[s];
+    __shared__ T s_c[5];
+    if (threadIdx.x == 0) {
+        s_c[0] = (T)st->eta;
+        s_c[1] = (T)st->s[0];
+        s_c[2] = (T)st->s[1];
+        s_c[3] = (T)(st->alpha[0] * st->eta);
+        s_c[4] = (T)st->alpha[0];
+    }
+    __syncthreads();
+    const T eta = s_c[0];
+    const T sh = s_c[1 + s];
     CandSched<T> sc;
     sc.K = 1;
     sc.mode = 3;
-    sc.ca[0] = (T)(st->alpha[0] * st->eta);
-    sc.al[0] = (T)st->alpha[0];
+    sc.ca[0] = s_c[3];
+    sc.al[0] = s_c[4];
     sc.cd = T(0);
     CandAcc<T> acc;
     cand_init(acc, sd.sign);
@@ -1510,8 +1556,9 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
     int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
     int nbs = s == 0 ? gP : gridDim.x - gP;
     const Side<T> &sd = p.side[s];
-    T eta_sgn = (T)(st->eta * sd.sign);
-    const T a = (T)alpha;
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const T eta_sgn = sd.sign > 0 ? K0.eta : -K0.eta;
+    const T a = K0.alpha_acc;
     Lse<T> acc{T(0), T(0)};
     if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
         const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x, nthr = (int64_t)nbs * blockDim.x;
