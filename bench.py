@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--step", default="newton", choices=["kary", "newton"],
                     help="step-size search: K candidates per pass (Alg. 3 generalised) or Newton (Sec. 4.2)")
+    ap.add_argument("--workload", default="densest-rmat18",
+                    choices=["densest-rmat18", "bmatching-batch256", "domset-rmat20", "vcover-rmat24"],
+                    help="densest-rmat18 is the headline line; the others measure the remaining configurations")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying captured iterations (for "
                          "profilers that cannot see the kernel nodes of graphs with conditional nodes)")
@@ -59,6 +62,20 @@ def parse():
 
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def aggregate(dist, seconds, units, device):
+    """Whole-job throughput over N independent replicas: the slowest rank's time
+    and the work units of all ranks (no data-path collective; one all-reduce of
+    two numbers after the timed region).  dist = None: one process."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds, units], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
 
 
 # ------------------------------------------------------------------ clocks
@@ -199,12 +216,7 @@ def run_ours(args):
     iters = sum(r["iters"] for r in timed)
     units = float(E) * iters
     launches = sum(r["launches"] for r in timed)
-    if dist is not None:
-        t = torch.tensor([total_s, units], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_s, units = float(tmax[0]), float(t[1])
+    total_s, units = aggregate(dist, total_s, units, "cuda")
     value = units / total_s
 
     # roofline of the dominant kernel class (device time from the events captured in the graph)
@@ -283,7 +295,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             e2e_s.append(time.perf_counter() - t0)
             e2e_units += E * r["iters"]
-        line["e2e"] = {"value": e2e_units / sum(e2e_s), "unit": UNIT,
+        e2e_tot, e2e_units = aggregate(dist, sum(e2e_s), e2e_units, "cuda")
+        line["e2e"] = {"value": e2e_units / e2e_tot, "unit": UNIT,
                        "h2d_bytes_per_step": int(edges_h.numel() * 4), "d2h_bytes_per_step": int(x_h.numel() * 4),
                        "seconds_per_step": statistics.mean(e2e_s)}
 
@@ -373,10 +386,94 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_other(args):
+    """Measurement line of a configuration other than the headline one: the
+    256-instance b-matching batch (one step = the whole batch), dominating set
+    on R-MAT 20 over an explicit CSR, or vertex cover on R-MAT 24 (one step =
+    one solve).  Same timing rules; no roofline (the byte model above is the
+    densest LP's)."""
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2307_03307_gb300 import lpspec
+    from paper_2307_03307_gb300 import mwu as M
+    from graphgen import workloads as W
+    step = M.STEP_NEWTON if args.step == "newton" else M.STEP_KARY
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    batch = args.workload == "bmatching-batch256"
+    if batch:
+        insts = W.bmatching_batch(count=256, seed=4, device="cuda")
+        mats = [lpspec.from_workload(w)[1] for w in insts]
+        ctx = M.mwu_create_batch(mats, step=step)
+        edges = [w.graph.m for w in insts]
+        cfg = {"workload": "bmatching-batch256", "lp": "b-matching (Appendix A.1, lb = 0), 256 independent instances",
+               "instances": 256, "edges": int(sum(edges)), "eps": 0.1}
+
+        def solve():
+            obj, it, tot = M.mwu_solve_batch(ctx, len(mats))
+            return float(sum(e * i for e, i in zip(edges, it))), tot["iters"], tot["probes"]
+    else:
+        wl = W.domset(20, seed=3, device="cuda") if args.workload == "domset-rmat20" else W.vcover(24, seed=5, device="cuda")
+        kind, P, C, obj = lpspec.from_workload(wl)
+        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step)
+        E = wl.graph.m
+        cfg = {"workload": args.workload, "lp": {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
+                                                 "vcover-rmat24": "vertex cover, M^T x >= 1 implicit"}[args.workload],
+               "vertices": wl.graph.n, "edges": E, "eps": wl.eps}
+
+        def solve():
+            r = M.mwu_solve(ctx)
+            return float(E) * r["iters"], r["iters"], r["probes"]
+    for _ in range(args.warmup):
+        solve()
+    clocks = ClockSampler(local_rank)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    out = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        out.append(solve())
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
+    total_s, units = aggregate(dist, sum(step_ms) / 1e3, sum(o[0] for o in out), "cuda")
+    cfg.update({"step": args.step, "precision": "f32 vectors, f64 reductions",
+                "l2": "flushed (512 MB write) between steps", "parallelism": "replicas" if world > 1 else "single"})
+    line = {"metric": METRIC, "value": units / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "time_to_approx_s": statistics.mean(step_ms) / 1e3,
+            "iters_per_step": sum(o[1] for o in out) / args.steps,
+            "probes_per_step": sum(o[2] for o in out) / args.steps,
+            "clocks": clk, "roofline": None}
+    M.mwu_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "densest-rmat18":
+        run_other(args)
     else:
         run_ours(args)
 

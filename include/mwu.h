@@ -130,6 +130,8 @@ typedef struct {
     int32_t max_newton;        /* Newton evaluations per step search; default 8              */
     double newton_tol;         /* Newton has converged once |alpha' - alpha| <= newton_tol
                                   alpha; <= 0 selects eps/20                                 */
+    int32_t batch_workers;     /* mwu_solve_batch: instances solved at once (host threads,
+                                  one stream each); 0 = tuned online over 4, 8, 16            */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
@@ -322,9 +324,12 @@ int mwu_candidates_static(const float *v, const float *dv, int64_t m, int32_t si
 int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
                      mwu_ctx **out);
 
-/* Solve every instance of a batch context: per-instance bisection on M, all
- * probes of all instances advanced together.  objective/iters may be NULL;
- * otherwise host arrays of `count` entries. */
+/* Solve every instance of a batch context: per-instance bisection on M, the
+ * instances solved concurrently (opt.batch_workers of them at a time, each on
+ * its own stream with its own captured iterations, largest first).  Results do
+ * not depend on the concurrency.  objective/iters may be NULL; otherwise host
+ * arrays of `count` entries.  The batch context is not safe for concurrent use
+ * from several host threads. */
 int mwu_solve_batch(mwu_ctx *ctx, double *objective, int64_t *iters, mwu_result *total);
 
 /* ------------------------------------------------------------ diagnostics */

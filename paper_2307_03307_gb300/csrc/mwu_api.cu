@@ -14,12 +14,14 @@
 #include "mwu_setup.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace mwu;
@@ -54,6 +56,7 @@ struct mwu_ctx {
     bool trace = false;          // MWU_TRACE=1: one line per probe on stderr
     // batch front end
     std::vector<mwu_ctx *> batch;
+    int batch_workers_used = 0;
 };
 
 // ------------------------------------------------------------ helpers
@@ -111,6 +114,7 @@ int mwu_default_options(mwu_options *o) {
     o->group = 0;
     o->max_newton = 8;
     o->newton_tol = 0.0;   // 0 -> eps / 20
+    o->batch_workers = 0;  // 0 -> tuned online
     o->timing = 0;
     o->stop_rule = 0;
     o->grad_tol = -1.0;   // precision default
@@ -1208,7 +1212,9 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
             return fail(nullptr, MWU_ERR_INVALID, "batch instances must be PACKING over INCIDENCE or CSR");
         }
         mwu_ctx *sub = nullptr;
-        int rc = mwu_create(MWU_PACKING, &P[k], nullptr, nullptr, &c->opt, &sub);
+        mwu_options so = c->opt;
+        so.stream = nullptr;   // every instance on its own stream, so that instances overlap
+        int rc = mwu_create(MWU_PACKING, &P[k], nullptr, nullptr, &so, &sub);
         if (rc != MWU_OK) {
             std::string m = g_create_error;
             mwu_destroy(c);
@@ -1220,14 +1226,65 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
     return MWU_OK;
 }
 
+// Instances are solved concurrently: W host workers take the next unsolved
+// instance (largest first) and run its whole solve on the instance's own
+// stream and captured iterations, so the GPU overlaps the small kernels and the
+// host round trips of many instances.  With opt.batch_workers = 0, W is tuned
+// online on the first instances, which count as solved work: W = 4, 8, 16
+// (clipped to the batch) each take a chunk of 2W instances, and the W with the
+// highest edges x iterations per second solves the rest.
 int mwu_solve_batch(mwu_ctx *c, double *objective, int64_t *iters, mwu_result *total) {
     if (!c || c->batch.empty()) return MWU_ERR_INVALID;
     auto t0 = std::chrono::steady_clock::now();
+    const size_t n = c->batch.size();
+    std::vector<size_t> order(n);
+    for (size_t k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return c->batch[a]->n > c->batch[b]->n; });
+    std::vector<mwu_result> res(n);
+    std::vector<int> rcs(n, MWU_OK);
+    auto run_chunk = [&](size_t begin, size_t end, int W) -> double {
+        auto s0 = std::chrono::steady_clock::now();
+        std::atomic<size_t> next{begin};
+        auto worker = [&]() {
+            for (;;) {
+                const size_t i = next.fetch_add(1);
+                if (i >= end) break;
+                const size_t k = order[i];
+                rcs[k] = mwu_solve(c->batch[k], 0.0, 0.0, &res[k]);
+            }
+        };
+        std::vector<std::thread> th;
+        for (int w = 1; w < W; ++w) th.emplace_back(worker);
+        worker();
+        for (auto &t : th) t.join();
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - s0).count();
+    };
+    auto units = [&](size_t begin, size_t end) {
+        double u = 0.0;
+        for (size_t i = begin; i < end; ++i) u += (double)c->batch[order[i]]->n * (double)res[order[i]].iters;
+        return u;
+    };
+    size_t pos = 0;
+    int best_w = c->opt.batch_workers;
+    if (best_w <= 0) {
+        double best_rate = -1.0;
+        for (int W : {4, 8, 16}) {
+            W = (int)std::min<size_t>((size_t)W, n);
+            const size_t chunk = std::min<size_t>(n - pos, 2 * (size_t)W);
+            if (chunk == 0) break;
+            const double sec = run_chunk(pos, pos + chunk, W);
+            const double rate = units(pos, pos + chunk) / std::max(sec, 1e-9);
+            if (rate > best_rate) { best_rate = rate; best_w = W; }
+            pos += chunk;
+        }
+    }
+    if (pos < n) run_chunk(pos, n, std::max(1, std::min(best_w, (int)n)));
+    c->batch_workers_used = best_w;
     mwu_result tot{};
-    for (size_t k = 0; k < c->batch.size(); ++k) {
-        mwu_result r{};
-        int rc = mwu_solve(c->batch[k], 0.0, 0.0, &r);
-        if (rc != MWU_OK) return fail(c, rc, std::string("instance ") + std::to_string(k) + ": " + c->batch[k]->err);
+    for (size_t k = 0; k < n; ++k) {
+        if (rcs[k] != MWU_OK)
+            return fail(c, rcs[k], std::string("instance ") + std::to_string(k) + ": " + c->batch[k]->err);
+        const mwu_result &r = res[k];
         if (objective) objective[k] = r.objective;
         if (iters) iters[k] = r.iters;
         tot.objective += r.objective;
