@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--step", default="newton", choices=["kary", "newton"],
                     help="step-size search: K candidates per pass (Alg. 3 generalised) or Newton (Sec. 4.2)")
     ap.add_argument("--workload", default="densest-rmat18",
-                    choices=["densest-rmat18", "bmatching-batch256", "domset-rmat20", "vcover-rmat24"],
+                    choices=["densest-rmat18", "bmatching-batch256", "domset-rmat20", "vcover-rmat24",
+                             "gmatch-200kx8k"],
                     help="densest-rmat18 is the headline line; the others measure the remaining configurations")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying captured iterations (for "
@@ -420,17 +421,25 @@ def run_other(args):
             obj, it, tot = M.mwu_solve_batch(ctx, len(mats))
             return float(sum(e * i for e, i in zip(edges, it))), tot["iters"], tot["probes"]
     else:
-        wl = W.domset(20, seed=3, device="cuda") if args.workload == "domset-rmat20" else W.vcover(24, seed=5, device="cuda")
+        wl = {"domset-rmat20": lambda: W.domset(20, seed=3, device="cuda"),
+              "vcover-rmat24": lambda: W.vcover(24, seed=5, device="cuda"),
+              "gmatch-200kx8k": lambda: W.gmatch(200_000, 8_000, seed=6, device="cuda")}[args.workload]()
         kind, P, C, obj = lpspec.from_workload(wl)
         ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step)
         E = wl.graph.m
         cfg = {"workload": args.workload, "lp": {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
-                                                 "vcover-rmat24": "vertex cover, M^T x >= 1 implicit"}[args.workload],
+                                                 "vcover-rmat24": "vertex cover, M^T x >= 1 implicit",
+                                                 "gmatch-200kx8k": "generalized matching, lb <= M x <= ub (users lb 3 "
+                                                                   "ub 5, items ub 200), feasibility"}[args.workload],
                "vertices": wl.graph.n, "edges": E, "eps": wl.eps}
 
         def solve():
             r = M.mwu_solve(ctx)
             return float(E) * r["iters"], r["iters"], r["probes"]
+        if args.workload == "gmatch-200kx8k":
+            solve_status = M.mwu_solve(ctx)
+            cfg["status"] = "feasible" if solve_status["status"] == M.OK else f"status {solve_status['status']}"
+            cfg["ratio_maxPx_minCx"] = solve_status["objective"]
     for _ in range(args.warmup):
         solve()
     clocks = ClockSampler(local_rank)

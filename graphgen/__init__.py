@@ -77,7 +77,7 @@ def uniform01(seed: int, stream: int, counters: torch.Tensor) -> torch.Tensor:
 
 
 # Stream ids (fixed, so that the same seed gives independent streams per purpose).
-_S_RMAT, _S_PERM, _S_BIP, _S_WEIGHT, _S_CAP, _S_SIZES, _S_INST = 1, 2, 3, 4, 5, 6, 7
+_S_RMAT, _S_PERM, _S_BIP, _S_WEIGHT, _S_CAP, _S_SIZES, _S_INST, _S_RATE = 1, 2, 3, 4, 5, 6, 7, 8
 
 
 @dataclass
@@ -190,6 +190,31 @@ def bipartite_uniform(n_left: int, n_right: int, m: int, seed: int = 1, device="
     v = (chosen % n_right + n_left).to(torch.int32)
     return Graph(n_left + n_right, u, v, n_left, {"generator": "bipartite_uniform", "n_left": n_left,
                                                  "n_right": n_right, "m": m, "seed": seed})
+
+
+def bipartite_ratings(n_users: int, n_items: int, min_deg: int = 10, mean_extra: float = 20.0, skew: float = 3.0,
+                      seed: int = 1, device="cpu") -> Graph:
+    """Users x items rating graph (the structure of the generalized-matching
+    inputs of Appendix A.2: every user rates at least ``min_deg`` items, item
+    popularity skewed).  User u rates min_deg + floor(Exp(mean_extra)) items;
+    each rating picks item floor(n_items * U**skew) (skew > 1 favours low item
+    ids); repeated (user, item) pairs are merged.  Users are 0..n_users-1,
+    items n_users..n-1.
+    """
+    users = torch.arange(n_users, device=device, dtype=torch.int64)
+    ue = uniform01(seed, _S_RATE, users)
+    extra = torch.floor(-mean_extra * torch.log1p(-ue)).to(torch.int64)
+    deg = min_deg + extra
+    total = int(deg.sum().item())
+    owner = torch.repeat_interleave(users, deg)
+    r = uniform01(seed, _S_RATE, torch.arange(n_users, n_users + total, device=device, dtype=torch.int64))
+    item = torch.clamp(torch.floor(n_items * r.pow(skew)).to(torch.int64), max=n_items - 1)
+    key = torch.unique(owner * n_items + item, sorted=True)
+    u = (key // n_items).to(torch.int32)
+    v = (key % n_items + n_users).to(torch.int32)
+    return Graph(n_users + n_items, u, v, n_users, {"generator": "bipartite_ratings", "n_users": n_users,
+                                                   "n_items": n_items, "min_deg": min_deg, "mean_extra": mean_extra,
+                                                   "skew": skew, "seed": seed})
 
 
 def vertex_weights(n: int, seed: int, lo: float = 1.0, hi: float = 10.0, device="cpu") -> torch.Tensor:

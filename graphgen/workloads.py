@@ -18,18 +18,20 @@ from typing import Optional
 
 import torch
 
-from . import Graph, bipartite_uniform, capacities, instance_seed, loguniform_sizes, rmat, symmetric_csr, vertex_weights
+from . import (Graph, bipartite_ratings, bipartite_uniform, capacities, instance_seed, loguniform_sizes, rmat,
+                symmetric_csr, vertex_weights)
 
 
 @dataclass
 class Workload:
     name: str
-    lp: str                      # bmatch | bmatching | densest | domset | vcover
+    lp: str                      # bmatch | bmatching | densest | domset | vcover | gmatch
     graph: Graph
     eps: float = 0.1
     objective: Optional[torch.Tensor] = None   # float32 [n] (vertex weights for domset)
     bounds: Optional[torch.Tensor] = None      # float32 [n_vertices] (b-matching capacities)
     csr: Optional[tuple] = None                # (rowptr, colidx) of I + A for domset
+    lower: Optional[torch.Tensor] = None       # float32 [n_left] lower bounds of the left vertices (gmatch)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -61,6 +63,18 @@ def domset(scale=20, seed=3, device="cpu") -> Workload:
 def vcover(scale=24, seed=5, device="cpu") -> Workload:
     g = rmat(scale, seed=seed, device=device)
     return Workload(f"vcover-rmat{scale}", "vcover", g)
+
+
+def gmatch(n_users=200_000, n_items=8_000, seed=6, lb=3.0, ub_user=5.0, ub_item=200.0, min_deg=10,
+           mean_extra=20.0, eps=0.1, device="cpu") -> Workload:
+    """Generalized matching (Appendix A.1): find x >= 0 with lb <= M x <= ub on a
+    users x items graph; users lb 3, ub 5, items ub 200 as in the paper's
+    Netflix setting (the datasets are not available; bipartite_ratings stands in)."""
+    g = bipartite_ratings(n_users, n_items, min_deg=min_deg, mean_extra=mean_extra, seed=seed, device=device)
+    ub = torch.full((g.n,), ub_item, dtype=torch.float32, device=device)
+    ub[:n_users] = ub_user
+    lower = torch.full((n_users,), lb, dtype=torch.float32, device=device)
+    return Workload(f"gmatch-{n_users}x{n_items}", "gmatch", g, eps=eps, bounds=ub, lower=lower)
 
 
 def bmatching_instance(m, seed, device="cpu") -> Workload:

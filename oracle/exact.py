@@ -120,3 +120,13 @@ def vertex_cover_bruteforce(n, u, v, c=None):
 def subsets(n):
     for k in range(1, n + 1):
         yield from itertools.combinations(range(n), k)
+
+
+def lp_mixed_feasible(P, C):
+    """Whether {x >= 0 : P x <= 1, C x >= 1} is non-empty (HiGHS, zero objective)."""
+    P = sp.csr_matrix(P, dtype=np.float64)
+    C = sp.csr_matrix(C, dtype=np.float64)
+    A = sp.vstack([P, -C]).tocsr()
+    b = np.concatenate([np.ones(P.shape[0]), -np.ones(C.shape[0])])
+    r = linprog(np.zeros(P.shape[1]), A_ub=A, b_ub=b, bounds=(0, None), method="highs")
+    return r.status == 0

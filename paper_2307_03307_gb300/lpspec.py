@@ -31,6 +31,24 @@ def domset_lp(n_vertices, rowptr, colidx, objective=None, val=None):
     return M.COVERING, None, C, objective
 
 
+def gmatch_lp(n_vertices, edges, upper, lower, n_left):
+    """Generalized matching (Appendix A.1): find x >= 0 with diag(1/ub) M x <= 1 and
+    diag(1/lb) M_L x >= 1, M the vertex-edge incidence and M_L its rows of the
+    left vertices 0..n_left-1 (those with a lower bound).  The edges must be
+    sorted with the left endpoint first (graphgen's canonical order), so that
+    left vertex u's edges are contiguous: M_L is a CSR over edge ids."""
+    import torch
+    e = _edges(edges)
+    P = M.implicit_matrix(M.MAT_INCIDENCE, e, n_vertices, row_bound=upper)
+    left = e[:, 0].long()
+    counts = torch.bincount(left, minlength=n_left)
+    rowptr = torch.zeros(n_left + 1, dtype=torch.int64, device=e.device)
+    rowptr[1:] = torch.cumsum(counts, 0)
+    colidx = torch.arange(e.shape[0], dtype=torch.int32, device=e.device)
+    C = M.csr_matrix(rowptr.to(torch.int32), colidx, None, n_left, e.shape[0], row_bound=lower)
+    return M.MIXED, P, C, None
+
+
 def densest_lp(n_vertices, edges):
     """min D s.t. W z >= 1, O z <= D (Sec. 3, Eq. densest_linalg)."""
     e = _edges(edges)
@@ -53,4 +71,6 @@ def from_workload(wl, device=None):
         return domset_lp(g.n, mv(rp), mv(ci), None if wl.objective is None else mv(wl.objective))
     if wl.lp == "densest":
         return densest_lp(g.n, e)
+    if wl.lp == "gmatch":
+        return gmatch_lp(g.n, e, mv(wl.bounds), mv(wl.lower), g.n_left)
     raise ValueError(wl.lp)

@@ -23,6 +23,7 @@ def small_workloads():
         "bmatch": W.bmatch(300, 300, 3001, seed=11),
         "bmatching": W.bmatching_instance(2999, seed=12),
         "densest": W.densest(10, seed=13),
+        "gmatch": W.gmatch(600, 60, seed=16, min_deg=6, mean_extra=8.0),
         "domset": W.domset(10, seed=14),
         "vcover": W.vcover(11, seed=15),
     }
@@ -50,6 +51,9 @@ def oracle_matrices(wl, target):
         O = olp.pair_matrix(g.n, u, v)
         Wm = olp.interweave(g.m)
         return (O / target).tocsr(), Wm, None
+    if wl.lp == "gmatch":
+        Mi = olp.incidence(g.n, u, v)
+        return olp.row_scaled(Mi, wl.bounds.numpy()), olp.row_scaled(Mi[: g.n_left], wl.lower.numpy()), None
     raise ValueError(wl.lp)
 
 
@@ -76,6 +80,8 @@ def n_vars(wl):
         return g.m
     if wl.lp == "densest":
         return 2 * g.m
+    if wl.lp == "gmatch":
+        return g.m
     return g.n
 
 

@@ -18,7 +18,7 @@ from tests import _helpers as H
 
 pytestmark = pytest.mark.gpu
 
-KINDS = ["bmatch", "bmatching", "densest", "domset", "vcover"]
+KINDS = ["bmatch", "bmatching", "densest", "domset", "vcover", "gmatch"]
 PRECS = ["f32", "fp64"]
 
 
@@ -57,6 +57,8 @@ def probe_target(wl):
         return 0.55 * g.n
     if wl.lp == "domset":
         return 0.3 * float(wl.objective.sum())
+    if wl.lp == "gmatch":
+        return 1.0                      # a feasibility LP: the target is unused
 
 
 def vec(M, ctx, which, n):
@@ -307,7 +309,30 @@ def certificate_from_x(wl, x):
 
 @pytest.mark.parametrize("step", ["kary", "newton"])
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("kind", KINDS)
+def test_gmatch_solve_feasible(M, wls, prec, step):
+    """Generalized matching (Appendix A.1): the mixed feasibility LP is solved to a
+    (1+eps)-relative feasible x, as the oracle's solve is, and the LP is feasible
+    by the exact solver."""
+    wl = wls["gmatch"]
+    ctx = make_ctx(M, wl, prec, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY)
+    try:
+        res = M.mwu_solve(ctx)
+        x = vec(M, ctx, M.VEC_X, H.n_vars(wl))
+    finally:
+        M.mwu_destroy(ctx)
+    P, C, _ = H.oracle_matrices(wl, 1.0)
+    assert exact.lp_mixed_feasible(P, C)
+    assert res["status"] == M.OK and (x >= 0).all()
+    xs = x / (C @ x).min()
+    assert (P @ xs).max() <= 1 + wl.eps + 1e-6
+    assert res["objective"] == pytest.approx((P @ x).max() / (C @ x).min(), rel=1e-4)
+    r = om.mwu(P, C, wl.eps, step=step)
+    assert r.status == om.FEASIBLE
+
+
+@pytest.mark.parametrize("step", ["kary", "newton"])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kind", [k for k in KINDS if k != "gmatch"])
 def test_solve_matches_oracle_and_exact(M, wls, kind, prec, step):
     wl = wls[kind]
     ctx = make_ctx(M, wl, prec, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY)

@@ -566,3 +566,41 @@ def _dphi_unweighted(z, dz, alpha, eta):
 def test_planted_mistake_is_caught(mutant, check):
     with pytest.raises(AssertionError):
         check(mutant)
+
+
+# ----------------------------------------------------------------------------
+# generalized matching (Appendix A.1): a mixed packing/covering feasibility LP
+# ----------------------------------------------------------------------------
+
+
+def _gmatch_matrices(wl, lower=None):
+    g = wl.graph
+    Mi = lp.incidence(g.n, g.u.numpy(), g.v.numpy())
+    P = lp.row_scaled(Mi, wl.bounds.numpy())
+    low = wl.lower.numpy() if lower is None else lower
+    C = lp.row_scaled(Mi[: g.n_left], low)
+    return P, C
+
+
+@pytest.mark.parametrize("step", ["kary", "newton"])
+def test_gmatch_feasible_against_exact_lp(step):
+    from graphgen import workloads as W
+    wl = W.gmatch(60, 20, seed=6, min_deg=6, mean_extra=4.0)
+    P, C = _gmatch_matrices(wl)
+    assert exact.lp_mixed_feasible(P, C)
+    r = mwu.mwu(P, C, EPS, step=step)
+    assert r.status == mwu.FEASIBLE
+    xs = r.x / r.z.min()                       # homogeneous: the (1+eps)-relative solution
+    assert (C @ xs).min() >= 1 - 1e-12
+    assert (P @ xs).max() <= 1 + EPS + 1e-12
+
+
+def test_gmatch_infeasible_lower_above_upper():
+    from graphgen import workloads as W
+    wl = W.gmatch(60, 20, seed=6, min_deg=6, mean_extra=4.0)
+    low = wl.lower.numpy().copy()
+    low[0] = 7.0                                # user 0: lb 7 > ub 5
+    P, C = _gmatch_matrices(wl, low)
+    assert not exact.lp_mixed_feasible(P, C)
+    r = mwu.mwu(P, C, EPS, step="newton")
+    assert r.status == mwu.INFEASIBLE
