@@ -164,6 +164,27 @@ def algorithmic_bytes(N, E):
     }
 
 
+def profiled_traffic(workload, cls):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary
+    (profiles/traffic_<workload>.md), or None when there is none or when the
+    kernel source has changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
+    src = os.path.join(ROOT, "paper_2307_03307_gb300", "csrc", "mwu_kernels.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if f"kernels_sha256_16: {digest}" not in text:
+        return None
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) == 3 and cells[0] == cls and cells[2].isdigit():
+            return int(cells[2])
+    return None
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -231,12 +252,7 @@ def run_ours(args):
     avg_ms = per_class_ms[dom] / per_launch[dom]
     achieved = ab[dom] / (avg_ms / 1e3) / 1e9 if timed_classes else None
     peak, peak_src = measured_peaks()
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get(f"densest-rmat{args.scale}", {}).get(dom)
-    except (OSError, ValueError):
-        traffic = None
+    traffic = profiled_traffic(f"densest-rmat{args.scale}", dom)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
