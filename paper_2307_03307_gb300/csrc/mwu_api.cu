@@ -573,6 +573,7 @@ int mwu_set_target(mwu_ctx *c, double target) {
     c->target = target;
     h.eps = o.eps;
     h.eta = o.eta_factor * std::log((double)(c->mP + c->mC)) / o.eps;
+    h.inv_eta = 1.0 / h.eta;
     h.c_d = (o.double_single && (c->mP == 1 || c->mC == 1)) ? 1.0 / h.eta : 1.0 / (2.0 * h.eta);
     h.target = target;
     h.scale[0] = h.scale[1] = 1.0;

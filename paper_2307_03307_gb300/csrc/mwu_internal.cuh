@@ -110,6 +110,8 @@ struct DevState {
     double ratio_stop;          // > 0: stop FEASIBLE once ymax <= ratio_stop * zmin
     // reductions of the current y, z (side 0 = P, side 1 = C)
     double s[2], S[2];
+    double lnS[2], invS[2];     // ln S (in the candidate passes' precision) and 1/S, set with S
+    double inv_eta;             // 1/eta, set with eta
     double dense_v[2], dense_dv[2];   // single objective row value and direction
     double ymax, zmin;
     // direction

@@ -494,6 +494,8 @@ __device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_va
                 st->S[s] = sh_fin[s][1];
             }
             if (!isfinite(st->s[s]) || !isfinite(st->S[s]) || !(st->S[s] > 0.0)) bad = true;
+            st->lnS[s] = (double)t_log((T)st->S[s]);
+            st->invS[s] = 1.0 / st->S[s];
         }
         st->ymax = st->s[0];
         st->zmin = st->s[1];
@@ -1104,17 +1106,18 @@ __device__ void loop_turn_end(DevState *st, cudaGraphConditionalHandle cond) {
 template <class T>
 __device__ double side_value(const Side<T> &q, int sg, const DevState *st, int ss, double a, double mx, double R,
                              double Tt) {
-    const double eta_d = st->eta, S0 = st->S[ss];
-    const double lS0 = (double)t_log((T)S0);
+    // ln S, 1/S and 1/eta come precomputed with S and eta: this runs on the
+    // critical path of every pass, where FP64 divisions are slow on GB300
+    const double inv_eta = st->inv_eta, lS0 = st->lnS[ss];
     if (q.rv.kind == RK_DENSE1) return a * st->dense_dv[ss];   // single row: smax / smin exact
     if (sg > 0) {
         // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p)
         const double lq = mx + (double)t_log((T)Tt) - lS0;
-        return (lq < 0.0) ? (double)t_log1p((T)exp_T<T>(lq)) / eta_d : (mx + (double)t_log((T)R) - lS0) / eta_d;
+        return (lq < 0.0) ? (double)t_log1p((T)exp_T<T>(lq)) * inv_eta : (mx + (double)t_log((T)R) - lS0) * inv_eta;
     }
     // Phi = -(1/eta) ln(R_true / S_c) = -(1/eta) ln(1 - T_true / S_c)
-    const double qv = Tt / S0;
-    return (qv <= 0.5) ? -(double)t_log1p((T)(-qv)) / eta_d : -(mx + (double)t_log((T)R) - lS0) / eta_d;
+    const double qv = Tt * st->invS[ss];
+    return (qv <= 0.5) ? -(double)t_log1p((T)(-qv)) * inv_eta : -(mx + (double)t_log((T)R) - lS0) * inv_eta;
 }
 
 // Last block of a candidate pass: merges the (side, k) quantities, k < K,
@@ -1159,7 +1162,22 @@ __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> 
     for (int k = 0; k < KMAX; ++k) { ca[k] = sc.ca[k]; al[k] = sc.al[k]; }
     const T cd = sc.cd;
     const int K = sc.K;
-    for (int64_t j0 = 4 * tid; j0 < m; j0 += 4 * nthr) {
+    int64_t start = 4 * tid;
+    if (KC == 1 && sizeof(T) == 4) {
+        // one candidate per row leaves the pass short of loads in flight: take
+        // eight rows per thread and iteration (four float4 loads issued together)
+        for (; start + 4 * nthr + 3 < m; start += 8 * nthr) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(sd.v + start);
+            const float4 b0 = *reinterpret_cast<const float4 *>(sd.dv + start);
+            const float4 a1 = *reinterpret_cast<const float4 *>(sd.v + start + 4 * nthr);
+            const float4 b1 = *reinterpret_cast<const float4 *>(sd.dv + start + 4 * nthr);
+            const T vv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const T dd[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r) cand_push_m<T, MODE, SGN, KC>(acc, ca, al, cd, K, vv[r], dd[r], eta, sh);
+        }
+    }
+    for (int64_t j0 = start; j0 < m; j0 += 4 * nthr) {
         const int nr = (int)min((int64_t)4, m - j0);
         T vv[4], dd[4];
         if (nr == 4 && sizeof(T) == 4) {
