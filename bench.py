@@ -51,6 +51,8 @@ def parse():
                     choices=["densest-rmat18", "bmatching-batch256", "domset-rmat20", "vcover-rmat24",
                              "gmatch-200kx8k"],
                     help="densest-rmat18 is the headline line; the others measure the remaining configurations")
+    ap.add_argument("--step-table", action="store_true",
+                    help="the step-rule comparison of Table 2 on rgg-18 (one probe per LP and rule) instead of a bench line")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying captured iterations (for "
                          "profilers that cannot see the kernel nodes of graphs with conditional nodes)")
@@ -493,8 +495,51 @@ def run_other(args):
         dist.destroy_process_group()
 
 
+def run_step_table(args):
+    """Table 2 of Sec. 6: MWU iterations and step-size evaluations per iteration
+    of the standard step (alpha = 1, Alg. 1), Alg. 3's bisection (warm-started
+    from the previous alpha, as in the table), the K = 8 candidate search and
+    Newton's method (Sec. 4.2), on the LPs of rgg-18.  Each rule runs one probe
+    at the certified objective of a Newton solve (a feasible target: the
+    certificate is a bound on the optimum), to the paper's stopping rule."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2307_03307_gb300 import lpspec
+    from paper_2307_03307_gb300 import mwu as M
+    from graphgen import workloads as W
+    rules = [("std", dict(step=M.STEP_STANDARD)), ("bin", dict(step=M.STEP_BINARY, warm_start=1)),
+             ("kary8", dict(step=M.STEP_KARY, K=8)), ("newton", dict(step=M.STEP_NEWTON))]
+    rows = {}
+    for kind in ["matching", "domset", "vcover", "densest"]:
+        wl = W.rgg_lp(kind, scale=args.scale, seed=7, device="cuda")
+        spec = lpspec.from_workload(wl)
+        ctx = M.mwu_create(*spec, eps=wl.eps, step=M.STEP_NEWTON)
+        target = M.mwu_solve(ctx)["objective"]
+        M.mwu_destroy(ctx)
+        row = {"target": target, "vertices": wl.graph.n, "edges": wl.graph.m}
+        for name, opts in rules:
+            ctx = M.mwu_create(*spec, eps=wl.eps, max_iter=60000, **opts)
+            M.mwu_set_target(ctx, target)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = M.mwu_iterate(ctx, 60000)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            M.mwu_destroy(ctx)
+            row[name] = {"iters": st["iters"], "evals_per_iter": st["evals"] / max(1, st["iters"]),
+                         "status": st["status"], "seconds": dt}
+        rows[kind] = row
+    print(json.dumps({"table": "step rules on rgg-18 (one probe at the certified objective)",
+                      "graph": f"rgg-{args.scale} seed 7", "eps": 0.1, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.step_table:
+        run_step_table(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "densest-rmat18":

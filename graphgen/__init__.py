@@ -77,7 +77,7 @@ def uniform01(seed: int, stream: int, counters: torch.Tensor) -> torch.Tensor:
 
 
 # Stream ids (fixed, so that the same seed gives independent streams per purpose).
-_S_RMAT, _S_PERM, _S_BIP, _S_WEIGHT, _S_CAP, _S_SIZES, _S_INST, _S_RATE = 1, 2, 3, 4, 5, 6, 7, 8
+_S_RMAT, _S_PERM, _S_BIP, _S_WEIGHT, _S_CAP, _S_SIZES, _S_INST, _S_RATE, _S_GEO = 1, 2, 3, 4, 5, 6, 7, 8, 9
 
 
 @dataclass
@@ -190,6 +190,62 @@ def bipartite_uniform(n_left: int, n_right: int, m: int, seed: int = 1, device="
     v = (chosen % n_right + n_left).to(torch.int32)
     return Graph(n_left + n_right, u, v, n_left, {"generator": "bipartite_uniform", "n_left": n_left,
                                                  "n_right": n_right, "m": m, "seed": seed})
+
+
+def rgg(scale: int, avg_deg: float = 30.0, seed: int = 1, device="cpu") -> Graph:
+    """Random geometric graph (the rgg-Y family of Sec. 6.3: planar-like, |E| about
+    15 |V|): n = 2**scale points uniform in the unit square, an edge between two
+    points closer than r with pi r^2 n = avg_deg.  Vertices are numbered in the
+    order of the r x r grid cells (row-major), which gives the banded structure
+    of the paper's rgg matrices.  Exact pair test in float64; duplicates cannot
+    occur (each unordered cell pair is visited once)."""
+    n = 1 << scale
+    r = math.sqrt(avg_deg / (math.pi * n))
+    idx = torch.arange(n, device=device, dtype=torch.int64)
+    px = uniform01(seed, _S_GEO, 2 * idx)
+    py = uniform01(seed, _S_GEO, 2 * idx + 1)
+    g = max(1, int(math.floor(1.0 / r)))
+    cx = torch.clamp((px * g).to(torch.int64), max=g - 1)
+    cy = torch.clamp((py * g).to(torch.int64), max=g - 1)
+    cell = cy * g + cx
+    order = torch.argsort(cell * n + idx)                 # cell-major numbering, stable within a cell
+    px, py, cell = px[order], py[order], cell[order]
+    counts = torch.bincount(cell, minlength=g * g)
+    start = torch.zeros(g * g + 1, dtype=torch.int64, device=device)
+    start[1:] = torch.cumsum(counts, 0)
+    us, vs = [], []
+    r2 = r * r
+    # each unordered pair of neighbouring cells once: the cell itself and 4 of its 8 neighbours
+    for dx, dy in [(0, 0), (1, 0), (-1, 1), (0, 1), (1, 1)]:
+        ca = torch.arange(g * g, device=device, dtype=torch.int64)
+        ax, ay = ca % g, ca // g
+        bx, by = ax + dx, ay + dy
+        ok = (bx >= 0) & (bx < g) & (by < g)
+        ca, cb = ca[ok], (by * g + bx)[ok]
+        na, nb = counts[ca], counts[cb]
+        npairs = na * nb
+        keep = npairs > 0
+        ca, cb, na, nb, npairs = ca[keep], cb[keep], na[keep], nb[keep], npairs[keep]
+        tot = int(npairs.sum().item())
+        if tot == 0:
+            continue
+        pair_cell = torch.repeat_interleave(torch.arange(ca.numel(), device=device), npairs)
+        off = torch.arange(tot, device=device, dtype=torch.int64) - torch.repeat_interleave(
+            torch.cumsum(npairs, 0) - npairs, npairs)
+        ia = start[ca][pair_cell] + off // nb[pair_cell]
+        ib = start[cb][pair_cell] + off % nb[pair_cell]
+        if dx == 0 and dy == 0:
+            sel = ia < ib
+            ia, ib = ia[sel], ib[sel]
+        d2 = (px[ia] - px[ib]) ** 2 + (py[ia] - py[ib]) ** 2
+        close = d2 < r2
+        us.append(ia[close])
+        vs.append(ib[close])
+    u = torch.cat(us)
+    v = torch.cat(vs)
+    uu, vv = _canonical_unique(u, v, n)
+    return Graph(n, uu, vv, None, {"generator": "rgg", "scale": scale, "avg_deg": avg_deg, "radius": r,
+                                   "seed": seed})
 
 
 def bipartite_ratings(n_users: int, n_items: int, min_deg: int = 10, mean_extra: float = 20.0, skew: float = 3.0,

@@ -18,14 +18,14 @@ from typing import Optional
 
 import torch
 
-from . import (Graph, bipartite_ratings, bipartite_uniform, capacities, instance_seed, loguniform_sizes, rmat,
+from . import (Graph, bipartite_ratings, bipartite_uniform, capacities, instance_seed, loguniform_sizes, rgg, rmat,
                 symmetric_csr, vertex_weights)
 
 
 @dataclass
 class Workload:
     name: str
-    lp: str                      # bmatch | bmatching | densest | domset | vcover | gmatch
+    lp: str                      # bmatch | bmatching | matching | densest | domset | vcover | gmatch
     graph: Graph
     eps: float = 0.1
     objective: Optional[torch.Tensor] = None   # float32 [n] (vertex weights for domset)
@@ -75,6 +75,25 @@ def gmatch(n_users=200_000, n_items=8_000, seed=6, lb=3.0, ub_user=5.0, ub_item=
     ub[:n_users] = ub_user
     lower = torch.full((n_users,), lb, dtype=torch.float32, device=device)
     return Workload(f"gmatch-{n_users}x{n_items}", "gmatch", g, eps=eps, bounds=ub, lower=lower)
+
+
+def rgg_lp(kind, scale=18, seed=7, device="cpu") -> Workload:
+    """The graph LPs of Sec. 3 on a random geometric graph (the rgg-Y family of
+    Sec. 6.3, Table 2): matching (incidence packing on the general graph),
+    unweighted dominating set, vertex cover, densest subgraph."""
+    g = rgg(scale, seed=seed, device=device)
+    name = f"{kind}-rgg{scale}"
+    if kind == "matching":
+        return Workload(name, "matching", g)
+    if kind == "domset":
+        rowptr, col = symmetric_csr(g, with_self=True)
+        return Workload(name, "domset", g, objective=torch.ones(g.n, dtype=torch.float32, device=device),
+                        csr=(rowptr, col))
+    if kind == "vcover":
+        return Workload(name, "vcover", g)
+    if kind == "densest":
+        return Workload(name, "densest", g)
+    raise ValueError(kind)
 
 
 def bmatching_instance(m, seed, device="cpu") -> Workload:

@@ -104,7 +104,7 @@ typedef struct {
     int32_t step;              /* MWU_STEP_*; default KARY                                    */
     int32_t K;                 /* candidates per pass, 1..8; default 8 (FP64 form forces 1)  */
     int32_t max_passes;        /* candidate passes per iteration; default 6 (F32 K-candidate),
-                                  10 (F32 Newton), 64 (FP64 or K = 1)                       */
+                                  16 (F32 Newton), 64 (FP64 or K = 1)                       */
     int32_t warm_start;        /* start the exponential phase at floor(log2 alpha_prev)      */
     int32_t double_single;     /* c_d = 1/eta when one side is a single row (Sec. 2.2)       */
     int32_t precision;         /* MWU_PREC_*; default F32_R64                                 */

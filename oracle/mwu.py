@@ -310,6 +310,9 @@ def make_newton_evaluator(y, dy, z, dz, eta):
     return evaluate
 
 
+NEWTON_JUMP = 256.0   # the exponential phase's reach in one pass of K = 8 candidates
+
+
 def newton_update(alpha, psi, phi, dpsi, dphi, lb, ub):
     """One Newton step on g(alpha) = f(alpha) - 1 with f = Phi/Psi (Sec. 4.2).
 
@@ -318,14 +321,24 @@ def newton_update(alpha, psi, phi, dpsi, dphi, lb, ub):
     Reading (safeguard; the paper gives none): [lb, ub] brackets the root by
     Prop. 4.2 (f(lb) >= 1 > f(ub)).  A step that is undefined (Psi <= 0,
     g' >= 0, not finite) or leaves the open bracket is replaced by the
-    midpoint (lb + ub)/2, or by 2 alpha while ub is still infinite.
+    geometric midpoint sqrt(lb ub) when both ends are known, and otherwise
+    moves toward the root by the exponential search's reach of one pass,
+    a factor NEWTON_JUMP = 2^8 (down from ub while no passing value is known,
+    up from alpha while no failing one is).  A warm start far above the new
+    root (after a large previous step) then needs a few passes, not one
+    halving per pass.
     """
     den = psi * dphi - phi * dpsi
     nxt = math.nan
     if psi > 0.0 and den < 0.0 and math.isfinite(den):
         nxt = alpha - (phi - psi) * psi / den
     if not (math.isfinite(nxt) and lb < nxt < ub):
-        nxt = 0.5 * (lb + ub) if math.isfinite(ub) else 2.0 * alpha
+        if lb > 0.0 and math.isfinite(ub):
+            nxt = math.sqrt(lb * ub)
+        elif math.isfinite(ub):
+            nxt = ub / NEWTON_JUMP
+        else:
+            nxt = alpha * NEWTON_JUMP
     return nxt
 
 

@@ -383,7 +383,7 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     c->fp64 = o.precision == MWU_PREC_FP64;
     if (const char *tr = std::getenv("MWU_TRACE")) c->trace = tr[0] == '1';
     if (c->fp64 || o.step == MWU_STEP_BINARY) o.K = 1;
-    if (o.max_passes <= 0) o.max_passes = (c->fp64 || o.K == 1) ? 64 : (o.step == MWU_STEP_NEWTON ? 10 : 6);
+    if (o.max_passes <= 0) o.max_passes = (c->fp64 || o.K == 1) ? 64 : (o.step == MWU_STEP_NEWTON ? 16 : 6);
     if (o.max_newton == 0) o.max_newton = 8;
     if (!(o.newton_tol > 0.0)) o.newton_tol = o.eps / 20.0;
     if (o.outer_tol <= 0.0) o.outer_tol = o.eps;

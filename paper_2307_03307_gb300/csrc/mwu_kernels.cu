@@ -1007,7 +1007,13 @@ __device__ void newton_decide(DevState *st, double psi, double phi, double dpsi,
     const double den = psi * dphi - phi * dpsi;
     double nxt = (double)NAN;
     if (psi > 0.0 && den < 0.0 && isfinite(den)) nxt = a - (phi - psi) * psi / den;
-    if (!(isfinite(nxt) && lb < nxt && nxt < ub)) nxt = isfinite(ub) ? 0.5 * (lb + ub) : 2.0 * a;
+    // safeguard: the geometric midpoint of the bracket, or a move by the
+    // exponential phase's reach per pass (2^8) while one end is unknown
+    if (!(isfinite(nxt) && lb < nxt && nxt < ub)) {
+        if (lb > 0.0 && isfinite(ub)) nxt = sqrt(lb * ub);
+        else if (isfinite(ub)) nxt = ub * (1.0 / 256.0);
+        else nxt = a * 256.0;
+    }
     if (fabs(nxt - a) <= st->newton_tol * a || st->newton_steps >= st->max_newton || st->passes >= st->max_passes) {
         if (ok) search_finish(st, a);
         else newton_start_backoff(st, a);

@@ -62,7 +62,7 @@ def from_workload(wl, device=None):
     g = wl.graph
     mv = (lambda t: t.to(device)) if device is not None else (lambda t: t)
     e = mv(wl.edges)
-    if wl.lp in ("bmatch", "bmatching"):
+    if wl.lp in ("bmatch", "bmatching", "matching"):
         return bmatch_lp(g.n, e, None if wl.bounds is None else mv(wl.bounds))
     if wl.lp == "vcover":
         return vcover_lp(g.n, e, None if wl.objective is None else mv(wl.objective))

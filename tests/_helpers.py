@@ -33,7 +33,7 @@ def oracle_matrices(wl, target):
     """Explicit (P, C, objective c or None) of a workload at probe target M (or D)."""
     g = wl.graph
     u, v = g.u.numpy(), g.v.numpy()
-    if wl.lp in ("bmatch", "bmatching"):
+    if wl.lp in ("bmatch", "bmatching", "matching"):
         A = olp.incidence(g.n, u, v)
         if wl.bounds is not None:
             A = olp.row_scaled(A, wl.bounds.numpy())
@@ -60,7 +60,7 @@ def oracle_matrices(wl, target):
 def oracle_solve(wl, **kw):
     g = wl.graph
     u, v = g.u.numpy(), g.v.numpy()
-    if wl.lp in ("bmatch", "bmatching"):
+    if wl.lp in ("bmatch", "bmatching", "matching"):
         A = olp.incidence(g.n, u, v)
         if wl.bounds is not None:
             A = olp.row_scaled(A, wl.bounds.numpy())
@@ -76,7 +76,7 @@ def oracle_solve(wl, **kw):
 
 def n_vars(wl):
     g = wl.graph
-    if wl.lp in ("bmatch", "bmatching"):
+    if wl.lp in ("bmatch", "bmatching", "matching"):
         return g.m
     if wl.lp == "densest":
         return 2 * g.m

@@ -53,7 +53,7 @@ def _chain_checks(M, wl, step):
             H.assert_rel([phi[k]], [om.Phi(ch.z, ch.dz, a, ch.eta)], 1e-5, abs_=bphi, what=f"Phi({a})")
         rc, alpha, ev = M.mwu_search(ctx)
         if step == M.STEP_NEWTON:
-            ao, _ = om.search_newton(ch.evaluate_nd, ch.evaluate, wl.eps, K=8, alpha0=None, max_passes=10)
+            ao, _ = om.search_newton(ch.evaluate_nd, ch.evaluate, wl.eps, K=8, alpha0=None, max_passes=16)
             check_step_decision(ch, e, "f32", alpha, ao, rel_gap=2 * wl.eps / 20 + 1e-3)
         else:
             ao, _ = om.search_kary(ch.evaluate, wl.eps, K=8, max_passes=6)

@@ -263,7 +263,7 @@ def test_newton_search_matches_oracle(M, wls, kind, prec):
         rc, alpha, ev = M.mwu_search(ctx)
         K = 1 if prec == "fp64" else 8
         ao, info = om.search_newton(ch.evaluate_nd, ch.evaluate, wl.eps, K=K, alpha0=None,
-                                    max_passes=10 if K == 8 else 64)
+                                    max_passes=16 if K == 8 else 64)
         # Newton iterates are continuous in Psi, Phi: the two searches may end a
         # Newton tolerance apart; decisions must otherwise be valid
         check_step_decision(ch, e, prec, alpha, ao, rel_gap=2 * wl.eps / 20 + 1e-3)
@@ -438,3 +438,29 @@ def test_one_minus_exp_neg_against_cuda_expm1(M):
     f32 = -torch.expm1(-b)
     rel32 = ((u - f32).abs() / f32.clamp_min(1e-38))[1:]
     assert float(rel32.max()) < 2.0 ** -20
+
+
+@pytest.mark.parametrize("kind", ["matching", "domset", "vcover", "densest"])
+def test_rgg_solves_match_exact_lp(M, kind):
+    """The LPs on a random geometric graph (banded, planar-like structure of the
+    rgg family): certified objective within (1+eps)^2 of the HiGHS optimum."""
+    from graphgen import workloads as W
+    wl = W.rgg_lp(kind, scale=9, seed=4)
+    g = wl.graph
+    u, v = g.u.numpy(), g.v.numpy()
+    ctx = make_ctx(M, wl, "f32", step=M.STEP_NEWTON)
+    try:
+        res = M.mwu_solve(ctx)
+    finally:
+        M.mwu_destroy(ctx)
+    tol2 = (1 + wl.eps) ** 2
+    if kind == "matching":
+        opt = exact.lp_packing_opt(olp.incidence(g.n, u, v), np.ones(g.m))
+        assert opt / tol2 <= res["objective"] <= opt * (1 + 1e-6)
+    elif kind == "densest":
+        opt = exact.lp_densest_opt(g.n, u, v)
+        assert opt * (1 - 1e-6) <= res["objective"] <= opt * tol2
+    else:
+        A = olp.dominating(g.n, u, v) if kind == "domset" else olp.incidence(g.n, u, v).T.tocsr()
+        opt = exact.lp_covering_opt(A, np.ones(g.n))
+        assert opt * (1 - 1e-6) <= res["objective"] <= opt * tol2

@@ -291,6 +291,22 @@ def test_newton_step_search():
         check_newton(mwu, seed)
 
 
+def test_newton_far_warm_start_stays_within_budget():
+    """After a large step the warm start can sit orders of magnitude above the
+    new root (or below it): the safeguard's jumps reach a passing step within
+    the pass budget of the FP32 form (16)."""
+    for seed in [3, 5, 7]:
+        P, C, x, eta, y, z, d, dy, dz = check_direction_invariants(mwu, seed)
+        ast = _root_of_b4b(mwu, y, dy, z, dz, eta)
+        evn = mwu.make_newton_evaluator(y, dy, z, dz, eta)
+        ev = mwu.make_evaluator(y, dy, z, dz, eta)
+        for f0 in [3000.0, 0.001]:
+            a, info = mwu.search_newton(evn, ev, EPS, K=8, alpha0=f0 * ast, max_passes=16)
+            ok, _ = ev([a])
+            assert ok[0] and 0.3 * ast <= a <= ast * (1 + 1e-12), (seed, f0, a / ast)
+            assert info.passes <= 16
+
+
 def test_newton_search_backoff_and_floor():
     """The (1 - eps)^p backoff on a threshold f, and alpha < 1 -> 0."""
     # f >= 1 iff alpha <= t, with Psi, Phi, and derivatives that make Newton
