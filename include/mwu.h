@@ -125,8 +125,12 @@ typedef struct {
                                   selects the default: 2^-16 for F32_R64 (a few FP32
                                   roundings of g/h, below which d = 0 is undecidable in
                                   FP32), 0 for FP64 (the exact test of Alg. 2)             */
-    void *stream;              /* cudaStream_t; NULL = a non-blocking stream the context
-                                  creates and owns                                           */
+    void *stream;              /* cudaStream_t for all of the context's work.  NULL = a
+                                  blocking stream the context creates and owns: it waits
+                                  for work queued on the legacy default stream, so inputs
+                                  written there before a call are complete when read.
+                                  With a stream of its own, the caller orders its inputs
+                                  on that stream                                             */
     int32_t max_newton;        /* Newton evaluations per step search; default 8              */
     double newton_tol;         /* Newton has converged once |alpha' - alpha| <= newton_tol
                                   alpha; <= 0 selects eps/20                                 */

@@ -401,7 +401,11 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     if (o.stream) {
         c->stream = (cudaStream_t)o.stream;
     } else {
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        // a blocking stream: its work is ordered after what the caller queued on
+        // the legacy default stream, so device inputs written there before the
+        // call are complete when the context reads them (a non-blocking stream
+        // could copy an edge list that is still being written)
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) {
             cudaGetLastError();
             c->err = "cannot create a CUDA stream (no device?)";
             return bail(MWU_ERR_CUDA);
