@@ -511,7 +511,11 @@ def run_step_table(args):
     from paper_2307_03307_gb300 import mwu as M
     from graphgen import workloads as W
     rules = [("std", dict(step=M.STEP_STANDARD, max_iter=30000)), ("bin", dict(step=M.STEP_BINARY, warm_start=1)),
-             ("kary8", dict(step=M.STEP_KARY, K=8)), ("newton", dict(step=M.STEP_NEWTON))]
+             ("kary8", dict(step=M.STEP_KARY, K=8)), ("newton", dict(step=M.STEP_NEWTON)),
+             # the same rules with the ratio stopping test (stop_rule = 1): a probe ends as soon
+             # as x / min(Cx) is a (1+eps)-relative solution
+             ("bin_ratio", dict(step=M.STEP_BINARY, warm_start=1, stop_rule=1)),
+             ("newton_ratio", dict(step=M.STEP_NEWTON, stop_rule=1))]
     rows = {}
     for kind in ["matching", "domset", "vcover", "densest"]:
         wl = W.rgg_lp(kind, scale=args.scale, seed=7, device="cuda")

@@ -359,10 +359,11 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
     * Backoff: the converged alpha_k may miss Eq. b4b_conv, so alpha_k (1 -
       eps)^p is taken for the smallest p >= 0 with f >= 1.  Reading: a value
       below 1 ends the backoff with 0 (alpha < 1 is INFEASIBLE in Alg. 2).
-    * Budget: every Newton evaluation is one pass, the backoff takes K values
-      per pass, and ``max_passes`` bounds the passes of the whole search (a
-      spent budget ends Newton as converged, and the backoff with the largest
-      passing value seen).
+    * Budget: every Newton evaluation and every backoff value is one pass
+      (the first backoff value nearly always passes: Newton converges to
+      within tol of the root), and ``max_passes`` bounds the passes of the
+      whole search (a spent budget ends Newton as converged, and the backoff
+      with the largest passing value seen).
     ``evaluate_nd(alpha)`` -> (Psi, Phi, Psi', Phi'); ``evaluate(alphas)`` ->
     (f >= 1 flags, min(z + alpha dz)) as for the other searches.
     Returns (alpha, info); info.evals counts f evaluations, info.newton the
@@ -422,18 +423,15 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
         alpha = nxt
     if ok:
         return alpha, info
-    # backoff alpha (1 - eps)^p, p = 1, 2, ... (the running product), K values
+    # backoff alpha (1 - eps)^p, p = 1, 2, ... (the running product), one value
     # per pass; when the pass budget is spent the largest passing value seen is
     # returned (0 if there is none or it is below 1)
     q = 1.0 - eps
     a = alpha
-    p = 0
     while True:
-        if p % K == 0:
-            if info.passes >= max_passes:
-                return (lb if lb >= 1.0 else 0.0), info
-            info.passes += 1
-        p += 1
+        if info.passes >= max_passes:
+            return (lb if lb >= 1.0 else 0.0), info
+        info.passes += 1
         a = a * q
         if a < 1.0:
             return 0.0, info

@@ -35,6 +35,7 @@ struct mwu_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t body_stream = nullptr;      // captures the body of the device-side search loop
+    cudaStream_t kc_stream = nullptr;        // captures the body of the IF node inside it
     Arena ar;
     std::string err;
     int64_t n = 0, mP = 0, mC = 0;
@@ -346,6 +347,7 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.grid_newton = std::max(2, c->n_sms * std::min(8, newton_blocks_per_sm<T>()));
     p.cond_on = 0;
     p.cond = 0;
+    p.cond_kc = 0;
     size_t recs = (size_t)std::max(std::max(p.grid_var, p.grid_newton), std::max(p.grid_row, p.grid_upd)) + 8;
     p.part_var = c->ar.alloc<double>((int64_t)(recs * REC));
     p.part_row = c->ar.alloc<double>((int64_t)(recs * REC));
@@ -524,6 +526,7 @@ void mwu_destroy(mwu_ctx *c) {
     c->ar.free_all();
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
+    if (c->kc_stream) cudaStreamDestroy(c->kc_stream);
     delete c;
 }
 
@@ -637,11 +640,13 @@ static int kernels_per_iteration(const mwu_ctx *c) { return 3 + c->opt.max_passe
 constexpr int EV_PER_IT = 5;
 
 // The step-size search of one iteration.  Captured (graph): a conditional WHILE
-// node, opened by the direction kernel, whose body is one Newton pass kernel
-// and one K-candidate pass kernel (each returns at once outside its phases);
-// every body turn ends by setting the loop condition, so the loop runs the
-// passes the search needs.  Eager: max_passes turns of the same kernels,
-// which return at once once the search has ended.
+// node, opened by the direction kernel, whose body is the one-candidate pass
+// kernel (Newton and backoff passes) followed by an IF node around the
+// K-candidate pass kernel; the first kernel sets the IF condition, and every
+// body turn ends by setting the loop condition, so the loop runs the passes the
+// search needs and no turn launches a kernel that has nothing to do.  Eager:
+// max_passes turns of the same kernels, which return at once outside their
+// phases or once the search has ended.
 template <class Prob>
 static cudaError_t enqueue_search(mwu_ctx *c, Prob &p, bool loop) {
     cudaError_t e;
@@ -669,13 +674,42 @@ static cudaError_t enqueue_search(mwu_ctx *c, Prob &p, bool loop) {
         return e;
     if (!c->body_stream && (e = cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return e;
-    if ((e = cudaStreamBeginCaptureToGraph(c->body_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    if (!c->kc_stream && (e = cudaStreamCreateWithFlags(&c->kc_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return e;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaGraphConditionalHandleCreate(&p.cond_kc, body, 0u, 0u)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+        cudaSuccess)
         return e;
     cudaError_t e1 = launch_cand_newton(p, c->body_stream);
-    if (e1 == cudaSuccess) e1 = launch_cand(p, 0, c->body_stream);
-    cudaGraph_t body = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(c->body_stream, &body);
+    cudaGraphNodeParams ip{};
+    if (e1 == cudaSuccess) {
+        cudaGraph_t bg = nullptr;
+        const cudaGraphNode_t *bdeps = nullptr;
+        size_t bnd = 0;
+        e1 = cudaStreamGetCaptureInfo(c->body_stream, &cs, nullptr, &bg, &bdeps, nullptr, &bnd);
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = p.cond_kc;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t inode;
+        if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&inode, bg, bdeps, nullptr, bnd, &ip);
+        if (e1 == cudaSuccess)
+            e1 = cudaStreamUpdateCaptureDependencies(c->body_stream, &inode, nullptr, 1,
+                                                     cudaStreamSetCaptureDependencies);
+    }
+    if (e1 == cudaSuccess) {
+        e1 = cudaStreamBeginCaptureToGraph(c->kc_stream, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed);
+        if (e1 == cudaSuccess) {
+            cudaError_t e3 = launch_cand(p, 0, c->kc_stream);
+            cudaGraph_t kbody = nullptr;
+            cudaError_t e4 = cudaStreamEndCapture(c->kc_stream, &kbody);
+            e1 = e3 != cudaSuccess ? e3 : e4;
+        }
+    }
+    cudaGraph_t bout = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->body_stream, &bout);
     return e1 != cudaSuccess ? e1 : e2;
 }
 
@@ -778,6 +812,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
     while (done < n_iters && c->st_host->status == ST_RUNNING) {
         const int iter0 = c->st_host->iter;
         const int64_t passes0 = c->st_host->total_passes;
+        const int64_t loop0 = c->st_host->loop_launches;
         if (c->fp64) {
             // plain form: host-driven search, one readback per candidate pass
             std::vector<cudaEvent_t> &ev = c->ev_one;
@@ -808,9 +843,9 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             int n = chunk ? c->opt.check_every : 1;
             TRY_CUDA(c, cudaGraphLaunch(chunk ? c->gexec_chunk : c->gexec_one, c->stream));
             if ((rc = pull_state(c)) != MWU_OK) return rc;
-            // 4 kernels per captured iteration plus the loop bodies (passes after the first)
-            c->launches += (int64_t)n * 4 +
-                           std::max<int64_t>(0, (c->st_host->total_passes - passes0) - (c->st_host->iter - iter0));
+            // direction, SpMV and update per captured iteration, plus the kernels
+            // the search loops ran (counted on the device)
+            c->launches += (int64_t)n * 3 + (c->st_host->loop_launches - loop0);
             if (c->opt.timing &&
                 (rc = accumulate_timing(c, chunk ? c->ev : c->ev_one, c->st_host->iter - iter0)) != MWU_OK)
                 return rc;

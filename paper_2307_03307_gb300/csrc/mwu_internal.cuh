@@ -125,6 +125,7 @@ struct DevState {
     double bo_cur;              // backoff: last value alpha (1 - eps)^p handed out
     double dpsi, dphi;          // Psi'(alpha_0), Phi'(alpha_0) of the last Newton pass
     int32_t loop_guard;         // passes run by the device-side search loop of this iteration
+    long long loop_launches;    // kernels run inside the device-side search loops (all iterations)
     double lb, ub;
     double alpha[KMAX];
     double psi[KMAX], phi[KMAX], zmink[KMAX];
@@ -156,9 +157,12 @@ struct Problem {
     int32_t grid_spmv;            // grid of the forward SpMV (its own occupancy)
     int32_t grid_newton;          // grid of the one-candidate Newton pass (its own occupancy)
     // a captured iteration: the handle of its step-search WHILE loop, which the
-    // direction kernel opens and every candidate pass sets (0 = not captured)
+    // direction kernel opens and every turn of the loop sets (0 = not captured),
+    // and the handle of the IF node inside the loop body that runs the
+    // K-candidate pass only in the turns whose phase needs it
     int32_t cond_on;
     cudaGraphConditionalHandle cond;
+    cudaGraphConditionalHandle cond_kc;
     int32_t G_var;      // lanes per variable for CSR column views
     int32_t heavy_var_len;
     int32_t n_heavy_var;

@@ -972,15 +972,20 @@ __device__ void search_finish(DevState *st, double acc) {
     }
 }
 
-// First backoff pass after Newton converged at alpha (f(alpha) < 1): the
-// values alpha (1 - eps)^p, p = 1..K, as a running product.
+// Next backoff value after Newton converged at alpha with f(alpha) < 1: the
+// running product alpha (1 - eps)^p, one value per pass (the first one nearly
+// always passes, Newton having stopped within tol of the root).  A value below
+// 1 ends the search with 0 (alpha < 1 is INFEASIBLE) without evaluating it.
 __device__ void backoff_next(DevState *st) {
-    const double q = 1.0 - st->eps;
-    st->kpass = st->K;
-    for (int k = 0; k < st->K; ++k) {
-        st->bo_cur = st->bo_cur * q;
-        st->alpha[k] = st->bo_cur;
+    st->bo_cur = st->bo_cur * (1.0 - st->eps);
+    if (st->bo_cur < 1.0) {
+        st->passes += 1;
+        st->total_passes += 1;
+        search_finish(st, 0.0);
+        return;
     }
+    st->kpass = 1;
+    st->alpha[0] = st->bo_cur;
 }
 
 __device__ void newton_start_backoff(DevState *st, double alpha) {
@@ -1023,18 +1028,13 @@ __device__ void newton_decide(DevState *st, double psi, double phi, double dpsi,
     st->kpass = 1;
 }
 
-// After a backoff pass: the first passing value in order; a value below 1
-// ends the search with 0 (alpha < 1 is INFEASIBLE); a spent budget returns
-// the largest passing value seen.
-__device__ void backoff_decide(DevState *st, const int *ok) {
-    const int K = st->kpass;
+// After a backoff pass at alpha[0]: accept it when it passes; a spent budget
+// returns the largest passing value seen.
+__device__ void backoff_decide(DevState *st, int ok) {
     st->passes += 1;
-    st->evals += K;
+    st->evals += 1;
     st->total_passes += 1;
-    for (int k = 0; k < K; ++k) {
-        if (st->alpha[k] < 1.0) { search_finish(st, 0.0); return; }
-        if (ok[k]) { search_finish(st, st->alpha[k]); return; }
-    }
+    if (ok) { search_finish(st, st->alpha[0]); return; }
     if (st->passes >= st->max_passes) { search_finish(st, st->lb >= 1.0 ? st->lb : 0.0); return; }
     backoff_next(st);
 }
@@ -1351,9 +1351,11 @@ template <class T>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<T> p, int gP, int external) {
     __shared__ CandSched<T> s_sc;
     DevState *st = p.st;
-    // in a captured iteration the Newton passes belong to k_cand_newton, which
-    // runs just before this kernel in each turn of the search loop
-    const bool searching = external || (st->phase != PH_DONE && !(p.cond_on && st->phase == PH_NEWTON));
+    // in a captured iteration the Newton and backoff passes belong to
+    // k_cand_newton, the first kernel of each turn of the search loop
+    const bool searching =
+        external || (st->phase != PH_DONE && !(p.cond_on && (st->phase == PH_NEWTON || st->phase == PH_BACKOFF)));
+    if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) st->loop_launches += 1;
     if (st->status != ST_RUNNING || !searching) {
         if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) loop_turn_end(st, p.cond);
         return;
@@ -1475,7 +1477,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
                 st->numeric_bad = 2;
             } else if (!external) {
                 if (newton) newton_decide(st, fin[0][0][0], fin[1][0][0], st->dpsi, st->dphi);
-                else if (st->phase == PH_BACKOFF) backoff_decide(st, ok);
+                else if (st->phase == PH_BACKOFF) backoff_decide(st, ok[0]);
                 else search_decide(st, ok, zmk);
             }
             if (p.cond_on) loop_turn_end(st, p.cond);
@@ -1485,14 +1487,27 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
 }
 
 // ============================================================ Newton pass
-// One-candidate pass of Newton's method (Sec. 4.2) in a captured iteration:
-// Psi, Phi and the sums of Psi', Phi' at alpha_0, then newton_decide.  Per row
+// One-candidate pass of the Newton step search (Sec. 4.2): Psi, Phi and the
+// sums of Psi', Phi' at alpha_0, then newton_decide (or, in the backoff that
+// follows a converged Newton step whose value fails, backoff_decide).  Per row
 // it is the K-candidate pass in its Newton mode, with one accumulator set and
-// small records, so it runs at higher occupancy than k_cand.
+// small records, so it runs at higher occupancy than k_cand.  In a captured
+// iteration it is the first kernel of each turn of the search loop: outside its
+// phases it hands the turn to k_cand through the IF node that follows it, and
+// after its own pass it skips k_cand and sets the loop condition itself.
 template <class T>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(Problem<T> p, int gP) {
     DevState *st = p.st;
-    if (st->status != ST_RUNNING || st->phase != PH_NEWTON) return;   // k_cand follows and ends the loop turn
+    const int phase = st->phase;
+    if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) st->loop_launches += 1;
+    if (st->status != ST_RUNNING || (phase != PH_NEWTON && phase != PH_BACKOFF)) {
+        if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) {
+            const bool kc = st->status == ST_RUNNING && phase != PH_DONE;
+            cudaGraphSetConditional(p.cond_kc, kc ? 1u : 0u);
+            if (!kc) cudaGraphSetConditional(p.cond, 0u);   // the search has ended: close the loop
+        }
+        return;
+    }
     const int s = (blockIdx.x < gP) ? 0 : 1;
     const int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
     const int nbs = s == 0 ? gP : gridDim.x - gP;
@@ -1561,8 +1576,14 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(P
         if (!isfinite(psi) || !isfinite(phi) || !isfinite(st->dpsi) || !isfinite(st->dphi)) {
             st->status = ST_NUMERIC;
             st->numeric_bad = 2;
-        } else {
+        } else if (phase == PH_NEWTON) {
             newton_decide(st, psi, phi, st->dpsi, st->dphi);
+        } else {
+            backoff_decide(st, phi >= psi);
+        }
+        if (p.cond_on) {
+            cudaGraphSetConditional(p.cond_kc, 0u);
+            loop_turn_end(st, p.cond);
         }
         st->counter[2] = 0;
     }
