@@ -298,15 +298,26 @@ def dPhi(z, dz, alpha, eta):
 
 
 def make_newton_evaluator(y, dy, z, dz, eta):
-    """Single-candidate evaluator for Newton's method: (Psi, Phi, Psi', Phi') at alpha."""
+    """Single-candidate evaluator for Newton's method: (Psi, Phi, Psi', Phi', min(z + alpha dz)) at alpha."""
     y = np.asarray(y, dtype=np.float64)
     dy = np.asarray(dy, dtype=np.float64)
     z = np.asarray(z, dtype=np.float64)
     dz = np.asarray(dz, dtype=np.float64)
 
     def evaluate(alpha):
-        return (Psi(y, dy, alpha, eta), Phi(z, dz, alpha, eta), dPsi(y, dy, alpha, eta), dPhi(z, dz, alpha, eta))
+        return (Psi(y, dy, alpha, eta), Phi(z, dz, alpha, eta), dPsi(y, dy, alpha, eta), dPhi(z, dz, alpha, eta),
+                float((z + alpha * dz).min()))
 
+    def alpha_cover():
+        """The smallest alpha with min(z + alpha dz) >= 1: max over z_j < 1 of (1 - z_j)/dz_j."""
+        open_ = z < 1.0
+        if not open_.any():
+            return 0.0
+        if (dz[open_] <= 0.0).any():
+            return math.inf
+        return float(((1.0 - z[open_]) / dz[open_]).max())
+
+    evaluate.alpha_cover = alpha_cover
     return evaluate
 
 
@@ -364,8 +375,20 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
       within tol of the root), and ``max_passes`` bounds the passes of the
       whole search (a spent budget ends Newton as converged, and the backoff
       with the largest passing value seen).
-    ``evaluate_nd(alpha)`` -> (Psi, Phi, Psi', Phi'); ``evaluate(alphas)`` ->
-    (f >= 1 flags, min(z + alpha dz)) as for the other searches.
+    * Early exit (reading: Alg. 3's rule, which the Newton search of Sec. 4.2
+      does not restate): a Newton value alpha with f >= 1 and min(z + alpha
+      dz) >= 1 completes MWU.  A warm start can sit far above the smallest
+      such step, so one more pass computes alpha_c = max over the rows with
+      z_j < 1 of (1 - z_j)/dz_j (the smallest step covering every row) and
+      the search returns max(1, min(alpha, alpha_c)), which passes by Prop.
+      4.2 (f decreases) as 1 <= alpha.  Without the rule f >= 1 can hold for
+      every alpha once few covering rows are left (with dropped rows), and the
+      search climbs by the safeguard's jumps until its budget is spent; with
+      alpha itself instead of alpha_c the overshoot pushed max y past 1 + eps.
+    ``evaluate_nd(alpha)`` -> (Psi, Phi, Psi', Phi'[, min(z + alpha dz)]),
+    with an optional attribute ``alpha_cover()`` -> alpha_c;
+    ``evaluate(alphas)`` -> (f >= 1 flags, min(z + alpha dz)) as for the other
+    searches.
     Returns (alpha, info); info.evals counts f evaluations, info.newton the
     Newton evaluations.
     """
@@ -406,13 +429,22 @@ def search_newton(evaluate_nd, evaluate, eps, K=8, alpha0=None, max_newton=8, ma
         alpha = float(alpha0)
     steps = 0
     while True:
-        psi, phi, dpsi, dphi = evaluate_nd(alpha)
+        r = evaluate_nd(alpha)
+        psi, phi, dpsi, dphi = r[:4]
+        zmin = r[4] if len(r) > 4 else -math.inf
         info.evals += 1
         info.passes += 1
         info.newton += 1
         info.candidates.append([alpha])
         steps += 1
         ok = bang_for_buck_ok(psi, phi)
+        if ok and zmin >= 1.0 and alpha >= 1.0:
+            info.early = True
+            cover = getattr(evaluate_nd, "alpha_cover", None)
+            if cover is None:
+                return alpha, info
+            info.passes += 1                  # the pass that computes alpha_c
+            return max(1.0, min(alpha, cover())), info
         if ok:
             lb = max(lb, alpha)
         else:
@@ -464,7 +496,7 @@ class MWUResult:
 
 def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_passes=64,
         double_single=True, warm_start=False, x0=None, on_iter=None, stop_rule=0, grad_tol=0.0, max_newton=8,
-        newton_tol=None, ratio_stop=0.0):
+        newton_tol=None, ratio_stop=0.0, drop_covered=False):
     """MWU_STEPSIZE_SEARCH (Alg. 2) on explicit P (m_P x n) and C (m_C x n).
 
     Per iteration: test, g and h, d, max(d) = 0 -> INFEASIBLE, dy = Pd and
@@ -490,6 +522,16 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
     Newton evaluations, relative tolerance ``newton_tol``) or "standard"
     (alpha = 1, Alg. 1).
     ``grad_tol`` is the tolerance of the gradient test (see ``direction``).
+
+    ``drop_covered`` keeps only the unsatisfied covering rows, the last step
+    of the loop of Alg. 1 and Alg. 2 (C <- {c_j : c_j^T x < 1}), where the
+    default keeps every row as the paper's own implementation does (Sec. 4).
+    Reading: x never decreases (d >= 0, alpha >= 0, C >= 0), so a dropped row
+    stays satisfied and the active set before an iteration is exactly the
+    rows with z_j < 1.  The active rows alone enter smin and its gradient h,
+    Phi, Phi' and the early exit of the search; the stopping tests read all of
+    z, which is the same since dropped rows have z_j >= 1 (min z >= 1 is
+    "C is empty").
     """
     P = sp.csr_matrix(P, dtype=np.float64)
     C = sp.csr_matrix(C, dtype=np.float64)
@@ -519,14 +561,20 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
         if it >= max_iter:
             status, reason = MAX_ITER, "max_iter"
             break
-        g, h = gradients(P, C, y, z, eta)
+        if drop_covered:
+            act = z < 1.0                   # the active covering rows (Alg. 2, keep unsatisfied)
+            Ca, za = C[np.flatnonzero(act)], z[act]
+        else:
+            Ca, za = C, z
+        g, h = gradients(P, Ca, y, za, eta)
         d = direction(g, h, x, c_d, grad_tol)
         if d.max() <= 0.0:
             status, reason = INFEASIBLE, "d=0"
             break
         dy = P @ d
         dz = C @ d
-        ev = make_evaluator(y, dy, z, dz, eta)
+        dza = dz[act] if drop_covered else dz
+        ev = make_evaluator(y, dy, za, dza, eta)
         if step == "standard":
             alpha = 1.0
             ok, _ = ev([1.0])
@@ -537,7 +585,7 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
             evals += info.evals
             passes += info.passes
         elif step == "newton":
-            evn = make_newton_evaluator(y, dy, z, dz, eta)
+            evn = make_newton_evaluator(y, dy, za, dza, eta)
             alpha, info = search_newton(evn, ev, eps, K=K, alpha0=alpha_prev, max_newton=max_newton,
                                         max_passes=max_passes, tol=newton_tol)
             evals += info.evals

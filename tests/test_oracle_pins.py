@@ -266,12 +266,12 @@ def check_newton(o=mwu, seed=3):
     evn = o.make_newton_evaluator(y, dy, z, dz, eta)
     # one step from each side of the root moves toward it (a contraction here)
     a0 = 0.95 * ast
-    ps, ph, dps, dph = evn(a0)
+    ps, ph, dps, dph, _ = evn(a0)
     assert ph >= ps
     a1 = o.newton_update(a0, ps, ph, dps, dph, a0, math.inf)
     assert a0 < a1 <= ast * (1 + 1e-12) and ast - a1 < 0.5 * (ast - a0)
     a0 = 1.05 * ast
-    ps, ph, dps, dph = evn(a0)
+    ps, ph, dps, dph, _ = evn(a0)
     assert ph < ps
     a1 = o.newton_update(a0, ps, ph, dps, dph, 0.0, a0)
     assert a1 < a0 and abs(a1 - ast) < 0.75 * (a0 - ast)
@@ -620,3 +620,93 @@ def test_gmatch_infeasible_lower_above_upper():
     assert not exact.lp_mixed_feasible(P, C)
     r = mwu.mwu(P, C, EPS, step="newton")
     assert r.status == mwu.INFEASIBLE
+
+
+# ----------------------------------------------------------------------------
+# active-set dropping of satisfied covering rows (the last step of the loop of
+# Alg. 1 and Alg. 2: C <- {c_j : c_j^T x < 1})
+# ----------------------------------------------------------------------------
+
+
+def test_drop_equals_keep_on_vertex_transitive_graph():
+    """On a cycle every covering row has the same value at every iteration (x0
+    is uniform and the graph is vertex-transitive), so the active set is all
+    rows until the stop: dropping must reproduce keeping bit for bit (the
+    standard step, alpha = 1, gives many iterations)."""
+    n, u, v = _cycle(12)
+    C = lp.incidence(n, u, v).T.tocsr()
+    P = lp.objective_row(np.ones(n), 0.6 * n)
+    r0 = mwu.mwu(P, C, EPS, step="standard")
+    r1 = mwu.mwu(P, C, EPS, step="standard", drop_covered=True)
+    assert r0.status == r1.status and r0.iters == r1.iters > 100
+    assert np.array_equal(r0.x, r1.x)
+
+
+def test_drop_gradient_special_case():
+    """Covering rows x_1 >= 1 (z_1 = 1: satisfied) and x_2 >= 1 (z_2 = 0.999),
+    packing row (x_1 + x_2)/M <= 1.  With dropping only row 2 is active: smin
+    of one row is exact, so h = (0, 1), g = (1/M, 1/M), and d = (0, c_d (1 -
+    1/M) x_2): x_1 stays and x_2 moves by alpha c_d (1 - 1/M) x_2.  Keeping
+    row 1 gives h_1 = e^{-eta}/(e^{-eta} + e^{-0.999 eta}) > 1/M: x_1 moves."""
+    M = 10.0
+    C = sp.identity(2, format="csr")
+    P = lp.objective_row(np.ones(2), M)
+    x0 = np.array([1.0, 0.999])
+    for drop in [True, False]:
+        seen = []
+        mwu.mwu(P, C, EPS, step="kary", x0=x0, max_iter=1, drop_covered=drop,
+                on_iter=lambda it, x, y, z, a: seen.append((x.copy(), a)))
+        (x1, a), = seen
+        if drop:
+            eta = mwu.eta_of(3, EPS)
+            c_d = mwu.step_coefficient(1, 2, eta)
+            assert x1[0] == x0[0]
+            assert x1[1] == pytest.approx(x0[1] + a * c_d * (1.0 - 1.0 / M) * x0[1], rel=1e-12)
+        else:
+            assert x1[0] > x0[0]
+
+
+@pytest.mark.parametrize("step", ["kary", "newton"])
+def test_drop_solves_within_bound(step):
+    """Whole solves with dropping still give (1 + eps)-relative objectives
+    (Theorem 4.1 with the outer search's tolerance) against the exact LP."""
+    gr = gg.rmat(7, seed=5)
+    A = lp.incidence(gr.n, gr.u, gr.v).T.tocsr()
+    opt = exact.lp_covering_opt(A, np.ones(gr.n))
+    r = mwu.solve_covering(A, np.ones(gr.n), EPS, step=step, drop_covered=True)
+    _covering_within(r.objective, opt)
+    g = gg.rmat(7, seed=3)
+    c = gg.vertex_weights(g.n, seed=3).numpy().astype(np.float64)
+    A = lp.dominating(g.n, g.u, g.v)
+    opt = exact.lp_covering_opt(A, c)
+    r = mwu.solve_covering(A, c, EPS, step=step, drop_covered=True)
+    _covering_within(r.objective, opt)
+    n, u, v = gr.n, gr.u.numpy(), gr.v.numpy()
+    opt = exact.lp_densest_opt(n, u, v)
+    r = mwu.solve_densest(n, u, v, EPS, step=step, drop_covered=True)
+    _covering_within(r.objective, opt)
+
+
+def test_newton_early_exit_when_step_covers():
+    """A passing Newton value that covers every row ends the search with the
+    smallest covering step alpha_c (Alg. 3's early exit; alpha_c passes by
+    Prop. 4.2), and never below 1."""
+    t = 50.0
+    ev = _threshold_eval(1e9)
+    evn = lambda a: (1.0, 2.0, 0.0, 0.0, a / t)     # f >= 1 everywhere, covers from alpha = t
+    evn.alpha_cover = lambda: t
+    a, info = mwu.search_newton(evn, ev, EPS, K=8, alpha0=3.0 * t, max_passes=16)
+    assert a == t and info.early and info.passes == 2
+    evn.alpha_cover = lambda: 0.25
+    a, info = mwu.search_newton(evn, ev, EPS, K=8, alpha0=3.0 * t, max_passes=16)
+    assert a == 1.0 and info.early
+    # the covering step of an instance: (1 - z_j)/dz_j over the open rows
+    z, dz = np.array([0.5, 1.2, 0.9]), np.array([0.1, 0.0, 0.4])
+    evr = mwu.make_newton_evaluator(np.zeros(1), np.zeros(1), z, dz, 10.0)
+    assert evr.alpha_cover() == pytest.approx(5.0, rel=1e-15)
+    assert mwu.make_newton_evaluator(np.zeros(1), np.zeros(1), z, np.array([0.1, 0.0, 0.0]),
+                                     10.0).alpha_cover() == math.inf
+    # without a covering value, f >= 1 everywhere drives the safeguard's jumps to the budget
+    evn4 = lambda a: (1.0, 2.0, 0.0, 0.0)
+    a, info = mwu.search_newton(evn4, ev, EPS, K=8, alpha0=3.0 * t, max_passes=4)
+    assert a == 3.0 * t * 256.0 ** 3 and info.passes == 4
