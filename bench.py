@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying captured iterations (for "
                          "profilers that cannot see the kernel nodes of graphs with conditional nodes)")
+    ap.add_argument("--drop", action="store_true",
+                    help="drop satisfied covering rows (the last step of Alg. 1/2's loop)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -208,7 +210,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     step = M.STEP_NEWTON if args.step == "newton" else M.STEP_KARY
     ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, timing=0 if args.eager else 1, step=step,
-                       use_graph=0 if args.eager else 1)
+                       use_graph=0 if args.eager else 1, drop_covered=int(args.drop))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -262,6 +264,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"densest-rmat{args.scale}", "lp": "densest subgraph (Charikar dual)",
                    "vertices": N, "edges": E, "variables": 2 * E, "eps": wl.eps, "K": 8, "step": args.step,
+                   "covering_rows": "dropped when satisfied" if args.drop else "kept",
                    "precision": "f32 vectors, f64 reductions", "l2": "flushed (512 MB write) between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "time_to_approx_s": statistics.mean(step_ms) / 1e3,
@@ -282,7 +285,8 @@ def run_ours(args):
     M.mwu_destroy(ctx)
 
     if rank == 0 and not args.no_fp64:
-        ctx64 = M.mwu_create(kind, P, C, obj, eps=wl.eps, precision=M.PREC_FP64, step=step)
+        ctx64 = M.mwu_create(kind, P, C, obj, eps=wl.eps, precision=M.PREC_FP64, step=step,
+                             drop_covered=int(args.drop))
         flush.zero_()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -307,7 +311,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             kd, Ph, Ch, oh = lpspec.densest_lp(N, edges_h)
-            cx = M.mwu_create(kd, Ph, Ch, oh, eps=wl.eps, step=step)
+            cx = M.mwu_create(kd, Ph, Ch, oh, eps=wl.eps, step=step, drop_covered=int(args.drop))
             r = M.mwu_solve(cx)
             M.load().mwu_get_vector(cx, M.VEC_X, x_h.data_ptr(), 2 * E, 0)
             M.mwu_destroy(cx)
@@ -443,7 +447,7 @@ def run_other(args):
               "vcover-rmat24": lambda: W.vcover(24, seed=5, device="cuda"),
               "gmatch-200kx8k": lambda: W.gmatch(200_000, 8_000, seed=6, device="cuda")}[args.workload]()
         kind, P, C, obj = lpspec.from_workload(wl)
-        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step)
+        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop))
         E = wl.graph.m
         cfg = {"workload": args.workload, "lp": {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
                                                  "vcover-rmat24": "vertex cover, M^T x >= 1 implicit",
@@ -479,7 +483,8 @@ def run_other(args):
     clk = clocks.stop()
     step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
     total_s, units = aggregate(dist, sum(step_ms) / 1e3, sum(o[0] for o in out), "cuda")
-    cfg.update({"step": args.step, "precision": "f32 vectors, f64 reductions",
+    cfg.update({"step": args.step, "covering_rows": "dropped when satisfied" if args.drop else "kept",
+                "precision": "f32 vectors, f64 reductions",
                 "l2": "flushed (512 MB write) between steps", "parallelism": "replicas" if world > 1 else "single"})
     line = {"metric": METRIC, "value": units / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
@@ -515,7 +520,9 @@ def run_step_table(args):
              # the same rules with the ratio stopping test (stop_rule = 1): a probe ends as soon
              # as x / min(Cx) is a (1+eps)-relative solution
              ("bin_ratio", dict(step=M.STEP_BINARY, warm_start=1, stop_rule=1)),
-             ("newton_ratio", dict(step=M.STEP_NEWTON, stop_rule=1))]
+             ("newton_ratio", dict(step=M.STEP_NEWTON, stop_rule=1)),
+             # Newton with the satisfied covering rows dropped (Alg. 1/2's last step)
+             ("newton_drop", dict(step=M.STEP_NEWTON, drop_covered=1))]
     rows = {}
     for kind in ["matching", "domset", "vcover", "densest"]:
         wl = W.rgg_lp(kind, scale=args.scale, seed=7, device="cuda")

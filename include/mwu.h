@@ -136,6 +136,12 @@ typedef struct {
                                   alpha; <= 0 selects eps/20                                 */
     int32_t batch_workers;     /* mwu_solve_batch: instances solved at once (host threads,
                                   one stream each); 0 = tuned online over 4, 8, 16            */
+    int32_t drop_covered;      /* 1: keep only the unsatisfied covering rows, the last step
+                                  of the loop of Alg. 1 and Alg. 2 (C <- {c_j : c_j^T x < 1}):
+                                  a row with (Cx)_j >= 1 leaves smin, h, Phi and Phi'.  x
+                                  never decreases, so the active rows are those with
+                                  (Cx)_j < 1.  0 (default): every row is kept, as the
+                                  paper's implementation does (Sec. 4)                     */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
@@ -281,7 +287,9 @@ int mwu_get_timing(mwu_ctx *ctx, mwu_timing *out, int32_t reset);
  *                    (+w x_i/M on the packing side, -w x_i/M on the covering side)
  *   grad_vals[k]   = d pot / d val[k] for the k-th stored value of the
  *                    explicit CSR matrix (sign +w_j x_i for P, -w_j x_i for C).
- * Sec. 4.1 defines the potential (its 1/eta factor is left out here). */
+ * Sec. 4.1 defines the potential (its 1/eta factor is left out here).  It
+ * takes every covering row, also with drop_covered set; the context's state is
+ * left at x with its reductions over the active rows. */
 int mwu_potential(mwu_ctx *ctx, const float *x, double *pot,
                   float *grad_x, float *grad_obj, float *grad_vals);
 

@@ -116,6 +116,7 @@ int mwu_default_options(mwu_options *o) {
     o->max_newton = 8;
     o->newton_tol = 0.0;   // 0 -> eps / 20
     o->batch_workers = 0;  // 0 -> tuned online
+    o->drop_covered = 0;
     o->timing = 0;
     o->stop_rule = 0;
     o->grad_tol = -1.0;   // precision default
@@ -593,6 +594,7 @@ int mwu_set_target(mwu_ctx *c, double target) {
     h.step_mode = o.step == MWU_STEP_STANDARD ? 2 : (o.step == MWU_STEP_BINARY ? 1 : (o.step == MWU_STEP_NEWTON ? 3 : 0));
     h.max_newton = o.max_newton;
     h.newton_tol = o.newton_tol;
+    h.act_hi = o.drop_covered ? 1.0 : (double)INFINITY;
     h.kpass = o.K;
     h.deriv = 0;
     h.stop_rule = o.stop_rule;
@@ -827,7 +829,10 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             int guard = 0;
             while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE && guard++ < 256) {
-                TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
+                const bool cover = c->st_host->phase == PH_COVER;
+                TRY_CUDA(c, with_prob(c, [&](auto &p) {
+                    return cover ? launch_cand_newton(p, c->stream) : launch_cand(p, 0, c->stream);
+                }));
                 c->launches += 1;
                 if ((rc = pull_state(c)) != MWU_OK) return rc;
             }
@@ -951,7 +956,10 @@ int mwu_search(mwu_ctx *c, double *alpha, int64_t *evals) {
     if (rc != MWU_OK) return rc;
     int guard = 0;
     while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE && guard++ < 256) {
-        TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
+        const bool cover = c->st_host->phase == PH_COVER;   // the covering-step pass
+        TRY_CUDA(c, with_prob(c, [&](auto &p) {
+            return cover ? launch_cand_newton(p, c->stream) : launch_cand(p, 0, c->stream);
+        }));
         if ((rc = pull_state(c)) != MWU_OK) return rc;
     }
     if (alpha) *alpha = c->st_host->status == ST_RUNNING ? c->st_host->alpha_acc : 0.0;
@@ -1207,8 +1215,32 @@ int mwu_solve(mwu_ctx *c, double lo, double hi, mwu_result *res) {
 }
 
 // ------------------------------------------------------------ potential
+// The potential takes every covering row, whatever drop_covered says: the
+// dropping threshold is lifted for the evaluation and put back after it.
+static int set_drop_threshold(mwu_ctx *c, double hi) {
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    c->st_host->act_hi = hi;
+    return push_state(c);
+}
+
+static int potential_all_rows(mwu_ctx *c, const float *x, double *pot, float *grad_x, float *grad_obj,
+                              float *grad_vals);
+
 int mwu_potential(mwu_ctx *c, const float *x, double *pot, float *grad_x, float *grad_obj, float *grad_vals) {
     if (!c || !x) return MWU_ERR_INVALID;
+    if (!c->opt.drop_covered) return potential_all_rows(c, x, pot, grad_x, grad_obj, grad_vals);
+    int rc = set_drop_threshold(c, (double)INFINITY);
+    if (rc != MWU_OK) return rc;
+    rc = potential_all_rows(c, x, pot, grad_x, grad_obj, grad_vals);
+    // back to the active rows: the sums of the state at x follow them again
+    int rc2 = set_drop_threshold(c, 1.0);
+    if (rc2 == MWU_OK) rc2 = mwu_set_x(c, x, 0);
+    return rc != MWU_OK ? rc : rc2;
+}
+
+static int potential_all_rows(mwu_ctx *c, const float *x, double *pot, float *grad_x, float *grad_obj,
+                              float *grad_vals) {
     int rc = mwu_set_x(c, x, 0);
     if (rc != MWU_OK) return rc;
     const DevState &h = *c->st_host;

@@ -97,7 +97,9 @@ enum : int32_t { RS_NONE = 0, RS_COVERED = 1, RS_PACKING = 2, RS_DZERO = 3, RS_A
                  RS_RATIO = 6 };
 
 // Search phases.
-enum : int32_t { PH_EXP = 0, PH_REFINE = 1, PH_DONE = 2, PH_NEWTON = 3, PH_BACKOFF = 4 };
+// PH_COVER: a passing Newton value covered every row; one pass computes the
+// smallest covering step alpha_c and the search ends with max(1, min(alpha, alpha_c)).
+enum : int32_t { PH_EXP = 0, PH_REFINE = 1, PH_DONE = 2, PH_NEWTON = 3, PH_BACKOFF = 4, PH_COVER = 5 };
 
 struct DevState {
     // problem scalars
@@ -112,6 +114,7 @@ struct DevState {
     double s[2], S[2];
     double lnS[2], invS[2];     // ln S (in the candidate passes' precision) and 1/S, set with S
     double inv_eta;             // 1/eta, set with eta
+    double act_hi;              // covering rows with z_j >= act_hi are dropped (1: drop_covered, +inf: kept)
     double dense_v[2], dense_dv[2];   // single objective row value and direction
     double ymax, zmin;
     // direction

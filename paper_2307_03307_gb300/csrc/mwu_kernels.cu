@@ -232,11 +232,14 @@ __device__ __forceinline__ bool last_block_done(unsigned int *counter) {
 }
 
 // ---------------------------------------------------------------- row weights
-// w_j (unnormalised) = exp(sgn*eta*(v_j - s)) / rdiv_j
+// w_j (unnormalised) = exp(sgn*eta*(v_j - s)) / rdiv_j, and 0 for a dropped
+// row (v_j >= hi: a satisfied covering row when they are dropped)
 template <class T> struct WeightFn {
-    const T *v; const float *rdiv; T eta_sgn; T s;
+    const T *v; const float *rdiv; T eta_sgn; T s; T hi;
     __device__ __forceinline__ T operator()(int64_t j) const {
-        T w = t_exp(eta_sgn * (v[j] - s));
+        const T vj = v[j];
+        if (!(vj < hi)) return T(0);
+        T w = t_exp(eta_sgn * (vj - s));
         if (rdiv) w /= (T)rdiv[j];
         return w;
     }
@@ -360,6 +363,7 @@ template <class T> __device__ __forceinline__ T row_coef(const Side<T> &sd, int6
 // the block must call it (it synchronises).
 template <class T> struct SweepConsts {
     T eta, s0, s1, fp, fc, kgh, cd, thr, scale0, scale1, alpha_prev, alpha_acc;
+    T hi;   // covering rows with z_j >= hi are dropped (+inf: every row is kept)
 };
 template <class T> __device__ __forceinline__ SweepConsts<T> sweep_consts(const DevState *st) {
     __shared__ SweepConsts<T> c;
@@ -377,6 +381,7 @@ template <class T> __device__ __forceinline__ SweepConsts<T> sweep_consts(const 
         c.scale1 = (T)st->scale[1];
         c.alpha_prev = st->pending ? (T)st->alpha_acc : T(0);
         c.alpha_acc = (T)st->alpha_acc;
+        c.hi = (T)st->act_hi;
     }
     __syncthreads();
     return c;
@@ -453,9 +458,9 @@ __device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_va
     // on the sign-adjusted shift sg * s_b.
     static_assert(BLOCK == 256, "merge layout assumes 256 threads");
     DevState *st = p.st;
-    __shared__ double sh_fin[2][2];
+    __shared__ double sh_fin[2][3];
     __shared__ double sh_d[32];
-    block_merge_shifted<T, 1, false>(
+    block_merge_shifted<T, 1, true>(
         2, (T)st->eta,
         [&](int q, int &b0, int &b1) { b0 = q == 0 ? 0 : gP; b1 = q == 0 ? gP : nb_row; },
         [&](int) { return 1u; },
@@ -463,11 +468,12 @@ __device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_va
             const T *o = rec_of<T>(p.part_row, b);
             m = p.side[q].sign > 0 ? o[0] : -o[0];   // sign-adjusted shift: the merge takes the max
             r[0] = o[1];
-            v = T(0);
+            v = o[2];
         },
-        [&](int q, T M, const double (&tot)[1], T) {
+        [&](int q, T M, const double (&tot)[1], T vmin) {
             sh_fin[q][0] = p.side[q].sign > 0 ? (double)M : -(double)M;
             sh_fin[q][1] = tot[0];
+            sh_fin[q][2] = (double)vmin;
         });
     double dense[2] = {0.0, 0.0};
     if (dense_from_var) {
@@ -482,6 +488,7 @@ __device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_va
     __syncthreads();
     if (threadIdx.x == 0) {
         bool bad = false;
+        const bool drop = isfinite(st->act_hi);
         for (int s = 0; s < 2; ++s) {
             const Side<T> &sd = p.side[s];
             if (sd.rv.kind == RK_DENSE1) {
@@ -492,13 +499,21 @@ __device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_va
             } else {
                 st->s[s] = sh_fin[s][0];
                 st->S[s] = sh_fin[s][1];
+                if (s == 1 && drop && !(st->S[1] > 0.0)) {
+                    // every covering row dropped (all satisfied): the sums are
+                    // empty and the stopping test below ends the probe
+                    st->s[1] = sh_fin[1][2];
+                    st->S[1] = 1.0;
+                }
             }
             if (!isfinite(st->s[s]) || !isfinite(st->S[s]) || !(st->S[s] > 0.0)) bad = true;
             st->lnS[s] = (double)t_log((T)st->S[s]);
             st->invS[s] = 1.0 / st->S[s];
         }
         st->ymax = st->s[0];
-        st->zmin = st->s[1];
+        // min z over every row: with dropped rows the shift of the sums is the
+        // minimum over the active rows only
+        st->zmin = (drop && p.side[1].rv.kind != RK_DENSE1) ? sh_fin[1][2] : st->s[1];
         if (bad) {
             st->status = ST_NUMERIC;
             st->numeric_bad = 1;
@@ -519,26 +534,35 @@ __device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_va
 }
 
 // End of a block's LSE accumulation: warps in T, then an 8-lane tree over the
-// warps in T, then one float record [shift, S] per block.
+// warps in T, then one record [shift, S, vmin] per block; vmin is the plain
+// minimum over every row the block saw (dropped covering rows included).
 template <class T>
-__device__ void lse_block_record(const Problem<T> &p, Lse<T> acc, T eta_sgn, int sgn) {
+__device__ void lse_block_record(const Problem<T> &p, Lse<T> acc, T eta_sgn, int sgn, T vmin) {
     for (int off = 16; off > 0; off >>= 1) {
         T os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
         lse_merge<T, T>(acc, os, oS, eta_sgn, sgn);
+        vmin = fmin(vmin, shfl_x(vmin, off));
     }
-    __shared__ T ws[BLOCK / 32], wS[BLOCK / 32];
-    if ((threadIdx.x & 31) == 0) { ws[threadIdx.x >> 5] = acc.s; wS[threadIdx.x >> 5] = acc.S; }
+    __shared__ T ws[BLOCK / 32], wS[BLOCK / 32], wm[BLOCK / 32];
+    if ((threadIdx.x & 31) == 0) {
+        ws[threadIdx.x >> 5] = acc.s;
+        wS[threadIdx.x >> 5] = acc.S;
+        wm[threadIdx.x >> 5] = vmin;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
         Lse<T> q{ws[threadIdx.x & 7], wS[threadIdx.x & 7]};
+        T mn = wm[threadIdx.x & 7];
         for (int off = 4; off > 0; off >>= 1) {
             T os = shfl_x(q.s, off), oS = shfl_x(q.S, off);
             lse_merge<T, T>(q, os, oS, eta_sgn, sgn);
+            mn = fmin(mn, shfl_x(mn, off));
         }
         if (threadIdx.x == 0) {
             T *rec = rec_of<T>(p.part_row, blockIdx.x);
             rec[0] = q.s;
             rec[1] = q.S;
+            rec[2] = mn;
         }
     }
 }
@@ -600,8 +624,9 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
     const T alpha_prev = K0.alpha_prev;
     const Side<T> &P = p.side[0];
     const Side<T> &C = p.side[1];
-    WeightFn<T> wp{P.v, P.rv.rdiv, K0.eta, K0.s0};
-    WeightFn<T> wc{C.v, C.rv.rdiv, -K0.eta, K0.s1};
+    WeightFn<T> wp{P.v, P.rv.rdiv, K0.eta, K0.s0, t_inf<T>()};
+    // the potential of Sec. 4.1 always takes every row
+    WeightFn<T> wc{C.v, C.rv.rdiv, -K0.eta, K0.s1, potential_mode ? t_inf<T>() : K0.hi};
     const T fp = K0.fp, fc = K0.fc, cd = K0.cd, thr = K0.thr;
     int npos = 0;   // positives of this thread
     T dense_dot[2] = {T(0), T(0)}, dense_cmp[2] = {T(0), T(0)};   // compensated per thread
@@ -704,7 +729,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
     const T alpha_prev = K0.alpha_prev;
     const Side<T> &P = p.side[0];
     const Side<T> &C = p.side[1];
-    const T eta = K0.eta, sp = K0.s0, sc = K0.s1, cd = K0.cd, thr = K0.thr;
+    const T eta = K0.eta, sp = K0.s0, sc = K0.s1, cd = K0.cd, thr = K0.thr, hi = K0.hi;
     const int64_t E = p.n >> 1;
     const int2 *ends = reinterpret_cast<const int2 *>(P.cv.idx);
     int npos = 0;   // positives of this thread
@@ -722,8 +747,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dir_pairs(Problem<T> p) {
             r0 *= re / (P.rv.rdiv ? (T)P.rv.rdiv[uv.x] : T(1));
             r1 *= re / (P.rv.rdiv ? (T)P.rv.rdiv[uv.y] : T(1));
         }
-        const T d0 = (r0 < thr) ? cd * (T(1) - r0) * x0 : T(0);
-        const T d1 = (r1 < thr) ? cd * (T(1) - r1) * x1 : T(0);
+        // a dropped covering row (z_e >= hi) gives h = 0 on both slots: d = 0
+        const bool live = ze < hi;
+        const T d0 = (live && r0 < thr) ? cd * (T(1) - r0) * x0 : T(0);
+        const T d1 = (live && r1 < thr) ? cd * (T(1) - r1) * x1 : T(0);
         if (sizeof(T) == 4) reinterpret_cast<float2 *>(p.d)[e] = make_float2((float)d0, (float)d1);
         else { p.d[2 * e] = d0; p.d[2 * e + 1] = d1; }
         C.dv[e] = (d0 + d1) * row_coef(C, e, scale_c);   // a6 for W: dz_e = d_{2e} + d_{2e+1}
@@ -819,7 +846,18 @@ template <class T> struct CandSched {
     int K, mode;
     T ca[KMAX], al[KMAX];
     T cd;
+    T hi;   // covering rows with v >= hi are dropped (+inf: all kept)
 };
+
+// Largest alpha_k eta of a schedule: the search's schedules ascend, but the
+// candidates of an external evaluation come in any order.
+template <class T> __device__ __forceinline__ T sched_camax(const T *ca, int K) {
+    T m = ca[0];
+#pragma unroll
+    for (int k = 1; k < KMAX; ++k)
+        if (k < K) m = fmax(m, ca[k]);
+    return m;
+}
 
 __device__ __forceinline__ float fast_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double fast_exp(double x) { return exp(x); }
@@ -845,14 +883,15 @@ template <> __device__ __forceinline__ double negl_margin<double>() { return 1.0
 
 template <class T, int MODE, int SGN, int KC>
 __device__ __forceinline__ void cand_push_m(CandAcc<T> &c, const T *ca, const T *al, T cd, int Kr, T v, T dv, T eta,
-                                            T s) {
+                                            T s, T hi, T camax) {
     const int K = KC > 0 ? KC : Kr;
+    if (SGN < 0 && !(v < hi)) return;   // a dropped covering row
     const T a = (SGN > 0 ? eta : -eta) * (v - s);
     // A row whose exponents lie more than NEGL below every shift adds nothing
     // representable to R_k and T_k.  Packing: x_k = a + b_k <= a + b_{K-1} and
     // mx_k >= 0.  Covering: x_k <= a <= 0 and exp(a) is the T weight (S_c >= 1).
     if (SGN > 0) {
-        if (a + ca[K - 1] * dv < -negl_margin<T>()) return;
+        if (a + camax * dv < -negl_margin<T>()) return;   // camax = max_k alpha_k eta
     } else {
         if (a < -negl_margin<T>() && a < c.mxmin - negl_margin<T>()) {
 #pragma unroll
@@ -907,21 +946,6 @@ __device__ __forceinline__ void cand_push_m(CandAcc<T> &c, const T *ca, const T 
         for (int k = 1; k < KMAX; ++k)
             if (k < K) mn = fmin(mn, c.mx[k]);
         c.mxmin = mn;
-    }
-}
-
-template <class T>
-__device__ __forceinline__ void cand_push(CandAcc<T> &c, const CandSched<T> &sc, int sgn, T v, T dv, T eta, T s) {
-    if (sgn > 0) {
-        if (sc.mode == 0) cand_push_m<T, 0, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
-        else if (sc.mode == 1) cand_push_m<T, 1, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
-        else if (sc.mode == 3) cand_push_m<T, 3, 1, 1>(c, sc.ca, sc.al, sc.cd, 1, v, dv, eta, s);
-        else cand_push_m<T, 2, 1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
-    } else {
-        if (sc.mode == 0) cand_push_m<T, 0, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
-        else if (sc.mode == 1) cand_push_m<T, 1, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
-        else if (sc.mode == 3) cand_push_m<T, 3, -1, 1>(c, sc.ca, sc.al, sc.cd, 1, v, dv, eta, s);
-        else cand_push_m<T, 2, -1, 0>(c, sc.ca, sc.al, sc.cd, sc.K, v, dv, eta, s);
     }
 }
 
@@ -999,13 +1023,21 @@ __device__ void newton_start_backoff(DevState *st, double alpha) {
 // g = f - 1 with the bracket safeguard, the convergence test, and the start
 // of the (1 - eps)^p backoff when the converged alpha misses Eq. b4b_conv.
 // The same steps as the oracle's search_newton.
-__device__ void newton_decide(DevState *st, double psi, double phi, double dpsi, double dphi) {
+__device__ void newton_decide(DevState *st, double psi, double phi, double dpsi, double dphi, double zmin) {
     st->passes += 1;
     st->evals += 1;
     st->total_passes += 1;
     st->newton_steps += 1;
     const double a = st->alpha[0];
     const bool ok = phi >= psi;
+    // Alg. 3's early exit: a passing step that covers every row completes MWU;
+    // one more pass finds the smallest such step (cover_pass)
+    if (ok && zmin >= 1.0 && a >= 1.0) {
+        st->early = 1;
+        st->phase = PH_COVER;
+        st->kpass = 1;
+        return;
+    }
     if (ok) st->lb = fmax(st->lb, a);
     else st->ub = fmin(st->ub, a);
     const double lb = st->lb, ub = st->ub;
@@ -1097,7 +1129,7 @@ __device__ void search_decide(DevState *st, const int *ok, const double *zmin_k)
 // ever fail.
 __device__ void loop_turn_end(DevState *st, cudaGraphConditionalHandle cond) {
     unsigned v = search_continues(st);
-    if (v && ++st->loop_guard > st->max_passes + 2) {
+    if (v && ++st->loop_guard > st->max_passes + 4) {
         st->status = ST_NUMERIC;
         st->numeric_bad = 3;
         v = 0u;
@@ -1166,8 +1198,9 @@ __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> 
     T ca[KMAX], al[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) { ca[k] = sc.ca[k]; al[k] = sc.al[k]; }
-    const T cd = sc.cd;
+    const T cd = sc.cd, hi = sc.hi;
     const int K = sc.K;
+    const T camax = sched_camax(ca, K);
     int64_t start = 4 * tid;
     if (KC == 1 && sizeof(T) == 4) {
         // one candidate per row leaves the pass short of loads in flight: take
@@ -1180,7 +1213,7 @@ __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> 
             const T vv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const T dd[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int r = 0; r < 8; ++r) cand_push_m<T, MODE, SGN, KC>(acc, ca, al, cd, K, vv[r], dd[r], eta, sh);
+            for (int r = 0; r < 8; ++r) cand_push_m<T, MODE, SGN, KC>(acc, ca, al, cd, K, vv[r], dd[r], eta, sh, hi, camax);
         }
     }
     for (int64_t j0 = start; j0 < m; j0 += 4 * nthr) {
@@ -1200,7 +1233,7 @@ __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> 
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-            if (r < nr) cand_push_m<T, MODE, SGN, KC>(acc, ca, al, cd, K, vv[r], dd[r], eta, sh);
+            if (r < nr) cand_push_m<T, MODE, SGN, KC>(acc, ca, al, cd, K, vv[r], dd[r], eta, sh, hi, camax);
     }
 }
 
@@ -1334,11 +1367,16 @@ __global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb
     const SweepConsts<T> K0 = sweep_consts<T>(st);
     const T eta_sgn = sd.sign > 0 ? K0.eta : -K0.eta;
     Lse<T> acc{T(0), T(0)};
+    const T hi = sd.sign > 0 ? t_inf<T>() : K0.hi;   // dropped covering rows leave the sums
+    T vmin = t_inf<T>();
     if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
-        for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < sd.m; j += (int64_t)nbs * blockDim.x)
-            lse_push(acc, sd.v[j], eta_sgn, sd.sign);
+        for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < sd.m; j += (int64_t)nbs * blockDim.x) {
+            const T vj = sd.v[j];
+            vmin = fmin(vmin, vj);
+            if (vj < hi) lse_push(acc, vj, eta_sgn, sd.sign);
+        }
     }
-    lse_block_record(p, acc, eta_sgn, sd.sign);
+    lse_block_record(p, acc, eta_sgn, sd.sign, vmin);
     if (last_block_done(&st->counter[0])) {
         finalize_reductions(p, gP, gridDim.x, nb_var, true, 0.0);
         if (threadIdx.x == 0) st->counter[0] = 0;
@@ -1353,8 +1391,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
     DevState *st = p.st;
     // in a captured iteration the Newton and backoff passes belong to
     // k_cand_newton, the first kernel of each turn of the search loop
-    const bool searching =
-        external || (st->phase != PH_DONE && !(p.cond_on && (st->phase == PH_NEWTON || st->phase == PH_BACKOFF)));
+    const bool searching = external || (st->phase != PH_DONE && st->phase != PH_COVER &&
+                                        !(p.cond_on && (st->phase == PH_NEWTON || st->phase == PH_BACKOFF)));
     if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) st->loop_launches += 1;
     if (st->status != ST_RUNNING || !searching) {
         if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) loop_turn_end(st, p.cond);
@@ -1371,6 +1409,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
         s_sc.K = K;
         s_sc.mode = newton ? 3 : external ? 2 : (st->phase == PH_EXP ? 0 : st->phase == PH_REFINE ? 1 : 2);
         s_sc.cd = (T)((st->ub - st->lb) / (K + 1) * st->eta);
+        s_sc.hi = (T)st->act_hi;
         s_eta = (T)st->eta;
         s_sh[0] = (T)st->s[0];
         s_sh[1] = (T)st->s[1];
@@ -1476,7 +1515,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
                 st->status = ST_NUMERIC;
                 st->numeric_bad = 2;
             } else if (!external) {
-                if (newton) newton_decide(st, fin[0][0][0], fin[1][0][0], st->dpsi, st->dphi);
+                if (newton) newton_decide(st, fin[0][0][0], fin[1][0][0], st->dpsi, st->dphi, zmk[0]);
                 else if (st->phase == PH_BACKOFF) backoff_decide(st, ok[0]);
                 else search_decide(st, ok, zmk);
             }
@@ -1496,10 +1535,17 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
 // phases it hands the turn to k_cand through the IF node that follows it, and
 // after its own pass it skips k_cand and sets the loop condition itself.
 template <class T>
+__device__ void cover_pass(const Problem<T> &p, int gP);
+
+template <class T>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(Problem<T> p, int gP) {
     DevState *st = p.st;
     const int phase = st->phase;
     if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) st->loop_launches += 1;
+    if (st->status == ST_RUNNING && phase == PH_COVER) {
+        cover_pass(p, gP);
+        return;
+    }
     if (st->status != ST_RUNNING || (phase != PH_NEWTON && phase != PH_BACKOFF)) {
         if (p.cond_on && blockIdx.x == 0 && threadIdx.x == 0) {
             const bool kc = st->status == ST_RUNNING && phase != PH_DONE;
@@ -1512,13 +1558,14 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(P
     const int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
     const int nbs = s == 0 ? gP : gridDim.x - gP;
     const Side<T> &sd = p.side[s];
-    __shared__ T s_c[5];
+    __shared__ T s_c[6];
     if (threadIdx.x == 0) {
         s_c[0] = (T)st->eta;
         s_c[1] = (T)st->s[0];
         s_c[2] = (T)st->s[1];
         s_c[3] = (T)(st->alpha[0] * st->eta);
         s_c[4] = (T)st->alpha[0];
+        s_c[5] = (T)st->act_hi;
     }
     __syncthreads();
     const T eta = s_c[0];
@@ -1529,6 +1576,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(P
     sc.ca[0] = s_c[3];
     sc.al[0] = s_c[4];
     sc.cd = T(0);
+    sc.hi = s_c[5];
     CandAcc<T> acc;
     cand_init(acc, sd.sign);
     const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x;
@@ -1577,10 +1625,64 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 5 : 2) k_cand_newton(P
             st->status = ST_NUMERIC;
             st->numeric_bad = 2;
         } else if (phase == PH_NEWTON) {
-            newton_decide(st, psi, phi, st->dpsi, st->dphi);
+            newton_decide(st, psi, phi, st->dpsi, st->dphi, st->zmink[0]);
         } else {
             backoff_decide(st, phi >= psi);
         }
+        if (p.cond_on) {
+            cudaGraphSetConditional(p.cond_kc, 0u);
+            loop_turn_end(st, p.cond);
+        }
+        st->counter[2] = 0;
+    }
+}
+
+// The pass after a Newton value alpha that passed and covered every row:
+// alpha_c = max over the open covering rows (z_j < 1) of (1 - z_j)/dz_j, the
+// smallest step that covers them all (+inf if an open row has dz_j <= 0), and
+// the search ends with max(1, min(alpha, alpha_c)): by Prop. 4.2 it passes,
+// as alpha_c <= alpha and 1 <= alpha do.
+template <class T>
+__device__ void cover_pass(const Problem<T> &p, int gP) {
+    DevState *st = p.st;
+    const Side<T> &C = p.side[1];
+    T mr = T(0);
+    if (blockIdx.x >= gP && C.rv.kind != RK_DENSE1 && C.rv.kind != RK_NONE) {
+        const int64_t nthr = (int64_t)(gridDim.x - gP) * blockDim.x;
+        for (int64_t j = (int64_t)(blockIdx.x - gP) * blockDim.x + threadIdx.x; j < C.m; j += nthr) {
+            const T v = C.v[j];
+            if (v < T(1)) {
+                const T dv = C.dv[j];
+                mr = fmax(mr, dv > T(0) ? (T(1) - v) / dv : t_inf<T>());
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) mr = fmax(mr, shfl_x(mr, off));
+    __shared__ T wmax[BLOCK / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T b = wmax[0];
+        for (int w = 1; w < BLOCK / 32; ++w) b = fmax(b, wmax[w]);
+        rec_of<T>(p.part_row, blockIdx.x)[0] = b;
+    }
+    if (!last_block_done(&st->counter[2])) return;
+    T gm = T(0);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) gm = fmax(gm, rec_of<T>(p.part_row, b)[0]);
+    for (int off = 16; off > 0; off >>= 1) gm = fmax(gm, shfl_x(gm, off));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = gm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ac = (double)wmax[0];
+        for (int w = 1; w < BLOCK / 32; ++w) ac = fmax(ac, (double)wmax[w]);
+        if (C.rv.kind == RK_DENSE1) {   // the single objective row: its own covering step
+            const double v = st->dense_v[1], dv = st->dense_dv[1];
+            ac = v >= 1.0 ? 0.0 : (dv > 0.0 ? (1.0 - v) / dv : (double)INFINITY);
+        }
+        st->passes += 1;
+        st->total_passes += 1;
+        search_finish(st, fmax(1.0, fmin(st->alpha[0], ac)));
         if (p.cond_on) {
             cudaGraphSetConditional(p.cond_kc, 0u);
             loop_turn_end(st, p.cond);
@@ -1604,6 +1706,8 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
     const SweepConsts<T> K0 = sweep_consts<T>(st);
     const T eta_sgn = sd.sign > 0 ? K0.eta : -K0.eta;
     const T a = K0.alpha_acc;
+    const T hi = sd.sign > 0 ? t_inf<T>() : K0.hi;   // dropped covering rows leave the sums
+    T vmin = t_inf<T>();
     Lse<T> acc{T(0), T(0)};
     if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
         const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x, nthr = (int64_t)nbs * blockDim.x;
@@ -1614,24 +1718,27 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
                 float4 d4 = *reinterpret_cast<const float4 *>(sd.dv + j0);
                 v4.x += (float)a * d4.x; v4.y += (float)a * d4.y; v4.z += (float)a * d4.z; v4.w += (float)a * d4.w;
                 *reinterpret_cast<float4 *>(sd.v + j0) = v4;
-                lse_push(acc, (T)v4.x, eta_sgn, sd.sign);
-                lse_push(acc, (T)v4.y, eta_sgn, sd.sign);
-                lse_push(acc, (T)v4.z, eta_sgn, sd.sign);
-                lse_push(acc, (T)v4.w, eta_sgn, sd.sign);
+                const T vv[4] = {(T)v4.x, (T)v4.y, (T)v4.z, (T)v4.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    vmin = fmin(vmin, vv[r]);
+                    if (vv[r] < hi) lse_push(acc, vv[r], eta_sgn, sd.sign);
+                }
             } else {
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     if (r >= nr) break;
                     T vj = sd.v[j0 + r] + a * sd.dv[j0 + r];
                     sd.v[j0 + r] = vj;
-                    lse_push(acc, vj, eta_sgn, sd.sign);
+                    vmin = fmin(vmin, vj);
+                    if (vj < hi) lse_push(acc, vj, eta_sgn, sd.sign);
                 }
             }
         }
     }
     // block record in T, then one completion level: the last block merges the
     // records of both sides (warp per side) and runs the stopping test
-    lse_block_record(p, acc, eta_sgn, sd.sign);
+    lse_block_record(p, acc, eta_sgn, sd.sign, vmin);
     if (last_block_done(&st->counter[3])) {
         if (threadIdx.x == 0) {
             st->iter += 1;
@@ -1927,9 +2034,12 @@ __global__ void __launch_bounds__(BLOCK) k_cand_static(Scratch *scr, const float
     cand_init(acc, sign);
     const float eta_f = (float)eta, sh = (float)shift;
     const int64_t r0 = (int64_t)blockIdx.x * RPB, r1 = min(m, r0 + RPB);
+    const float camax = sched_camax(sc.ca, sc.K);
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-        if (sign > 0) cand_push_m<float, 2, 1, 0>(acc, sc.ca, sc.al, sc.cd, sc.K, v[j], dv[j], eta_f, sh);
-        else cand_push_m<float, 2, -1, 0>(acc, sc.ca, sc.al, sc.cd, sc.K, v[j], dv[j], eta_f, sh);
+        if (sign > 0)
+            cand_push_m<float, 2, 1, 0>(acc, sc.ca, sc.al, sc.cd, sc.K, v[j], dv[j], eta_f, sh, sc.hi, camax);
+        else
+            cand_push_m<float, 2, -1, 0>(acc, sc.ca, sc.al, sc.cd, sc.K, v[j], dv[j], eta_f, sh, sc.hi, camax);
     }
     // block merge (as in k_cand), record to the static array
     __shared__ double wm[BLOCK / 32][KMAX][4];
@@ -2038,6 +2148,7 @@ extern "C" int mwu_candidates_static(const float *v, const float *dv, int64_t m,
     sc.K = K;
     sc.mode = 2;
     sc.cd = 0.0f;
+    sc.hi = INFINITY;   // every row of the given side counts
     for (int k = 0; k < KMAX; ++k) {
         double a = k < K ? alphas[k] : 0.0;
         sc.ca[k] = (float)(a * eta);

@@ -42,7 +42,8 @@ class mwu_options(C.Structure):
                 ("outer_tol", C.c_double), ("max_probes", C.c_int32), ("use_graph", C.c_int32),
                 ("check_every", C.c_int32), ("group", C.c_int32), ("timing", C.c_int32),
                 ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p),
-                ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("batch_workers", C.c_int32)]
+                ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("batch_workers", C.c_int32),
+                ("drop_covered", C.c_int32)]
 
 
 class mwu_iter_stats(C.Structure):

@@ -121,7 +121,7 @@ def run_direction_checks(M, ctx, wl, prec, ch):
     # factor of at most e^{2 eta e_v} (v and its shift both move by <= e_v)
     sc = M.mwu_get_scalars(ctx)
     s_p, S_p = om.lse_shift_sum(ch.y, eta, +1)
-    s_c, S_c = om.lse_shift_sum(ch.z, eta, -1)
+    s_c, S_c = om.lse_shift_sum(getattr(ch, "za", ch.z), eta, -1)   # the active covering rows
     assert abs(sc["s_p"] - s_p) <= ey and abs(sc["s_c"] - s_c) <= ez
     tw_p = rel + 1.1 * math.expm1(2 * eta * ey)
     tw_c = rel + 1.1 * math.expm1(2 * eta * ez)
