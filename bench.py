@@ -51,6 +51,8 @@ def parse():
                     choices=["densest-rmat18", "bmatching-batch256", "domset-rmat20", "vcover-rmat24",
                              "gmatch-200kx8k"],
                     help="densest-rmat18 is the headline line; the others measure the remaining configurations")
+    ap.add_argument("--rules", default="",
+                    help="--step-table: comma-separated subset of the step rules (default: all)")
     ap.add_argument("--step-table", action="store_true",
                     help="the step-rule comparison of Table 2 on rgg-18 (one probe per LP and rule) instead of a bench line")
     ap.add_argument("--eager", action="store_true",
@@ -529,6 +531,8 @@ def run_step_table(args):
         spec = lpspec.from_workload(wl)
         row = {"vertices": wl.graph.n, "edges": wl.graph.m}
         for name, opts in rules:
+            if args.rules and name not in args.rules.split(","):
+                continue
             ctx = M.mwu_create(*spec, eps=wl.eps, **opts)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
