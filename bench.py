@@ -49,7 +49,7 @@ def parse():
                     help="step-size search: K candidates per pass (Alg. 3 generalised) or Newton (Sec. 4.2)")
     ap.add_argument("--workload", default="densest-rmat18",
                     choices=["densest-rmat18", "bmatching-batch256", "domset-rmat20", "vcover-rmat24",
-                             "gmatch-200kx8k"],
+                             "gmatch-200kx8k", "matching-rgg18", "domset-rgg18", "vcover-rgg18", "densest-rgg18"],
                     help="densest-rmat18 is the headline line; the others measure the remaining configurations")
     ap.add_argument("--rules", default="",
                     help="--step-table: comma-separated subset of the step rules (default: all)")
@@ -447,14 +447,23 @@ def run_other(args):
     else:
         wl = {"domset-rmat20": lambda: W.domset(20, seed=3, device="cuda"),
               "vcover-rmat24": lambda: W.vcover(24, seed=5, device="cuda"),
-              "gmatch-200kx8k": lambda: W.gmatch(200_000, 8_000, seed=6, device="cuda")}[args.workload]()
+              "gmatch-200kx8k": lambda: W.gmatch(200_000, 8_000, seed=6, device="cuda"),
+              "matching-rgg18": lambda: W.rgg_lp("matching", scale=18, seed=7, device="cuda"),
+              "domset-rgg18": lambda: W.rgg_lp("domset", scale=18, seed=7, device="cuda"),
+              "vcover-rgg18": lambda: W.rgg_lp("vcover", scale=18, seed=7, device="cuda"),
+              "densest-rgg18": lambda: W.rgg_lp("densest", scale=18, seed=7, device="cuda")}[args.workload]()
         kind, P, C, obj = lpspec.from_workload(wl)
-        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop))
+        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop), timing=1)
         E = wl.graph.m
-        cfg = {"workload": args.workload, "lp": {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
-                                                 "vcover-rmat24": "vertex cover, M^T x >= 1 implicit",
-                                                 "gmatch-200kx8k": "generalized matching, lb <= M x <= ub (users lb 3 "
-                                                                   "ub 5, items ub 200), feasibility"}[args.workload],
+        lp_names = {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
+                    "vcover-rmat24": "vertex cover, M^T x >= 1 implicit",
+                    "gmatch-200kx8k": "generalized matching, lb <= M x <= ub (users lb 3 ub 5, items ub 200), "
+                                      "feasibility",
+                    "matching-rgg18": "fractional matching M x <= 1 on a random geometric graph",
+                    "domset-rgg18": "dominating set on a random geometric graph",
+                    "vcover-rgg18": "vertex cover on a random geometric graph",
+                    "densest-rgg18": "densest subgraph on a random geometric graph"}
+        cfg = {"workload": args.workload, "lp": lp_names[args.workload],
                "vertices": wl.graph.n, "edges": E, "eps": wl.eps}
 
         def solve():
@@ -466,6 +475,8 @@ def run_other(args):
             cfg["ratio_maxPx_minCx"] = solve_status["objective"]
     for _ in range(args.warmup):
         solve()
+    if not batch:
+        M.mwu_get_timing(ctx, reset=True)
     clocks = ClockSampler(local_rank)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -495,6 +506,10 @@ def run_other(args):
             "iters_per_step": sum(o[1] for o in out) / args.steps,
             "probes_per_step": sum(o[2] for o in out) / args.steps,
             "clocks": clk, "roofline": None}
+    if not batch:
+        tim = M.mwu_get_timing(ctx)
+        nit = max(1, tim["iters"])
+        line["per_class_ms_per_iter"] = {k: tim[f"{k}_ms"] / nit for k in ("dir", "spmv", "cand", "update")}
     M.mwu_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)

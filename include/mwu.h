@@ -142,6 +142,12 @@ typedef struct {
                                   never decreases, so the active rows are those with
                                   (Cx)_j < 1.  0 (default): every row is kept, as the
                                   paper's implementation does (Sec. 4)                     */
+    int32_t spmv_tiles;        /* forward SpMV of an explicit or incidence CSR side: 0
+                                  (default) stages each tile of rows' input window in
+                                  shared memory when the columns of 90 % of the tiles
+                                  span at most 12288 (FP32) / 6144 (FP64) entries, as on
+                                  banded matrices (the CSB-like tiles of Sec. 5.1); -1
+                                  always uses the row-binned gather kernel               */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
@@ -277,6 +283,11 @@ int mwu_get_scalars(mwu_ctx *ctx, mwu_scalars *out);
 
 /* Accumulated per-kernel-class times (see mwu_timing); reset != 0 clears them. */
 int mwu_get_timing(mwu_ctx *ctx, mwu_timing *out, int32_t reset);
+
+/* Tiles of the staged forward SpMV of each side (opt.spmv_tiles): *tiles_p and
+ * *tiles_c (host, may be NULL) receive the number of row tiles of P and C, 0
+ * where the side uses the row-binned kernel (or has no CSR rows). */
+int mwu_spmv_tiles(mwu_ctx *ctx, int32_t *tiles_p, int32_t *tiles_c);
 
 /* --------------------------------------- smoothed potential (autograd) */
 /* pot = smax_eta(P x) - smin_eta(C x) at the given x (device, n float32) with

@@ -117,6 +117,7 @@ int mwu_default_options(mwu_options *o) {
     o->newton_tol = 0.0;   // 0 -> eps / 20
     o->batch_workers = 0;  // 0 -> tuned online
     o->drop_covered = 0;
+    o->spmv_tiles = 0;     // automatic
     o->timing = 0;
     o->stop_rule = 0;
     o->grad_tol = -1.0;   // precision default
@@ -298,6 +299,20 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
             sb.rv.seg_beg = d_sbeg;
             sb.rv.n_seg = ns;
         }
+        // staged SpMV for banded matrices: tiles of 4 row steps of a block; taken
+        // when at least 90 % of the tiles' input windows fit in shared memory
+        if (c->opt.spmv_tiles >= 0 && sb.rv.rows > 0) {
+            const int tr = 4 * (BLOCK / sb.rv.G);
+            const int wmax = c->fp64 ? tile_wmax<double>() : tile_wmax<float>();
+            int32_t *tlo = nullptr, *tlen = nullptr, nt = 0, fit = 0;
+            TRY_CUDA(c, build_tiles(c->ar, sb.rv.ptr, sb.rv.idx, sb.rv.rows, tr, wmax, &tlo, &tlen, &nt, &fit, s));
+            if (nt > 0 && (double)fit >= 0.9 * (double)nt) {
+                sb.rv.n_tiles = nt;
+                sb.rv.tile_rows = tr;
+                sb.rv.tile_lo = tlo;
+                sb.rv.tile_len = tlen;
+            }
+        }
     }
     if (sb.cv.kind == CK_CSR) sb.cv.heavy_len = heavy_len_for(sb.cv.G);
     return MWU_OK;
@@ -346,6 +361,7 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.grid_upd = std::max(2, c->n_sms * std::min(upd_bps, row_bps));
     p.grid_spmv = std::max(2, c->n_sms * std::min(8, spmv_blocks_per_sm<T>()));
     p.grid_newton = std::max(2, c->n_sms * std::min(8, newton_blocks_per_sm<T>()));
+    p.grid_tiled = std::max(1, c->n_sms * tiled_blocks_per_sm<T>());
     p.cond_on = 0;
     p.cond = 0;
     p.cond_kc = 0;
@@ -877,6 +893,15 @@ int mwu_get_timing(mwu_ctx *c, mwu_timing *out, int32_t reset) {
     if (!c) return MWU_ERR_INVALID;
     if (out) *out = c->tim;
     if (reset) c->tim = mwu_timing{};
+    return MWU_OK;
+}
+
+int mwu_spmv_tiles(mwu_ctx *c, int32_t *tiles_p, int32_t *tiles_c) {
+    if (!c || c->kind < 0) return MWU_ERR_INVALID;
+    int32_t t[2];
+    for (int s = 0; s < 2; ++s) t[s] = c->fp64 ? c->pd.side[s].rv.n_tiles : c->pf.side[s].rv.n_tiles;
+    if (tiles_p) *tiles_p = t[0];
+    if (tiles_c) *tiles_c = t[1];
     return MWU_OK;
 }
 

@@ -60,7 +60,16 @@ struct RowView {
     int32_t n_seg = 0, n_long = 0;
     const int32_t *seg_row = nullptr, *seg_beg = nullptr;     // per segment: its row and first entry
     const int32_t *long_rows = nullptr, *long_seg = nullptr;  // per long row: row id; segments [long_seg[i], long_seg[i+1])
+    // staged SpMV (banded matrices): tiles of tile_rows consecutive rows whose
+    // entries' columns span [tile_lo[t], tile_lo[t] + tile_len[t]); a tile
+    // with a span of at most tile_wmax<T>() reads its input window from shared
+    // memory.  n_tiles > 0 selects the staged SpMV for this side.
+    int32_t n_tiles = 0, tile_rows = 0;
+    const int32_t *tile_lo = nullptr, *tile_len = nullptr;
 };
+
+constexpr int TILE_SMEM = 48 * 1024;   // shared memory of one tile's input window
+template <class T> constexpr int tile_wmax() { return TILE_SMEM / (int)sizeof(T); }
 
 constexpr int SHORT_LEN = 16;
 constexpr int MED_LEN = 256;
@@ -159,6 +168,7 @@ struct Problem {
     int32_t grid_upd;             // grid of the update kernel
     int32_t grid_spmv;            // grid of the forward SpMV (its own occupancy)
     int32_t grid_newton;          // grid of the one-candidate Newton pass (its own occupancy)
+    int32_t grid_tiled;           // grid of the staged SpMV (its own occupancy)
     // a captured iteration: the handle of its step-search WHILE loop, which the
     // direction kernel opens and every turn of the loop sets (0 = not captured),
     // and the handle of the IF node inside the loop body that runs the
@@ -202,5 +212,6 @@ void set_global_error(const char *msg);
 template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_bps);
 template <class T> int spmv_blocks_per_sm();
 template <class T> int newton_blocks_per_sm();
+template <class T> int tiled_blocks_per_sm();
 
 }  // namespace mwu

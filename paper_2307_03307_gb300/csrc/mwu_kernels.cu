@@ -1322,15 +1322,18 @@ __device__ __forceinline__ void spmv_side(const Problem<T> &p, int s, const T *_
 // thread.  Every gather loop keeps four independent loads in flight.  Segment
 // partials are added per row in a fixed order by the last block, so the
 // result does not depend on scheduling.
+// skip: bit s set -> side s is not computed here (written by the direction
+// kernel, or by the staged SpMV).
 template <class T>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<T> p, const T *__restrict__ in, int to_v,
-                                                                         int skip_c) {
+                                                                         int skip) {
     DevState *st = p.st;
     if (!to_v && st->status != ST_RUNNING) return;
     const SweepConsts<T> K0 = sweep_consts<T>(st);
-    spmv_side(p, 0, in, to_v, K0.scale0);
-    if (!skip_c) spmv_side(p, 1, in, to_v, K0.scale1);
-    if (p.side[0].rv.n_seg == 0 && p.side[1].rv.n_seg == 0) return;
+    if (!(skip & 1)) spmv_side(p, 0, in, to_v, K0.scale0);
+    if (!(skip & 2)) spmv_side(p, 1, in, to_v, K0.scale1);
+    const int nseg0 = (skip & 1) ? 0 : p.side[0].rv.n_seg, nseg1 = (skip & 2) ? 0 : p.side[1].rv.n_seg;
+    if (nseg0 == 0 && nseg1 == 0) return;
     __shared__ bool s_last;
     __threadfence();
     __syncthreads();
@@ -1342,7 +1345,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<
     for (int s = 0; s < 2; ++s) {
         const Side<T> &sd = p.side[s];
         const RowView &rv = sd.rv;
-        if (rv.kind != RK_CSR) continue;
+        if (rv.kind != RK_CSR || ((skip >> s) & 1)) continue;
         T *out = to_v ? sd.v : sd.dv;
         const T scale = (T)st->scale[s];
         for (int i = threadIdx.x; i < rv.n_long; i += blockDim.x) {
@@ -1353,6 +1356,75 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<
         }
     }
     if (threadIdx.x == 0) st->counter[5] = 0;
+}
+
+// Sum over [beg, end) with stride `step` of val[k] * win[idx[k] - lo], the
+// input read from a shared-memory window; four independent index loads in
+// flight per lane.
+template <class T>
+__device__ __forceinline__ T strided_window_gather(const int32_t *idx, const float *val, const T *win, int lo, int beg,
+                                                   int end, int step) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int k = beg;
+    for (; k + 3 * step < end; k += 4 * step) {
+        const int i0 = idx[k] - lo, i1 = idx[k + step] - lo, i2 = idx[k + 2 * step] - lo, i3 = idx[k + 3 * step] - lo;
+        T t0 = win[i0], t1 = win[i1], t2 = win[i2], t3 = win[i3];
+        if (val) {
+            t0 *= (T)val[k]; t1 *= (T)val[k + step]; t2 *= (T)val[k + 2 * step]; t3 *= (T)val[k + 3 * step];
+        }
+        a0 += t0; a1 += t1; a2 += t2; a3 += t3;
+    }
+    for (; k < end; k += step) {
+        T t = win[idx[k] - lo];
+        if (val) t *= (T)val[k];
+        a0 += t;
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
+// Staged forward SpMV of one CSR side for banded matrices (the CSB-like tiles
+// of Sec. 5.1 on one GPU): each block takes tiles of consecutive rows, copies
+// the tile's input window [lo, lo + len) into shared memory with coalesced
+// loads, and gathers from there; G lanes per row.  A tile whose window does
+// not fit gathers from global memory.  Rows are summed whole, so no segment
+// pass follows.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_spmv_tiled(Problem<T> p, const T *__restrict__ in, int to_v, int s) {
+    DevState *st = p.st;
+    if (!to_v && st->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *win = reinterpret_cast<T *>(sm_raw);
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const Side<T> &sd = p.side[s];
+    const RowView &rv = sd.rv;
+    const T scale = s == 0 ? K0.scale0 : K0.scale1;
+    T *out = to_v ? sd.v : sd.dv;
+    const int G = rv.G;
+    const int lane = threadIdx.x & (G - 1);
+    const int nslot = BLOCK / G;
+    const int wslot = (threadIdx.x & ~31) / G;   // first row slot of this warp
+    const int sub = (threadIdx.x & 31) / G;
+    for (int t = blockIdx.x; t < rv.n_tiles; t += gridDim.x) {
+        const int64_t r0 = (int64_t)t * rv.tile_rows;
+        const int64_t r1 = min(sd.m, r0 + rv.tile_rows);
+        const int lo = rv.tile_lo[t], len = rv.tile_len[t];
+        const bool staged = len <= tile_wmax<T>();
+        __syncthreads();   // the previous tile's rows are done with the window
+        if (staged)
+            for (int k = threadIdx.x; k < len; k += BLOCK) win[k] = in[lo + k];
+        __syncthreads();
+        for (int64_t jb = r0 + wslot; jb < r1; jb += nslot) {   // warp-uniform trip count
+            const int64_t j = jb + sub;
+            T sum = T(0);
+            if (j < r1) {
+                const int kb = rv.ptr[j], ke = rv.ptr[j + 1];
+                sum = staged ? strided_window_gather(rv.idx, rv.val, win, lo, kb + lane, ke, G)
+                             : strided_gather(rv.idx, rv.val, in, kb + lane, ke, G);
+            }
+            sum = group_sum(sum, G);
+            if (j < r1 && lane == 0) out[j] = sum * row_coef(sd, j, scale);
+        }
+    }
 }
 
 // Log-sum-exp reductions of y and z at a new x (a2, a3): a stream over both
@@ -1827,24 +1899,39 @@ template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC,
 
 // grid of the forward SpMV: every block covers both sides; no more blocks than
 // the larger side has work items (a warp per segment, four rows per thread)
-template <class T> static int spmv_grid(const Problem<T> &p) {
+template <class T> static int spmv_grid(const Problem<T> &p, int skip) {
     auto need = [&](const Side<T> &sd) -> int64_t {
         if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) return 0;
         const int64_t items = sd.rv.kind == RK_CSR ? std::max<int64_t>(sd.m / 4, 32 * (int64_t)sd.rv.n_seg)
                                                    : (sd.m + 3) / 4;
         return (items + BLOCK - 1) / BLOCK;
     };
-    const int64_t n = std::max(need(p.side[0]), need(p.side[1]));
+    const int64_t n = std::max((skip & 1) ? 0 : need(p.side[0]), (skip & 2) ? 0 : need(p.side[1]));
     return (int)std::max<int64_t>(0, std::min<int64_t>(n, p.grid_spmv));
 }
 
-template <class T> static cudaError_t rows_at_x(const Problem<T> &p, int nb_var, cudaStream_t s) {
-    const int gs = spmv_grid(p);
-    if (gs > 0) {
-        k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.x, 1, 0);
+// out = A in on both sides (to_v: v = A x, else dv = A d): the staged kernel
+// for tiled CSR sides, the binned kernel for the rest; skip bit s leaves side s.
+template <class T> static cudaError_t spmv_sides(const Problem<T> &p, const T *in, int to_v, int skip, cudaStream_t s) {
+    for (int q = 0; q < 2; ++q) {
+        const RowView &rv = p.side[q].rv;
+        if (((skip >> q) & 1) || rv.kind != RK_CSR || rv.n_tiles <= 0) continue;
+        const int g = std::max(1, std::min(rv.n_tiles, p.grid_tiled));
+        k_spmv_tiled<T><<<g, BLOCK, TILE_SMEM, s>>>(p, in, to_v, q);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        skip |= 1 << q;
     }
+    if (skip == 3) return cudaSuccess;
+    const int gs = spmv_grid(p, skip);
+    if (gs == 0) return cudaSuccess;
+    k_spmv<T><<<gs, BLOCK, 0, s>>>(p, in, to_v, skip);
+    return cudaGetLastError();
+}
+
+template <class T> static cudaError_t rows_at_x(const Problem<T> &p, int nb_var, cudaStream_t s) {
+    cudaError_t e = spmv_sides(p, p.x, 1, 0, s);
+    if (e != cudaSuccess) return e;
     int gP, gC;
     split_rows(p, &gP, &gC, false);
     k_rows_lse<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, nb_var);
@@ -1885,10 +1972,7 @@ template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cuda
 }
 
 template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s, int skip_c) {
-    const int gs = spmv_grid(p);
-    if (gs == 0) return cudaSuccess;
-    k_spmv<T><<<gs, BLOCK, 0, s>>>(p, p.d, 0, skip_c);
-    return cudaGetLastError();
+    return spmv_sides(p, p.d, 0, skip_c ? 2 : 0, s);
 }
 
 template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s) {
@@ -1987,6 +2071,12 @@ template <class T> int spmv_blocks_per_sm() {
     return a > 0 ? a : 1;
 }
 
+template <class T> int tiled_blocks_per_sm() {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spmv_tiled<T>, BLOCK, TILE_SMEM);
+    return a > 0 ? a : 1;
+}
+
 #define MWU_INSTANTIATE(T)                                                                                     \
     template cudaError_t launch_x_init<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_x_set<T>(const Problem<T> &, const void *, int, cudaStream_t);                 \
@@ -2003,7 +2093,8 @@ template <class T> int spmv_blocks_per_sm() {
                                                    float *, float *, cudaStream_t);                            \
     template cudaError_t launch_copy_vec<T>(const T *, void *, int64_t, int, cudaStream_t);                    \
     template int sweep_blocks_per_sm<T>(int *, int *, int *);                                                  \
-    template int spmv_blocks_per_sm<T>();
+    template int spmv_blocks_per_sm<T>();                                                                      \
+    template int tiled_blocks_per_sm<T>();
 
 MWU_INSTANTIATE(float)
 MWU_INSTANTIATE(double)

@@ -277,6 +277,53 @@ cudaError_t bin_list(Arena &ar, const int32_t *ptr, int64_t rows, int lo, int hi
     return select_flagged(ar, flag, rows, list, count, s);
 }
 
+// one block per tile: min and max column over the tile's entries
+__global__ void k_tile_windows(const int32_t *ptr, const int32_t *idx, int64_t rows, int tile_rows, int wmax,
+                               int32_t *lo, int32_t *len, int *fit) {
+    __shared__ int s_lo[8], s_hi[8];
+    const int64_t t = blockIdx.x;
+    const int64_t r0 = t * tile_rows, r1 = r0 + tile_rows < rows ? r0 + tile_rows : rows;
+    int mn = INT32_MAX, mx = -1;
+    for (int64_t k = ptr[r0] + threadIdx.x; k < ptr[r1]; k += blockDim.x) {
+        const int c = idx[k];
+        mn = min(mn, c);
+        mx = max(mx, c);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if ((threadIdx.x & 31) == 0) { s_lo[threadIdx.x >> 5] = mn; s_hi[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { mn = min(mn, s_lo[w]); mx = max(mx, s_hi[w]); }
+        mn = min(mn, s_lo[0]);
+        mx = max(mx, s_hi[0]);
+        const int span = mx >= mn ? mx - mn + 1 : 0;
+        lo[t] = span > 0 ? mn : 0;
+        len[t] = span;
+        if (span <= wmax) atomicAdd(fit, 1);
+    }
+}
+
+cudaError_t build_tiles(Arena &ar, const int32_t *ptr, const int32_t *idx, int64_t rows, int tile_rows, int wmax,
+                        int32_t **lo, int32_t **len, int32_t *n_tiles, int32_t *fit, cudaStream_t s) {
+    const int64_t nt = (rows + tile_rows - 1) / tile_rows;
+    *n_tiles = (int32_t)nt;
+    *fit = 0;
+    if (nt <= 0) return cudaSuccess;
+    *lo = ar.alloc<int32_t>(nt);
+    *len = ar.alloc<int32_t>(nt);
+    int *d_fit = ar.alloc_tmp<int>(1);
+    if (!*lo || !*len || !d_fit) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(d_fit, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_tile_windows<<<(unsigned)nt, 256, 0, s>>>(ptr, idx, rows, tile_rows, wmax, *lo, *len, d_fit);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(fit, d_fit, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
 cudaError_t heavy_list2(Arena &ar, const int32_t *p1, int thr1, const int32_t *p2, int thr2, int64_t rows,
                         int32_t **list, int32_t *count, cudaStream_t s) {
     char *flag = ar.alloc_tmp<char>(rows > 0 ? rows : 1);

@@ -43,7 +43,7 @@ class mwu_options(C.Structure):
                 ("check_every", C.c_int32), ("group", C.c_int32), ("timing", C.c_int32),
                 ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p),
                 ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("batch_workers", C.c_int32),
-                ("drop_covered", C.c_int32)]
+                ("drop_covered", C.c_int32), ("spmv_tiles", C.c_int32)]
 
 
 class mwu_iter_stats(C.Structure):
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "mwu_get_vector": (C.c_int, [V, I32, V, I64, I32]),
         "mwu_get_scalars": (C.c_int, [V, P(mwu_scalars)]),
         "mwu_get_timing": (C.c_int, [V, P(mwu_timing), I32]),
+        "mwu_spmv_tiles": (C.c_int, [V, P(I32), P(I32)]),
         "mwu_potential": (C.c_int, [V, V, P(D), V, V, V]),
         "mwu_candidates_static": (C.c_int, [V, V, I64, I32, D, D, D, P(D), I32, P(D), P(D), V]),
         "mwu_create_batch": (C.c_int, [I32, P(mwu_matrix), P(mwu_options), P(V)]),
@@ -129,8 +130,8 @@ def exported_symbols():
     return ["mwu_default_options", "mwu_create", "mwu_destroy", "mwu_last_error", "mwu_set_target",
             "mwu_set_x", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_eval_newton", "mwu_search",
             "mwu_solve",
-            "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_potential", "mwu_candidates_static",
-            "mwu_create_batch", "mwu_solve_batch", "mwu_diag_one_minus_exp_neg"]
+            "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_spmv_tiles", "mwu_potential",
+            "mwu_candidates_static", "mwu_create_batch", "mwu_solve_batch", "mwu_diag_one_minus_exp_neg"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -287,6 +288,13 @@ def mwu_get_scalars(ctx):
     s = mwu_scalars()
     _check(ctx, load().mwu_get_scalars(ctx, C.byref(s)))
     return _as_dict(s)
+
+
+def mwu_spmv_tiles(ctx):
+    """(tiles of P, tiles of C) of the staged SpMV; 0 = the row-binned kernel."""
+    tp, tc = C.c_int32(), C.c_int32()
+    _check(ctx, load().mwu_spmv_tiles(ctx, C.byref(tp), C.byref(tc)))
+    return tp.value, tc.value
 
 
 def mwu_get_timing(ctx, reset=False):
