@@ -60,6 +60,8 @@ def parse():
                          "profilers that cannot see the kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--drop", action="store_true",
                     help="drop satisfied covering rows (the last step of Alg. 1/2's loop)")
+    ap.add_argument("--no-tiles", action="store_true",
+                    help="row-binned gather SpMV everywhere (no staged tiles for banded CSR sides)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -453,7 +455,8 @@ def run_other(args):
               "vcover-rgg18": lambda: W.rgg_lp("vcover", scale=18, seed=7, device="cuda"),
               "densest-rgg18": lambda: W.rgg_lp("densest", scale=18, seed=7, device="cuda")}[args.workload]()
         kind, P, C, obj = lpspec.from_workload(wl)
-        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop), timing=1)
+        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop), timing=1,
+                           spmv_tiles=-1 if args.no_tiles else 0)
         E = wl.graph.m
         lp_names = {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
                     "vcover-rmat24": "vertex cover, M^T x >= 1 implicit",
@@ -464,7 +467,9 @@ def run_other(args):
                     "vcover-rgg18": "vertex cover on a random geometric graph",
                     "densest-rgg18": "densest subgraph on a random geometric graph"}
         cfg = {"workload": args.workload, "lp": lp_names[args.workload],
-               "vertices": wl.graph.n, "edges": E, "eps": wl.eps}
+               "vertices": wl.graph.n, "edges": E, "eps": wl.eps,
+               "spmv": "staged tiles (P %d, C %d)" % M.mwu_spmv_tiles(ctx) if any(M.mwu_spmv_tiles(ctx))
+               else "row-binned gathers"}
 
         def solve():
             r = M.mwu_solve(ctx)

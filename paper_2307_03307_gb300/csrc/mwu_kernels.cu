@@ -1900,9 +1900,12 @@ template <class T> static void split_rows(const Problem<T> &p, int *gP, int *gC,
 // grid of the forward SpMV: every block covers both sides; no more blocks than
 // the larger side has work items (a warp per segment, four rows per thread)
 template <class T> static int spmv_grid(const Problem<T> &p, int skip) {
+    // threads the side can use: one per short row, MED_LANES per medium row and
+    // a warp per long-row segment (CSR); one per four rows otherwise
     auto need = [&](const Side<T> &sd) -> int64_t {
         if (sd.rv.kind == RK_DENSE1 || sd.rv.kind == RK_NONE) return 0;
-        const int64_t items = sd.rv.kind == RK_CSR ? std::max<int64_t>(sd.m / 4, 32 * (int64_t)sd.rv.n_seg)
+        const int64_t items = sd.rv.kind == RK_CSR ? (int64_t)sd.rv.n_short + (int64_t)MED_LANES * sd.rv.n_med +
+                                                         32 * (int64_t)sd.rv.n_seg
                                                    : (sd.m + 3) / 4;
         return (items + BLOCK - 1) / BLOCK;
     };
@@ -2071,7 +2074,11 @@ template <class T> int spmv_blocks_per_sm() {
     return a > 0 ? a : 1;
 }
 
+// Also raises the kernel's dynamic shared memory limit to the window size (its
+// static shared memory plus TILE_SMEM exceed the 48 KB default); it runs
+// before the first launch of a context.
 template <class T> int tiled_blocks_per_sm() {
+    cudaFuncSetAttribute(k_spmv_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
     int a = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spmv_tiled<T>, BLOCK, TILE_SMEM);
     return a > 0 ? a : 1;

@@ -19,9 +19,11 @@ pytestmark = pytest.mark.gpu
 PRECS = ["f32", "fp64"]
 
 
-def _x_for(P, n, prec, seed=3):
+def _x_for(P, C, n, prec, seed=3):
+    """A positive x at which the probe still runs (max Px and min Cx below 1)."""
     rng = np.random.default_rng(seed)
     x = om.x_init(P, 0.1) * rng.uniform(1.0, 40.0, n)
+    x *= min(1.0, 0.8 / max(float((P @ x).max()), float((C @ x).min())))
     return x.astype(np.float32 if prec == "f32" else np.float64)
 
 
@@ -44,7 +46,7 @@ def test_tiled_equals_oracle_and_binned_on_small_workloads(M, wls, kind, prec):
     wl = wls[kind]
     T = probe_target(wl)
     P, C, _ = H.oracle_matrices(wl, T)
-    x = _x_for(P, H.n_vars(wl), prec)
+    x = _x_for(P, C, H.n_vars(wl), prec)
     res = {}
     for mode in [0, -1]:
         ctx = make_ctx(M, wl, prec, spmv_tiles=mode)
@@ -76,7 +78,7 @@ def test_tiles_follow_locality(M, prec):
     for wl, tiled in [(W.rgg_lp("domset", scale=14, seed=7), True), (W.domset(14, seed=3), False)]:
         T = 0.3 * float(wl.objective.sum())
         P, C, _ = H.oracle_matrices(wl, T)
-        x = _x_for(P, H.n_vars(wl), prec)
+        x = _x_for(P, C, H.n_vars(wl), prec)
         ctx = make_ctx(M, wl, prec)
         try:
             assert (M.mwu_spmv_tiles(ctx)[1] > 0) == tiled, wl.lp
@@ -89,13 +91,13 @@ def test_tiles_follow_locality(M, prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_tiles_that_do_not_fit_gather_from_global(M, prec):
     """A banded covering matrix (rows j: columns j-3..j+3) with one wide row per
-    5000 (an extra column 20000 away): the tiles holding a wide row span more
+    10000 (an extra column 20000 away): the tiles holding a wide row span more
     than a window, the rest fit, so the side is tiled with a few unstaged tiles."""
     n = 40000
     rows, cols = [], []
     for j in range(n):
         cs = list(range(max(0, j - 3), min(n, j + 4)))
-        if j % 5000 == 0:
+        if j % 10000 == 0:
             cs.append((j + 20000) % n)
         cs = sorted(set(cs))
         rows.append(len(cs))
@@ -109,7 +111,7 @@ def test_tiles_that_do_not_fit_gather_from_global(M, prec):
     Cm = olp.csr_from_arrays(rowptr, colidx, None, (n, n))
     T = 0.3 * n
     Pm = olp.objective_row(np.ones(n), T)
-    x = _x_for(Pm, n, prec)
+    x = _x_for(Pm, Cm, n, prec)
     ctx = M.mwu_create(kind, P_, C_, obj, precision=M.PREC_FP64 if prec == "fp64" else M.PREC_F32_R64, eps=0.1)
     try:
         tiles = M.mwu_spmv_tiles(ctx)[1]
