@@ -455,7 +455,8 @@ def run_other(args):
               "vcover-rgg18": lambda: W.rgg_lp("vcover", scale=18, seed=7, device="cuda"),
               "densest-rgg18": lambda: W.rgg_lp("densest", scale=18, seed=7, device="cuda")}[args.workload]()
         kind, P, C, obj = lpspec.from_workload(wl)
-        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop), timing=1,
+        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop),
+                           timing=0 if args.eager else 1, use_graph=0 if args.eager else 1,
                            spmv_tiles=-1 if args.no_tiles else 0)
         E = wl.graph.m
         lp_names = {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
@@ -511,7 +512,7 @@ def run_other(args):
             "iters_per_step": sum(o[1] for o in out) / args.steps,
             "probes_per_step": sum(o[2] for o in out) / args.steps,
             "clocks": clk, "roofline": None}
-    if not batch:
+    if not batch and not args.eager:
         tim = M.mwu_get_timing(ctx)
         nit = max(1, tim["iters"])
         line["per_class_ms_per_iter"] = {k: tim[f"{k}_ms"] / nit for k in ("dir", "spmv", "cand", "update")}

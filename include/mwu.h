@@ -269,7 +269,10 @@ int mwu_search(mwu_ctx *ctx, double *alpha, int64_t *evals);
 /* ------------------------------------------------------- the whole solve */
 /* Bisect on M (or D) between lo and hi (<= 0: the automatic bracket of Sec.
  * 2.2 / Sec. 3) until hi <= (1+outer_tol) lo, one probe per midpoint, and
- * report the best certified objective.  MIXED runs a single probe. */
+ * report the best certified objective.  MIXED runs a single probe.  The
+ * automatic bracket is computed by the first mwu_solve of a context and
+ * reused: a caller that rewrites the objective or the matrix values in place
+ * passes lo and hi itself. */
 int mwu_solve(mwu_ctx *ctx, double lo, double hi, mwu_result *res);
 
 /* --------------------------------------------------------- read back */

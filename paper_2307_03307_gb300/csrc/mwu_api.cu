@@ -36,6 +36,8 @@ struct mwu_ctx {
     bool own_stream = false;
     cudaStream_t body_stream = nullptr;      // captures the body of the device-side search loop
     cudaStream_t kc_stream = nullptr;        // captures the body of the IF node inside it
+    bool bracket_ok = false;                 // automatic bracket of mwu_solve, once computed
+    double bracket_lo = 0.0, bracket_hi = 0.0;
     Arena ar;
     std::string err;
     int64_t n = 0, mP = 0, mC = 0;
@@ -85,6 +87,12 @@ template <class F> static cudaError_t with_prob(mwu_ctx *c, F f) {
 static int pow2_floor(double v) {
     int g = 1;
     while (g * 2 <= v && g < 32) g *= 2;
+    return g;
+}
+
+static int pow2_ceil(int v) {
+    int g = 1;
+    while (g < v && g < 32) g *= 2;
     return g;
 }
 
@@ -329,7 +337,7 @@ static void dense_side(SideBuild &sb, const float *c, int32_t sign) {
 
 template <class T>
 static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32_t *heavy_var, int32_t n_heavy_var,
-                         int G_var, int var_bps, int row_bps, int upd_bps) {
+                         int32_t *med_var, int32_t n_med_var, int G_var, int var_bps, int row_bps, int upd_bps) {
     p.n = c->n;
     p.x = c->ar.alloc<T>(c->n);
     p.d = c->ar.alloc<T>(c->n);
@@ -376,6 +384,8 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.heavy_var = heavy_var;
     p.n_heavy_var = n_heavy_var;
     p.heavy_var_len = 0;
+    p.med_var = med_var;
+    p.n_med_var = n_med_var;
     return MWU_OK;
 }
 
@@ -487,18 +497,26 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     }
     c->mP = sb[0].m;
     c->mC = sb[1].m;
-    // heavy variables (long CSR columns on either side)
+    // variables of CSR column views by column length: lanes per light variable
+    // from the 75th percentile of the lengths (power-law graphs have a mean
+    // far above the typical column), G_var lanes covering four loads each;
+    // light columns up to 16 G_var entries, medium up to HEAVY_LEN (a warp
+    // each), heavy beyond (a block each)
     int G_var = 1;
-    for (int s = 0; s < 2; ++s)
-        if (sb[s].cv.kind == CK_CSR) G_var = std::max(G_var, sb[s].cv.G);
-    for (int s = 0; s < 2; ++s)
-        if (sb[s].cv.kind == CK_CSR) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = heavy_len_for(G_var); }
-    int32_t *hv = nullptr, nhv = 0;
-    if (sb[0].cv.kind == CK_CSR || sb[1].cv.kind == CK_CSR) {
-        cudaError_t e = heavy_list2(c->ar, sb[0].cv.kind == CK_CSR ? sb[0].cv.ptr : nullptr, sb[0].cv.heavy_len,
-                                    sb[1].cv.kind == CK_CSR ? sb[1].cv.ptr : nullptr, sb[1].cv.heavy_len, c->n, &hv,
-                                    &nhv, c->stream);
-        if (e != cudaSuccess) { fail_cuda(c, e, "heavy variable list"); return bail(MWU_ERR_CUDA); }
+    int32_t *hv = nullptr, nhv = 0, *mv = nullptr, nmv = 0;
+    const int32_t *cp0 = sb[0].cv.kind == CK_CSR ? sb[0].cv.ptr : nullptr;
+    const int32_t *cp1 = sb[1].cv.kind == CK_CSR ? sb[1].cv.ptr : nullptr;
+    if (cp0 || cp1) {
+        int lq = 1;
+        cudaError_t e = length_quantile2(c->ar, cp0, cp1, c->n, 0.75, &lq, c->stream);
+        if (e != cudaSuccess) { fail_cuda(c, e, "column length quantile"); return bail(MWU_ERR_CUDA); }
+        G_var = c->opt.group > 0 ? c->opt.group : std::max(1, std::min(32, pow2_ceil((lq + 3) / 4)));
+        const int light = std::min(16 * G_var, HEAVY_LEN);
+        for (int s = 0; s < 2; ++s)
+            if (sb[s].cv.kind == CK_CSR) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = light; }
+        e = heavy_list2(c->ar, cp0, HEAVY_LEN, cp1, HEAVY_LEN, c->n, &hv, &nhv, c->stream);
+        if (e == cudaSuccess) e = range_list2(c->ar, cp0, cp1, c->n, light, HEAVY_LEN, &mv, &nmv, c->stream);
+        if (e != cudaSuccess) { fail_cuda(c, e, "variable length classes"); return bail(MWU_ERR_CUDA); }
     }
     // device state
     c->st_dev = c->ar.alloc<DevState>(1);
@@ -514,8 +532,13 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         return bail(MWU_ERR_CUDA);
     }
     int vb = 1, rb = 1, ub = 1;
-    if (c->fp64) { sweep_blocks_per_sm<double>(&vb, &rb, &ub); rc = alloc_problem(c, c->pd, sb, hv, nhv, G_var, vb, rb, ub); }
-    else { sweep_blocks_per_sm<float>(&vb, &rb, &ub); rc = alloc_problem(c, c->pf, sb, hv, nhv, G_var, vb, rb, ub); }
+    if (c->fp64) {
+        sweep_blocks_per_sm<double>(&vb, &rb, &ub);
+        rc = alloc_problem(c, c->pd, sb, hv, nhv, mv, nmv, G_var, vb, rb, ub);
+    } else {
+        sweep_blocks_per_sm<float>(&vb, &rb, &ub);
+        rc = alloc_problem(c, c->pf, sb, hv, nhv, mv, nmv, G_var, vb, rb, ub);
+    }
     if (rc != MWU_OK) return bail(rc);
     c->x_best = c->ar.raw((size_t)c->n * (c->fp64 ? sizeof(double) : sizeof(float)));
     if (!c->x_best) { c->err = "allocating best x"; return bail(MWU_ERR_OOM); }
@@ -1098,7 +1121,22 @@ static int certify(mwu_ctx *c, double *cert) {
     return MWU_OK;
 }
 
+static int auto_bracket_compute(mwu_ctx *c, double *lo, double *hi);
+
+// The automatic bracket depends on the matrices and the objective only, which
+// a context keeps: it is computed by the first solve and reused.
 static int auto_bracket(mwu_ctx *c, double *lo, double *hi) {
+    if (!c->bracket_ok) {
+        int rc = auto_bracket_compute(c, &c->bracket_lo, &c->bracket_hi);
+        if (rc != MWU_OK) return rc;
+        c->bracket_ok = true;
+    }
+    *lo = c->bracket_lo;
+    *hi = c->bracket_hi;
+    return MWU_OK;
+}
+
+static int auto_bracket_compute(mwu_ctx *c, double *lo, double *hi) {
     double a = 0, b = 0, dmax = 0;
     cudaStream_t s = c->stream;
     auto side_views = [&](int sd, RowView &rv, ColView &cv, int64_t &m) {

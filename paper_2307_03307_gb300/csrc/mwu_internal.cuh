@@ -69,6 +69,7 @@ struct RowView {
 };
 
 constexpr int TILE_SMEM = 48 * 1024;   // shared memory of one tile's input window
+constexpr int HEAVY_LEN = 4096;        // columns longer than this take a whole block in the direction kernel
 template <class T> constexpr int tile_wmax() { return TILE_SMEM / (int)sizeof(T); }
 
 constexpr int SHORT_LEN = 16;
@@ -176,10 +177,15 @@ struct Problem {
     int32_t cond_on;
     cudaGraphConditionalHandle cond;
     cudaGraphConditionalHandle cond_kc;
-    int32_t G_var;      // lanes per variable for CSR column views
+    // variables of CSR column views by column length (the longer of the two
+    // sides): light ones (<= the views' heavy_len) take G_var lanes in the
+    // main loop, medium ones (<= HEAVY_LEN) a warp each, heavy ones a block each
+    int32_t G_var;
     int32_t heavy_var_len;
     int32_t n_heavy_var;
     const int32_t *heavy_var;
+    int32_t n_med_var;
+    const int32_t *med_var;
 };
 
 // ---------------------------------------------------------------- launchers

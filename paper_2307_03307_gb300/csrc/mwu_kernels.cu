@@ -246,19 +246,32 @@ template <class T> struct WeightFn {
 };
 
 // Column-view gather for variable i: sum_j A_ji w_j (without the side's scale).
-// Simple kinds are computed by lane 0 of the group only.
-template <class T, class F>
+// Simple kinds are computed by lane 0 of the group only.  Unless ALL, a CSR
+// column longer than heavy_len gives 0 (the medium and heavy paths take it).
+template <class T, bool ALL = false, class F>
 __device__ __forceinline__ T col_gather(const ColView &cv, int64_t i, int lane, int G, const F &w, T dense_w) {
     T acc = T(0);
     switch (cv.kind) {
     case CK_CSR: {
         int beg = cv.ptr[i], end = cv.ptr[i + 1];
-        if (end - beg > cv.heavy_len) return T(0);   // heavy variable: block path
-        for (int k = beg + lane; k < end; k += G) {
+        if (!ALL && end - beg > cv.heavy_len) return T(0);
+        // four independent gathers of v (and their exponentials) in flight per lane
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int k = beg + lane;
+        for (; k + 3 * G < end; k += 4 * G) {
+            const int j0 = cv.idx[k], j1 = cv.idx[k + G], j2 = cv.idx[k + 2 * G], j3 = cv.idx[k + 3 * G];
+            T t0 = w(j0), t1 = w(j1), t2 = w(j2), t3 = w(j3);
+            if (cv.val) {
+                t0 *= (T)cv.val[k]; t1 *= (T)cv.val[k + G]; t2 *= (T)cv.val[k + 2 * G]; t3 *= (T)cv.val[k + 3 * G];
+            }
+            a0 += t0; a1 += t1; a2 += t2; a3 += t3;
+        }
+        for (; k < end; k += G) {
             T t = w(cv.idx[k]);
             if (cv.val) t *= (T)cv.val[k];
-            acc += t;
+            a0 += t;
         }
+        acc = (a0 + a1) + (a2 + a3);
         break;
     }
     case CK_FIXED2:
@@ -663,6 +676,18 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
         if (C.cv.kind == CK_CSR) sh = heavy_col_gather<T>(C.cv, i, wc, sm);
         else { sh = col_gather<T>(C.cv, i, threadIdx.x, 1 << 30, wc, T(1)); sh = block_sum(threadIdx.x == 0 ? sh : T(0), sm); }
         if (threadIdx.x == 0) finish(i, sg, sh);
+    }
+    {   // medium variables: a warp each (warp-uniform loop)
+        const int wl = threadIdx.x & 31;
+        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < p.n_med_var; q += nw) {
+            const int64_t i = p.med_var[q];
+            T sg = col_gather<T, true>(P.cv, i, wl, 32, wp, T(1));
+            T sh = col_gather<T, true>(C.cv, i, wl, 32, wc, T(1));
+            sg = group_sum(sg, 32);
+            sh = group_sum(sh, 32);
+            if (wl == 0) finish(i, sg, sh);
+        }
     }
     int G = p.G_var, lane = threadIdx.x & (G - 1);
     int64_t per_block = blockDim.x / G;

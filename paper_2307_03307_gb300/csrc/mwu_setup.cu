@@ -139,6 +139,33 @@ __global__ void k_heavy_flags2(const int32_t *p1, int thr1, const int32_t *p2, i
     }
 }
 
+// rows whose longer column over the two views has a length in (lo, hi]
+__global__ void k_range_flags2(const int32_t *p1, const int32_t *p2, int64_t rows, int lo, int hi, char *flag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < rows; j += (int64_t)gridDim.x * blockDim.x) {
+        int len = 0;
+        if (p1) len = max(len, p1[j + 1] - p1[j]);
+        if (p2) len = max(len, p2[j + 1] - p2[j]);
+        flag[j] = len > lo && len <= hi;
+    }
+}
+
+// Histogram of the longer column length per row in power-of-two buckets:
+// bucket 0 holds lengths 0 and 1, bucket b > 0 lengths in (2^(b-1), 2^b].
+__global__ void k_len_hist(const int32_t *p1, const int32_t *p2, int64_t rows, unsigned long long *hist) {
+    __shared__ unsigned int h[33];
+    if (threadIdx.x < 33) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < rows; j += (int64_t)gridDim.x * blockDim.x) {
+        int len = 0;
+        if (p1) len = max(len, p1[j + 1] - p1[j]);
+        if (p2) len = max(len, p2[j + 1] - p2[j]);
+        const int b = len <= 1 ? 0 : 32 - __clz(len - 1);
+        atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
 // Exclusive scan of counts[0..n) into ptr[0..n] (ptr[n] = total), int32.
 static cudaError_t scan_counts(Arena &ar, const int32_t *cnt, int32_t *ptr, int64_t n, cudaStream_t s) {
     size_t tmp = 0;
@@ -322,6 +349,35 @@ cudaError_t build_tiles(Arena &ar, const int32_t *ptr, const int32_t *idx, int64
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(fit, d_fit, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
+}
+
+cudaError_t range_list2(Arena &ar, const int32_t *p1, const int32_t *p2, int64_t rows, int lo, int hi,
+                        int32_t **list, int32_t *count, cudaStream_t s) {
+    char *flag = ar.alloc_tmp<char>(rows > 0 ? rows : 1);
+    if (!flag) return cudaErrorMemoryAllocation;
+    k_range_flags2<<<g1d(rows), 256, 0, s>>>(p1, p2, rows, lo, hi, flag);
+    return select_flagged(ar, flag, rows, list, count, s);
+}
+
+cudaError_t length_quantile2(Arena &ar, const int32_t *p1, const int32_t *p2, int64_t rows, double q, int *len_q,
+                             cudaStream_t s) {
+    unsigned long long *d_h = ar.alloc_tmp<unsigned long long>(33);
+    if (!d_h) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(d_h, 0, 33 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_len_hist<<<g1d(rows), 256, 0, s>>>(p1, p2, rows, d_h);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned long long h[33];
+    if ((e = cudaMemcpyAsync(h, d_h, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    const double want = q * (double)rows;
+    double acc = 0.0;
+    *len_q = 1;
+    for (int b = 0; b < 33; ++b) {
+        acc += (double)h[b];
+        if (acc >= want) { *len_q = b == 0 ? 1 : (b >= 31 ? INT32_MAX : (1 << b)); break; }
+    }
+    return cudaSuccess;
 }
 
 cudaError_t heavy_list2(Arena &ar, const int32_t *p1, int thr1, const int32_t *p2, int thr2, int64_t rows,

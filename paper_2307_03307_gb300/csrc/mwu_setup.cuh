@@ -81,6 +81,14 @@ cudaError_t bin_list(Arena &ar, const int32_t *ptr, int64_t rows, int lo, int hi
                      cudaStream_t s);
 cudaError_t heavy_list2(Arena &ar, const int32_t *p1, int thr1, const int32_t *p2, int thr2, int64_t rows,
                         int32_t **list, int32_t *count, cudaStream_t s);
+// rows whose longer column (of the views p1, p2; either may be NULL) has a
+// length in (lo, hi], in increasing order
+cudaError_t range_list2(Arena &ar, const int32_t *p1, const int32_t *p2, int64_t rows, int lo, int hi,
+                        int32_t **list, int32_t *count, cudaStream_t s);
+// *len_q = the power-of-two upper end of the bucket holding quantile q of the
+// longer column lengths
+cudaError_t length_quantile2(Arena &ar, const int32_t *p1, const int32_t *p2, int64_t rows, double q, int *len_q,
+                             cudaStream_t s);
 // Tile plan of a CSR row view for the staged SpMV: tiles of tile_rows
 // consecutive rows; per tile the first column and the column span of its
 // entries (0 for an empty tile).  *fit = tiles whose span is at most wmax.
