@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying captured iterations (for "
                          "profilers that cannot see the kernel nodes of graphs with conditional nodes)")
+    ap.add_argument("--one-iteration", action="store_true",
+                    help="profiling aid: after a warm-up solve, run 10 eager iterations of a probe at 1.1 x the "
+                         "certified density and then one more inside the NVTX range 'mwu_iteration' "
+                         "(ncu --nvtx --nvtx-include mwu_iteration/ captures exactly its kernels)")
     ap.add_argument("--drop", action="store_true",
                     help="drop satisfied covering rows (the last step of Alg. 1/2's loop)")
     ap.add_argument("--no-tiles", action="store_true",
@@ -215,6 +219,22 @@ def run_ours(args):
     step = M.STEP_NEWTON if args.step == "newton" else M.STEP_KARY
     ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, timing=0 if args.eager else 1, step=step,
                        use_graph=0 if args.eager else 1, drop_covered=int(args.drop))
+    if args.one_iteration:
+        r = M.mwu_solve(ctx)
+        M.mwu_destroy(ctx)
+        ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, use_graph=0, drop_covered=int(args.drop))
+        M.mwu_set_target(ctx, 1.1 * r["objective"])
+        M.mwu_iterate(ctx, 10)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("mwu_iteration")
+        rc, st = M.mwu_iterate(ctx, 1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        M.mwu_destroy(ctx)
+        print(json.dumps({"one_iteration": {"workload": f"densest-rmat{args.scale}", "target": 1.1 * r["objective"],
+                                            "status": st["status"], "iters": st["iters"],
+                                            "last_passes": st["last_passes"], "alpha": st["alpha"]}}), flush=True)
+        return
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
