@@ -492,11 +492,12 @@ class MWUResult:
     eta: float
     c_d: float
     alphas: list
+    drift: list = field(default_factory=list)   # (iteration, max rel. |y - Px|, max rel. |z - Cx|)
 
 
 def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_passes=64,
         double_single=True, warm_start=False, x0=None, on_iter=None, stop_rule=0, grad_tol=0.0, max_newton=8,
-        newton_tol=None, ratio_stop=0.0, drop_covered=False):
+        newton_tol=None, ratio_stop=0.0, drop_covered=False, drift_every=64):
     """MWU_STEPSIZE_SEARCH (Alg. 2) on explicit P (m_P x n) and C (m_C x n).
 
     Per iteration: test, g and h, d, max(d) = 0 -> INFEASIBLE, dy = Pd and
@@ -523,6 +524,11 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
     (alpha = 1, Alg. 1).
     ``grad_tol`` is the tolerance of the gradient test (see ``direction``).
 
+    ``drift_every``: every that many iterations y and z are recomputed from x
+    and the largest relative difference to the incrementally updated ones is
+    logged in ``drift`` (a diagnostic: the iterates keep the incremental
+    values, as Alg. 2 updates y and z by alpha dy and alpha dz).
+
     ``drop_covered`` keeps only the unsatisfied covering rows, the last step
     of the loop of Alg. 1 and Alg. 2 (C <- {c_j : c_j^T x < 1}), where the
     default keeps every row as the paper's own implementation does (Sec. 4).
@@ -544,6 +550,7 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
     z = C @ x
     it = evals = passes = 0
     alphas = []
+    drift = []
     alpha_prev = None
     reason = ""
     while True:
@@ -606,9 +613,13 @@ def mwu(P, C, eps, *, eta_factor=10.0, step="kary", K=8, max_iter=5000, max_pass
         alphas.append(alpha)
         alpha_prev = alpha
         it += 1
+        if drift_every and it % drift_every == 0:
+            yx, zx = P @ x, C @ x
+            drift.append((it, float(np.max(np.abs(y - yx) / np.maximum(np.abs(yx), 1e-300))),
+                          float(np.max(np.abs(z - zx) / np.maximum(np.abs(zx), 1e-300)))))
         if on_iter is not None:
             on_iter(it, x, y, z, alpha)
-    return MWUResult(x, y, z, status, reason, it, evals, passes, eta, c_d, alphas)
+    return MWUResult(x, y, z, status, reason, it, evals, passes, eta, c_d, alphas, drift)
 
 
 # ----------------------------------------------------------------------------

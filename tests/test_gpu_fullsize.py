@@ -183,3 +183,43 @@ def test_fullsize_vcover_rmat24_sampled(M):
         assert (xs >= 0).all()
     finally:
         M.mwu_destroy(ctx)
+
+
+def test_fullsize_vcover_rmat24_duality_bracket(M):
+    """C5 whole solve at full size through weak LP duality.  The fractional
+    vertex cover LP (min 1^T x, M^T x >= 1) and the fractional matching LP on
+    the same graph (max 1^T y, M y <= 1) are dual, so any certified matching
+    value is a lower bound and any certified cover value an upper bound on the
+    common optimum.  Both solves run on the GPU (K = 8 search); both
+    certificates are computed here, in FP64 on the host, from the returned x
+    and y alone.  Each certified value lies within (1+eps)^2 of the optimum,
+    so the bracket is at most (1+eps)^4 wide."""
+    from paper_2307_03307_gb300 import lpspec
+    wl = W.vcover(24, seed=5, device="cuda")
+    g = wl.graph
+    n, E = g.n, g.m
+    kind, P, C, obj = lpspec.from_workload(wl)
+    ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, K=8)
+    try:
+        res = M.mwu_solve(ctx)
+        x = vec(M, ctx, M.VEC_X, n)
+    finally:
+        M.mwu_destroy(ctx)
+    kind_m, Pm, Cm, objm = lpspec.bmatch_lp(n, g.edge_pairs())
+    ctx = M.mwu_create(kind_m, Pm, Cm, objm, eps=wl.eps, K=8)
+    try:
+        resm = M.mwu_solve(ctx)
+        y = vec(M, ctx, M.VEC_X, E)
+    finally:
+        M.mwu_destroy(ctx)
+    u = g.u.cpu().numpy()
+    v = g.v.cpu().numpy()
+    assert (x >= 0).all() and (y >= 0).all()
+    cover_min = float((x[u] + x[v]).min())
+    cert_vc = float(x.sum()) / cover_min
+    load = np.bincount(u, weights=y, minlength=n) + np.bincount(v, weights=y, minlength=n)
+    cert_m = float(y.sum()) / float(load.max())
+    assert cert_vc == pytest.approx(res["objective"], rel=1e-4)
+    assert cert_m == pytest.approx(resm["objective"], rel=1e-4)
+    assert cert_m <= cert_vc * (1 + 1e-9), (cert_m, cert_vc)          # weak duality
+    assert cert_vc <= (1 + wl.eps) ** 4 * cert_m, (cert_m, cert_vc)

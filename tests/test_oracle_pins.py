@@ -710,3 +710,18 @@ def test_newton_early_exit_when_step_covers():
     evn4 = lambda a: (1.0, 2.0, 0.0, 0.0)
     a, info = mwu.search_newton(evn4, ev, EPS, K=8, alpha0=3.0 * t, max_passes=4)
     assert a == 3.0 * t * 256.0 ** 3 and info.passes == 4
+
+
+def test_incremental_y_z_drift_is_rounding_only():
+    """Alg. 2 updates y and z by alpha dy and alpha dz instead of recomputing
+    Px and Cx; the oracle logs the drift every 64 iterations: FP64 rounding
+    only (a wrong dy, dz or update would show at once)."""
+    n, u, v = _cycle(30)
+    A = lp.incidence(n, u, v).T.tocsr()
+    r = mwu.mwu(lp.objective_row(np.ones(n), 0.6 * n), A, EPS, step="standard", drift_every=16)
+    assert r.iters > 64 and len(r.drift) >= 4
+    assert max(max(dy, dz) for _, dy, dz in r.drift) < 1e-12
+    g = gg.rmat(7, seed=5)
+    A = lp.incidence(g.n, g.u, g.v).T.tocsr()
+    r = mwu.mwu(lp.objective_row(np.ones(g.n), 0.6 * g.n), A, EPS, step="kary", drift_every=4)
+    assert len(r.drift) >= 2 and max(max(dy, dz) for _, dy, dz in r.drift) < 1e-12
