@@ -93,7 +93,9 @@ enum { MWU_STEP_KARY = 0,      /* K candidates per pass (Alg. 3 generalised; K =
        MWU_STEP_NEWTON = 3 };  /* Newton's method on f(alpha) = 1 (Sec. 4.2): warm start from
                                   the previous alpha (else the exponential phase), one
                                   candidate and Psi', Phi' per pass, then the (1-eps)^p
-                                  backoff, K values per pass                                */
+                                  backoff, one value per pass; a passing value that covers
+                                  every row ends the search with the smallest covering step
+                                  (Alg. 3's early exit)                                     */
 enum { MWU_PREC_F32_R64 = 0,   /* FP32 vectors and per-element math, FP64 reductions         */
        MWU_PREC_FP64 = 1 };    /* everything FP64, one candidate per pass, host-driven search*/
 

@@ -376,10 +376,7 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     size_t recs = (size_t)std::max(std::max(p.grid_var, p.grid_newton), std::max(p.grid_row, p.grid_upd)) + 8;
     p.part_var = c->ar.alloc<double>((int64_t)(recs * REC));
     p.part_row = c->ar.alloc<double>((int64_t)(recs * REC));
-    p.part_grp = c->ar.alloc<double>((int64_t)2 * GRP_MAX * REC);
-    if (!p.part_var || !p.part_row || !p.part_grp) return fail(c, MWU_ERR_OOM, "allocating partial buffers");
-    if (std::max(std::max(p.grid_row, p.grid_newton), p.grid_upd) > GRP * GRP_MAX)
-        return fail(c, MWU_ERR_INVALID, "grid too large for the group tickets");
+    if (!p.part_var || !p.part_row) return fail(c, MWU_ERR_OOM, "allocating partial buffers");
     p.G_var = G_var;
     p.heavy_var = heavy_var;
     p.n_heavy_var = n_heavy_var;
@@ -596,8 +593,6 @@ static void reset_probe_fields(DevState &h) {
     h.total_passes = 0;
     h.n_pos = 0;
     for (int k = 0; k < 8; ++k) h.counter[k] = 0;
-    for (int r = 0; r < 2; ++r)
-        for (int g = 0; g < GRP_MAX; ++g) h.grp_counter[r][g] = 0;
 }
 
 static int probe_status(const DevState &h) {

@@ -20,8 +20,6 @@ namespace mwu {
 constexpr int KMAX = 8;           // candidates per pass (compile-time bound)
 constexpr int BLOCK = 256;        // threads per block of the sweep kernels
 constexpr int REC = 72;           // doubles per per-block partial record
-constexpr int GRP = 16;           // blocks per group of the two-level completion
-constexpr int GRP_MAX = 128;      // groups (grids up to 2048 blocks)
 
 // Row views (constraint rows of one side, for y = A x).
 enum RowKind : int32_t {
@@ -152,8 +150,6 @@ struct DevState {
     long long evals, total_passes;
     // last-block-done counters
     unsigned int counter[8];
-    // per-group tickets of the two-level completion (row 0: candidate passes, row 1: update)
-    unsigned int grp_counter[2][GRP_MAX];
 };
 
 template <class T>
@@ -164,7 +160,6 @@ struct Problem {
     DevState *st;
     double *part_var;   // per-block records of variable-side kernels
     double *part_row;   // per-block records of row-side kernels
-    double *part_grp;   // per-group records (2 x GRP_MAX x REC): candidate passes, update
     int32_t grid_var, grid_row;   // grid sizes (blocks): variable kernels, candidate passes
     int32_t grid_upd;             // grid of the update kernel
     int32_t grid_spmv;            // grid of the forward SpMV (its own occupancy)
