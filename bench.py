@@ -19,7 +19,13 @@ HBM bandwidth against the measured peak, and the oracle timed on host cores.
 """
 from __future__ import annotations
 
-import argparse
+import os
+
+# before torch initialises CUDA: more hardware work queues for the concurrent
+# streams of the batched solve (see the package's __init__)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+import argparse  # noqa: E402
 import json
 import math
 import os
