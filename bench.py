@@ -70,6 +70,8 @@ def parse():
                          "(ncu --nvtx --nvtx-include mwu_iteration/ captures exactly its kernels)")
     ap.add_argument("--drop", action="store_true",
                     help="drop satisfied covering rows (the last step of Alg. 1/2's loop)")
+    ap.add_argument("--h-scatter", action="store_true",
+                    help="vertex cover: h by an edge scatter with atomic adds (not bit-reproducible)")
     ap.add_argument("--no-tiles", action="store_true",
                     help="row-binned gather SpMV everywhere (no staged tiles for banded CSR sides)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
@@ -483,7 +485,7 @@ def run_other(args):
         kind, P, C, obj = lpspec.from_workload(wl)
         ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop),
                            timing=0 if args.eager else 1, use_graph=0 if args.eager else 1,
-                           spmv_tiles=-1 if args.no_tiles else 0)
+                           spmv_tiles=-1 if args.no_tiles else 0, h_scatter=int(args.h_scatter))
         E = wl.graph.m
         lp_names = {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
                     "vcover-rmat24": "vertex cover, M^T x >= 1 implicit",
@@ -495,6 +497,7 @@ def run_other(args):
                     "densest-rgg18": "densest subgraph on a random geometric graph"}
         cfg = {"workload": args.workload, "lp": lp_names[args.workload],
                "vertices": wl.graph.n, "edges": E, "eps": wl.eps,
+               "h": "edge scatter (atomic adds)" if args.h_scatter else "gather",
                "spmv": "staged tiles (P %d, C %d)" % M.mwu_spmv_tiles(ctx) if any(M.mwu_spmv_tiles(ctx))
                else "row-binned gathers"}
 

@@ -126,6 +126,7 @@ int mwu_default_options(mwu_options *o) {
     o->batch_workers = 0;  // 0 -> tuned online
     o->drop_covered = 0;
     o->spmv_tiles = 0;     // automatic
+    o->h_scatter = 0;
     o->timing = 0;
     o->stop_rule = 0;
     o->grad_tol = -1.0;   // precision default
@@ -383,6 +384,15 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.heavy_var_len = 0;
     p.med_var = med_var;
     p.n_med_var = n_med_var;
+    p.hacc = nullptr;
+    if (c->opt.h_scatter && sb[1].rv.kind == RK_FIXED2 && sb[1].cv.kind == CK_CSR) {
+        p.hacc = c->ar.alloc<T>(c->n);
+        if (!p.hacc) return fail(c, MWU_ERR_OOM, "allocating the scatter sums");
+        if (cudaMemsetAsync(p.hacc, 0, sizeof(T) * (size_t)c->n, c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, MWU_ERR_CUDA, "clearing the scatter sums");
+        }
+    }
     return MWU_OK;
 }
 
@@ -884,7 +894,8 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             // direction, SpMV and update per captured iteration, plus the kernels
             // the search loops ran (counted on the device)
-            c->launches += (int64_t)n * 3 + (c->st_host->loop_launches - loop0);
+            c->launches += (int64_t)n * (3 + (c->fp64 ? c->pd.hacc != nullptr : c->pf.hacc != nullptr)) +
+                           (c->st_host->loop_launches - loop0);
             if (c->opt.timing &&
                 (rc = accumulate_timing(c, chunk ? c->ev : c->ev_one, c->st_host->iter - iter0)) != MWU_OK)
                 return rc;

@@ -157,6 +157,7 @@ struct Problem {
     Side<T> side[2];
     int64_t n;          // variables
     T *x, *d, *g, *h;   // g, h may be nullptr (not kept)
+    T *hacc;            // per-variable sums of k_h_scatter (option h_scatter), else nullptr
     DevState *st;
     double *part_var;   // per-block records of variable-side kernels
     double *part_row;   // per-block records of row-side kernels

@@ -640,6 +640,8 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
     WeightFn<T> wp{P.v, P.rv.rdiv, K0.eta, K0.s0, t_inf<T>()};
     // the potential of Sec. 4.1 always takes every row
     WeightFn<T> wc{C.v, C.rv.rdiv, -K0.eta, K0.s1, potential_mode ? t_inf<T>() : K0.hi};
+    // h from k_h_scatter's sums (read once and cleared for the next iteration)
+    T *const hacc = potential_mode ? nullptr : p.hacc;
     const T fp = K0.fp, fc = K0.fc, cd = K0.cd, thr = K0.thr;
     int npos = 0;   // positives of this thread
     T dense_dot[2] = {T(0), T(0)}, dense_cmp[2] = {T(0), T(0)};   // compensated per thread
@@ -673,9 +675,13 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
         T sg, sh;
         if (P.cv.kind == CK_CSR) sg = heavy_col_gather<T>(P.cv, i, wp, sm);
         else { sg = col_gather<T>(P.cv, i, threadIdx.x, 1 << 30, wp, T(1)); sg = block_sum(threadIdx.x == 0 ? sg : T(0), sm); }
-        if (C.cv.kind == CK_CSR) sh = heavy_col_gather<T>(C.cv, i, wc, sm);
+        if (hacc) { sh = hacc[i]; }
+        else if (C.cv.kind == CK_CSR) sh = heavy_col_gather<T>(C.cv, i, wc, sm);
         else { sh = col_gather<T>(C.cv, i, threadIdx.x, 1 << 30, wc, T(1)); sh = block_sum(threadIdx.x == 0 ? sh : T(0), sm); }
-        if (threadIdx.x == 0) finish(i, sg, sh);
+        if (threadIdx.x == 0) {
+            if (hacc) hacc[i] = T(0);
+            finish(i, sg, sh);
+        }
     }
     {   // medium variables: a warp each (warp-uniform loop)
         const int wl = threadIdx.x & 31;
@@ -683,10 +689,13 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
         for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < p.n_med_var; q += nw) {
             const int64_t i = p.med_var[q];
             T sg = col_gather<T, true>(P.cv, i, wl, 32, wp, T(1));
-            T sh = col_gather<T, true>(C.cv, i, wl, 32, wc, T(1));
+            T sh = hacc ? (wl == 0 ? hacc[i] : T(0)) : col_gather<T, true>(C.cv, i, wl, 32, wc, T(1));
             sg = group_sum(sg, 32);
             sh = group_sum(sh, 32);
-            if (wl == 0) finish(i, sg, sh);
+            if (wl == 0) {
+                if (hacc) hacc[i] = T(0);
+                finish(i, sg, sh);
+            }
         }
     }
     int G = p.G_var, lane = threadIdx.x & (G - 1);
@@ -703,12 +712,15 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
                     (C.cv.kind == CK_CSR && C.cv.ptr[i + 1] - C.cv.ptr[i] > C.cv.heavy_len);
             if (!heavy) {
                 sg = col_gather<T>(P.cv, i, lane, G, wp, T(1));
-                sh = col_gather<T>(C.cv, i, lane, G, wc, T(1));
+                sh = hacc ? (lane == 0 ? hacc[i] : T(0)) : col_gather<T>(C.cv, i, lane, G, wc, T(1));
             }
         }
         sg = group_sum(sg, G);
         sh = group_sum(sh, G);
-        if (live && lane == 0 && !heavy) finish(i, sg, sh);
+        if (live && lane == 0 && !heavy) {
+            if (hacc) hacc[i] = T(0);
+            finish(i, sg, sh);
+        }
     }
     if (potential_mode) return;
     // block partials: n_pos, dense dots
@@ -735,6 +747,56 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
             st->counter[1] = 0;
             if (p.cond_on) cudaGraphSetConditional(p.cond, search_continues(st));
         }
+    }
+}
+
+// ------------------------------------------------------------ h by edge scatter
+// h for a covering side whose rows are the edges (u, v) of an incidence
+// transpose (vertex cover, M^T x >= 1): one stream over the edges, each
+// adding its weight w_e = e^{-eta (z_e - s_c)} / rdiv_e to hacc[u] and hacc[v]
+// with atomic adds, instead of gathering z over every vertex's incident edges.
+// Runs of equal u in a warp (edge lists sorted by u) are summed with shuffles
+// first, so they cost one atomic each.  The sums' order depends on scheduling
+// (the option trades determinism for speed); k_dir reads and clears them.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_h_scatter(Problem<T> p) {
+    DevState *st = p.st;
+    if (st->status != ST_RUNNING) return;
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const Side<T> &C = p.side[1];
+    const int2 *ends = reinterpret_cast<const int2 *>(C.rv.idx);
+    const T eta = K0.eta, sc = K0.s1, hi = K0.hi;
+    const int lane = threadIdx.x & 31;
+    const int64_t m = C.m, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < m; e0 += stride) {   // warp-uniform
+        const int64_t e = e0 + lane;
+        const bool live = e < m;
+        T w = T(0);
+        int2 uv = make_int2(-1, -1);
+        if (live) {
+            uv = ends[e];
+            const T z = C.v[e];
+            if (z < hi) {
+                w = t_exp(-eta * (z - sc));
+                if (C.rv.rdiv) w /= (T)C.rv.rdiv[e];
+            }
+        }
+        // segmented inclusive sum over runs of equal u (lanes in order)
+        const int u = uv.x;
+        const int u_prev = __shfl_up_sync(0xffffffffu, u, 1);
+        const bool head = lane == 0 || u_prev != u;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        // first lane of this lane's run: the highest head at or below it
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        T run = w;
+        for (int off = 1; off < 32; off <<= 1) {
+            const T o = __shfl_up_sync(0xffffffffu, run, off);
+            if (lane - off >= start) run += o;
+        }
+        const int u_next = __shfl_down_sync(0xffffffffu, u, 1);
+        const bool tail = lane == 31 || u_next != u;
+        if (live && tail && run != T(0)) atomicAdd(&p.hacc[u], run);
+        if (live && w != T(0)) atomicAdd(&p.hacc[uv.y], w);
     }
 }
 
@@ -1991,6 +2053,12 @@ template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cuda
         int g = (int)std::max<int64_t>(1, std::min<int64_t>((p.n / 2 + BLOCK - 1) / BLOCK, p.grid_var));
         k_dir_pairs<T><<<g, BLOCK, 0, s>>>(p);
         return cudaGetLastError();
+    }
+    if (p.hacc) {   // h of the edge-row covering side by scatter, read by k_dir
+        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((p.side[1].m + BLOCK - 1) / BLOCK, p.grid_upd));
+        k_h_scatter<T><<<gs, BLOCK, 0, s>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
     int64_t per_block = BLOCK / p.G_var;
     int64_t need = std::max<int64_t>((p.n + per_block - 1) / per_block, p.n_heavy_var);

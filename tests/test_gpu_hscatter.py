@@ -1,0 +1,50 @@
+"""The edge-scatter form of h for vertex cover (option h_scatter: h = M w_c
+by one stream over the edges with atomic adds) against the oracle: one
+iteration's quantities from the oracle chain, and whole solves against the
+exact LP and the oracle's solve.  The sums' order varies, so the bounds are
+those of the gather form (propagated FP32 error), not bit equality."""
+import numpy as np
+import pytest
+
+from oracle import mwu as om
+from tests import _helpers as H
+from tests.test_gpu_parity import (M, wls, make_ctx, probe_target, vec, run_direction_checks,  # noqa: F401
+                                   Chain, check_step_decision, certificate_from_x, exact_opt)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["f32", "fp64"])
+def test_h_scatter_iteration_matches_oracle(M, wls, prec):
+    wl = wls["vcover"]
+    ctx = make_ctx(M, wl, prec, h_scatter=1)
+    try:
+        T = probe_target(wl)
+        M.mwu_set_target(ctx, T)
+        ch = Chain(wl, prec, T)
+        for _ in range(2):   # twice: k_dir clears the sums for the next direction
+            e = run_direction_checks(M, ctx, wl, prec, ch)
+        rc, alpha, ev = M.mwu_search(ctx)
+        K = 1 if prec == "fp64" else 8
+        ao, info = om.search_kary(ch.evaluate, wl.eps, K=K, max_passes=6 if K == 8 else 64)
+        check_step_decision(ch, e, prec, alpha, ao)
+    finally:
+        M.mwu_destroy(ctx)
+
+
+@pytest.mark.parametrize("step", ["kary", "newton"])
+@pytest.mark.parametrize("prec", ["f32", "fp64"])
+def test_h_scatter_solve_matches_oracle_and_exact(M, wls, prec, step):
+    wl = wls["vcover"]
+    ctx = make_ctx(M, wl, prec, h_scatter=1, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY)
+    try:
+        res = M.mwu_solve(ctx)
+        x = vec(M, ctx, M.VEC_X, H.n_vars(wl))
+    finally:
+        M.mwu_destroy(ctx)
+    cert = certificate_from_x(wl, x)
+    assert cert == pytest.approx(res["objective"], rel=1e-4)
+    opt = exact_opt(wl)
+    assert opt * (1 - 1e-9) <= cert <= opt * (1 + wl.eps) ** 2
+    ores = H.oracle_solve(wl, step=step)
+    assert 1 / (1 + wl.eps) <= cert / ores.objective <= 1 + wl.eps
