@@ -71,7 +71,8 @@ def parse():
     ap.add_argument("--drop", action="store_true",
                     help="drop satisfied covering rows (the last step of Alg. 1/2's loop)")
     ap.add_argument("--h-scatter", action="store_true",
-                    help="vertex cover: h by an edge scatter with atomic adds (not bit-reproducible)")
+                    help="vertex cover, dominating set: h by a scatter over C's rows with atomic adds "
+                         "(not bit-reproducible)")
     ap.add_argument("--no-tiles", action="store_true",
                     help="row-binned gather SpMV everywhere (no staged tiles for banded CSR sides)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
@@ -497,7 +498,7 @@ def run_other(args):
                     "densest-rgg18": "densest subgraph on a random geometric graph"}
         cfg = {"workload": args.workload, "lp": lp_names[args.workload],
                "vertices": wl.graph.n, "edges": E, "eps": wl.eps,
-               "h": "edge scatter (atomic adds)" if args.h_scatter else "gather",
+               "h": "row scatter (atomic adds)" if args.h_scatter else "gather",
                "spmv": "staged tiles (P %d, C %d)" % M.mwu_spmv_tiles(ctx) if any(M.mwu_spmv_tiles(ctx))
                else "row-binned gathers"}
 

@@ -151,12 +151,13 @@ typedef struct {
                                   banded matrices (the CSB-like tiles of Sec. 5.1); -1
                                   always uses the row-binned gather kernel               */
     int32_t h_scatter;         /* covering side of edge rows (MWU_MAT_INCIDENCE_T, vertex
-                                  cover): 1 computes h = M w_c by one stream over the
-                                  edges with atomic adds into per-vertex sums instead of a
-                                  gather of z over each vertex's incident edges.  Faster
-                                  on large graphs, but the sums' order, and so the last
-                                  bits of h and the iterates, vary from run to run.  0
-                                  (default): the deterministic gather                      */
+                                  cover) or an explicit CSR (dominating set): 1 computes
+                                  h = C^T w_c by one pass over C's rows with atomic adds
+                                  into per-variable sums instead of a gather of z over
+                                  each variable's column.  Faster on large graphs, but
+                                  the sums' order, and so the last bits of h and the
+                                  iterates, vary from run to run.  0 (default): the
+                                  deterministic gather                                     */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */

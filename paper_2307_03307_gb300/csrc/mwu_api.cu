@@ -385,7 +385,7 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.med_var = med_var;
     p.n_med_var = n_med_var;
     p.hacc = nullptr;
-    if (c->opt.h_scatter && sb[1].rv.kind == RK_FIXED2 && sb[1].cv.kind == CK_CSR) {
+    if (c->opt.h_scatter && (sb[1].rv.kind == RK_FIXED2 || sb[1].rv.kind == RK_CSR) && sb[1].cv.kind == CK_CSR) {
         p.hacc = c->ar.alloc<T>(c->n);
         if (!p.hacc) return fail(c, MWU_ERR_OOM, "allocating the scatter sums");
         if (cudaMemsetAsync(p.hacc, 0, sizeof(T) * (size_t)c->n, c->stream) != cudaSuccess) {

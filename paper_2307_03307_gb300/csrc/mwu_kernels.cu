@@ -758,14 +758,62 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
 // Runs of equal u in a warp (edge lists sorted by u) are summed with shuffles
 // first, so they cost one atomic each.  The sums' order depends on scheduling
 // (the option trades determinism for speed); k_dir reads and clears them.
+// A CSR covering side (explicit C, dominating set) scatters row j's weight
+// w_j val_jk into hacc[k] over the row's entries, with the SpMV's length bins
+// (a thread per short row, MED_LANES lanes per medium row, a warp per segment
+// of a long row).
+template <class T>
+__device__ void h_scatter_csr(const Problem<T> &p, T eta, T sc, T hi) {
+    const Side<T> &C = p.side[1];
+    const RowView &rv = C.rv;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+    auto wt = [&](int64_t j) -> T {
+        const T z = C.v[j];
+        if (!(z < hi)) return T(0);
+        T w = t_exp(-eta * (z - sc));
+        if (rv.rdiv) w /= (T)rv.rdiv[j];
+        return w;
+    };
+    auto put = [&](int k, T w) { atomicAdd(&p.hacc[rv.idx[k]], rv.val ? w * (T)rv.val[k] : w); };
+    {   // segments of long rows: a warp each
+        const int lane = threadIdx.x & 31;
+        for (int64_t i = tid >> 5; i < rv.n_seg; i += nthr >> 5) {
+            const int j = rv.seg_row[i];
+            const T w = wt(j);
+            if (w == T(0)) continue;
+            const int ke = min(rv.seg_beg[i] + SEG_LEN, rv.ptr[j + 1]);
+            for (int k = rv.seg_beg[i] + lane; k < ke; k += 32) put(k, w);
+        }
+    }
+    {   // medium rows: MED_LANES lanes each
+        const int lane = threadIdx.x & (MED_LANES - 1);
+        for (int64_t i = tid / MED_LANES; i < rv.n_med; i += nthr / MED_LANES) {
+            const int j = rv.med_rows[i];
+            const T w = wt(j);
+            if (w == T(0)) continue;
+            for (int k = rv.ptr[j] + lane; k < rv.ptr[j + 1]; k += MED_LANES) put(k, w);
+        }
+    }
+    for (int64_t i = tid; i < rv.n_short; i += nthr) {   // short rows: a thread each
+        const int j = rv.short_rows[i];
+        const T w = wt(j);
+        if (w == T(0)) continue;
+        for (int k = rv.ptr[j]; k < rv.ptr[j + 1]; ++k) put(k, w);
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(BLOCK) k_h_scatter(Problem<T> p) {
     DevState *st = p.st;
     if (st->status != ST_RUNNING) return;
     const SweepConsts<T> K0 = sweep_consts<T>(st);
     const Side<T> &C = p.side[1];
-    const int2 *ends = reinterpret_cast<const int2 *>(C.rv.idx);
     const T eta = K0.eta, sc = K0.s1, hi = K0.hi;
+    if (C.rv.kind == RK_CSR) {
+        h_scatter_csr(p, eta, sc, hi);
+        return;
+    }
+    const int2 *ends = reinterpret_cast<const int2 *>(C.rv.idx);
     const int lane = threadIdx.x & 31;
     const int64_t m = C.m, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < m; e0 += stride) {   // warp-uniform
@@ -2054,8 +2102,11 @@ template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cuda
         k_dir_pairs<T><<<g, BLOCK, 0, s>>>(p);
         return cudaGetLastError();
     }
-    if (p.hacc) {   // h of the edge-row covering side by scatter, read by k_dir
-        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((p.side[1].m + BLOCK - 1) / BLOCK, p.grid_upd));
+    if (p.hacc) {   // h of the covering side by scatter, read by k_dir
+        const RowView &rv = p.side[1].rv;
+        const int64_t items = rv.kind == RK_CSR ? (int64_t)rv.n_short + (int64_t)MED_LANES * rv.n_med + 32 * (int64_t)rv.n_seg
+                                                : p.side[1].m;
+        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((items + BLOCK - 1) / BLOCK, p.grid_upd));
         k_h_scatter<T><<<gs, BLOCK, 0, s>>>(p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

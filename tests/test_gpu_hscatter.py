@@ -1,5 +1,6 @@
-"""The edge-scatter form of h for vertex cover (option h_scatter: h = M w_c
-by one stream over the edges with atomic adds) against the oracle: one
+"""The scatter form of h (option h_scatter: h = C^T w_c by one pass over C's
+rows with atomic adds; vertex cover's edge rows, the explicit CSR rows of
+dominating set and of generalized matching's lower bounds) against the oracle: one
 iteration's quantities from the oracle chain, and whole solves against the
 exact LP and the oracle's solve.  The sums' order varies, so the bounds are
 those of the gather form (propagated FP32 error), not bit equality."""
@@ -15,8 +16,9 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("prec", ["f32", "fp64"])
-def test_h_scatter_iteration_matches_oracle(M, wls, prec):
-    wl = wls["vcover"]
+@pytest.mark.parametrize("kind", ["vcover", "domset", "gmatch"])
+def test_h_scatter_iteration_matches_oracle(M, wls, kind, prec):
+    wl = wls[kind]
     ctx = make_ctx(M, wl, prec, h_scatter=1)
     try:
         T = probe_target(wl)
@@ -34,8 +36,9 @@ def test_h_scatter_iteration_matches_oracle(M, wls, prec):
 
 @pytest.mark.parametrize("step", ["kary", "newton"])
 @pytest.mark.parametrize("prec", ["f32", "fp64"])
-def test_h_scatter_solve_matches_oracle_and_exact(M, wls, prec, step):
-    wl = wls["vcover"]
+@pytest.mark.parametrize("kind", ["vcover", "domset"])
+def test_h_scatter_solve_matches_oracle_and_exact(M, wls, kind, prec, step):
+    wl = wls[kind]
     ctx = make_ctx(M, wl, prec, h_scatter=1, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY)
     try:
         res = M.mwu_solve(ctx)
