@@ -8,6 +8,11 @@ they pin the oracle to something other than itself.
 * bipartite matching LP = maximum matching ............. no integrality gap on bipartite graphs (Sec. 3, match)
 * b-matching LP = max flow ............................. totally unimodular incidence matrix (Appendix A.1 with lb = 0)
 * densest-subgraph LP = max density .................... Charikar's LP is exact (Sec. 3, dense-sub)
+* a certified lower bound on the max density of large graphs: the density of
+  the best subgraph met while peeling (Bahmani, Kumar and Vassilvitskii's
+  parallel peeling: each round removes every vertex of degree at most
+  2 (1 + delta) times the current density; the best round is within a factor
+  2 (1 + delta) of the optimum)
 """
 from __future__ import annotations
 
@@ -102,6 +107,28 @@ def max_density_bruteforce(n, u, v):
     for a, b in zip(u.tolist(), v.tolist()):
         inside += ((masks >> a) & 1) & ((masks >> b) & 1)
     best = float((inside / size).max())
+    return best
+
+
+def densest_peel_lower_bound(n, u, v, delta=0.1):
+    """Density |E(S)|/|S| of the densest subgraph S met by parallel peeling: a
+    lower bound on the max density (S is a real subgraph) and at least
+    max density / (2 (1 + delta)).  Vectorised rounds over the edge list."""
+    u, v = _np(u).astype(np.int64), _np(v).astype(np.int64)
+    alive = np.ones(n, dtype=bool)
+    eu, ev = u, v
+    best = 0.0
+    while alive.any():
+        nv = int(alive.sum())
+        dens = eu.size / nv
+        best = max(best, dens)
+        if eu.size == 0:
+            break
+        deg = np.bincount(eu, minlength=n) + np.bincount(ev, minlength=n)
+        drop = alive & (deg <= 2.0 * (1.0 + delta) * dens)
+        alive &= ~drop
+        keep = alive[eu] & alive[ev]
+        eu, ev = eu[keep], ev[keep]
     return best
 
 

@@ -725,3 +725,21 @@ def test_incremental_y_z_drift_is_rounding_only():
     A = lp.incidence(g.n, g.u, g.v).T.tocsr()
     r = mwu.mwu(lp.objective_row(np.ones(g.n), 0.6 * g.n), A, EPS, step="kary", drift_every=4)
     assert len(r.drift) >= 2 and max(max(dy, dz) for _, dy, dz in r.drift) < 1e-12
+
+
+def test_densest_peel_lower_bound_brackets_the_optimum():
+    """The peeling bound is a real subgraph's density (<= the max density) and
+    within 2 (1 + delta) of it, on graphs with brute-force optima."""
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        n = 12
+        pairs = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.35]
+        if not pairs:
+            continue
+        u = np.array([p[0] for p in pairs])
+        v = np.array([p[1] for p in pairs])
+        opt = exact.max_density_bruteforce(n, u, v)
+        lb = exact.densest_peel_lower_bound(n, u, v, delta=0.1)
+        assert lb <= opt * (1 + 1e-12) and lb >= opt / (2 * 1.1) - 1e-12
+    n, u, v = _complete(7)                       # K_7: density 3, peeling keeps it whole
+    assert exact.densest_peel_lower_bound(n, np.asarray(u), np.asarray(v)) == pytest.approx(3.0)
