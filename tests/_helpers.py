@@ -13,7 +13,8 @@ from oracle import mwu as om
 
 EPS = 0.1
 
-# Tolerances ("Parity tolerances").
+# Relative tolerance of a product computed from identical inputs: a few FP32
+# roundings (FP32 form) or FP64 roundings (FP64 form).
 REL = {"f32": 1e-5, "fp64": 1e-12}
 
 

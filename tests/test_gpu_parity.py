@@ -1,9 +1,12 @@
 """Parity of every hot-path step of the CUDA library with the FP64 CPU oracle.
 
-Each step is fed the same inputs on both sides (the FP32 vectors the GPU
-produced, widened to FP64 for the oracle) and compared element by element:
-relative 1e-5 for the FP32 form and 1e-12 for the FP64 form, with the
-allowances for gradient-test flips and step decisions derived in the design doc.
+Both sides start from the same host-seeded x (drawn from the oracle's x0,
+rounded once to the form's precision); the oracle then runs its own chain of
+one iteration and no GPU value enters it.  Each GPU step is compared element
+by element with a bound propagated from the measured error of that step's
+inputs: relative 1e-5 (FP32 form) or 1e-12 (FP64 form) on the products, the
+softmax bound e^{2 eta e} - 1 on weights and sums, the cost of a gradient test
+decided differently on d, and the band around f = 1 for step decisions.
 """
 import math
 
