@@ -8,6 +8,7 @@ they pin the oracle to something other than itself.
 * bipartite matching LP = maximum matching ............. no integrality gap on bipartite graphs (Sec. 3, match)
 * b-matching LP = max flow ............................. totally unimodular incidence matrix (Appendix A.1 with lb = 0)
 * densest-subgraph LP = max density .................... Charikar's LP is exact (Sec. 3, dense-sub)
+* vertex cover LP of a general graph = half the maximum matching of its bipartite double cover
 * a certified lower bound on the max density of large graphs: the density of
   the best subgraph met while peeling (Bahmani, Kumar and Vassilvitskii's
   parallel peeling: each round removes every vertex of degree at most
@@ -74,6 +75,17 @@ def bipartite_matching_size(n_left, n, u, v):
     B = sp.csr_matrix((np.ones(u.size), (u, v - n_left)), shape=(n_left, n - n_left))
     match = maximum_bipartite_matching(B, perm_type="column")
     return int((match >= 0).sum())
+
+
+def vertex_cover_lp_double_cover(n, u, v):
+    """Fractional vertex cover optimum of a general graph as half the maximum
+    matching of its bipartite double cover G x K2 (vertices w and w'; edges
+    (u, v') and (v, u') for every edge (u, v)): the LP is half-integral, and
+    this equality is a classical result (Nemhauser and Trotter)."""
+    u, v = _np(u).astype(np.int64), _np(v).astype(np.int64)
+    uu = np.concatenate([u, v])
+    vv = np.concatenate([v, u]) + n
+    return bipartite_matching_size(n, 2 * n, uu, vv) / 2.0
 
 
 def b_matching_size(n_left, n, u, v, b, edge_cap=None):

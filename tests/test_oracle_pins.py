@@ -743,3 +743,20 @@ def test_densest_peel_lower_bound_brackets_the_optimum():
         assert lb <= opt * (1 + 1e-12) and lb >= opt / (2 * 1.1) - 1e-12
     n, u, v = _complete(7)                       # K_7: density 3, peeling keeps it whole
     assert exact.densest_peel_lower_bound(n, np.asarray(u), np.asarray(v)) == pytest.approx(3.0)
+
+
+def test_vertex_cover_lp_by_bipartite_double_cover():
+    """Fractional vertex cover of non-bipartite graphs: the LP solver, the
+    matching of the bipartite double cover, closed forms (odd cycle n/2,
+    K_n n/2) and the oracle's MWU solve agree."""
+    for n, u, v, closed in [(*_cycle(9), 4.5), (*_complete(6), 3.0)]:
+        u, v = np.asarray(u), np.asarray(v)
+        A = lp.incidence(n, u, v).T.tocsr()
+        assert exact.lp_covering_opt(A, np.ones(n)) == pytest.approx(closed)
+        assert exact.vertex_cover_lp_double_cover(n, u, v) == pytest.approx(closed)
+    g = gg.rmat(7, seed=11)
+    A = lp.incidence(g.n, g.u, g.v).T.tocsr()
+    opt = exact.vertex_cover_lp_double_cover(g.n, g.u.numpy(), g.v.numpy())
+    assert exact.lp_covering_opt(A, np.ones(g.n)) == pytest.approx(opt)
+    r = mwu.solve_covering(A, np.ones(g.n), EPS, step="newton")
+    _covering_within(r.objective, opt)
