@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--h-scatter", action="store_true",
                     help="vertex cover, dominating set: h by a scatter over C's rows with atomic adds "
                          "(not bit-reproducible)")
+    ap.add_argument("--dv-scatter", action="store_true",
+                    help="dominating set: dz = C d by a scatter over the columns of the moving variables "
+                         "(not bit-reproducible)")
     ap.add_argument("--no-tiles", action="store_true",
                     help="row-binned gather SpMV everywhere (no staged tiles for banded CSR sides)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
@@ -486,7 +489,8 @@ def run_other(args):
         kind, P, C, obj = lpspec.from_workload(wl)
         ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=step, drop_covered=int(args.drop),
                            timing=0 if args.eager else 1, use_graph=0 if args.eager else 1,
-                           spmv_tiles=-1 if args.no_tiles else 0, h_scatter=int(args.h_scatter))
+                           spmv_tiles=-1 if args.no_tiles else 0, h_scatter=int(args.h_scatter),
+                           dv_scatter=int(args.dv_scatter))
         E = wl.graph.m
         lp_names = {"domset-rmat20": "dominating set, (I + A) x >= 1 explicit CSR",
                     "vcover-rmat24": "vertex cover, M^T x >= 1 implicit",
@@ -499,6 +503,7 @@ def run_other(args):
         cfg = {"workload": args.workload, "lp": lp_names[args.workload],
                "vertices": wl.graph.n, "edges": E, "eps": wl.eps,
                "h": "row scatter (atomic adds)" if args.h_scatter else "gather",
+               "dz": "column scatter of the moving variables" if args.dv_scatter else "SpMV",
                "spmv": "staged tiles (P %d, C %d)" % M.mwu_spmv_tiles(ctx) if any(M.mwu_spmv_tiles(ctx))
                else "row-binned gathers"}
 

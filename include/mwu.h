@@ -158,6 +158,13 @@ typedef struct {
                                   the sums' order, and so the last bits of h and the
                                   iterates, vary from run to run.  0 (default): the
                                   deterministic gather                                     */
+    int32_t dv_scatter;        /* covering side given as an explicit CSR (dominating set,
+                                  generalized matching): 1 computes dz = C d by a scatter
+                                  over the columns of the variables with d_i > 0 (atomic
+                                  adds, then the row scaling) instead of the row-wise
+                                  SpMV: late in a probe few variables move, and only
+                                  their columns are read.  Not bit-reproducible; 0
+                                  (default): the SpMV                                       */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */

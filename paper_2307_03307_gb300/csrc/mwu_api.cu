@@ -127,6 +127,7 @@ int mwu_default_options(mwu_options *o) {
     o->drop_covered = 0;
     o->spmv_tiles = 0;     // automatic
     o->h_scatter = 0;
+    o->dv_scatter = 0;
     o->timing = 0;
     o->stop_rule = 0;
     o->grad_tol = -1.0;   // precision default
@@ -385,6 +386,7 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.med_var = med_var;
     p.n_med_var = n_med_var;
     p.hacc = nullptr;
+    p.dv_scatter = (c->opt.dv_scatter && sb[1].rv.kind == RK_CSR && sb[1].cv.kind == CK_CSR) ? 2 : 0;
     if (c->opt.h_scatter && (sb[1].rv.kind == RK_FIXED2 || sb[1].rv.kind == RK_CSR) && sb[1].cv.kind == CK_CSR) {
         p.hacc = c->ar.alloc<T>(c->n);
         if (!p.hacc) return fail(c, MWU_ERR_OOM, "allocating the scatter sums");
@@ -679,6 +681,20 @@ int mwu_set_x(mwu_ctx *c, const void *x, int32_t x_is_fp64) {
     return MWU_OK;
 }
 
+// a6: dv = A d for both sides.  The covering side's dz is already written by
+// the edge-pair direction kernel (densest), or comes by scatter over the
+// columns of the moving variables (option dv_scatter); the rest by the SpMV.
+template <class Prob>
+static cudaError_t spmv_direction(const Prob &p, int keep_gh, cudaStream_t s) {
+    bool skip_c = dir_fuses_dz(p, keep_gh);
+    if (!skip_c && (p.dv_scatter & 2)) {
+        cudaError_t e = launch_spmv_scatter(p, 1, s);
+        if (e != cudaSuccess) return e;
+        skip_c = true;
+    }
+    return launch_spmv(p, s, skip_c ? 1 : 0);
+}
+
 // ------------------------------------------------------------ iterations
 // kernels of one iteration; ev (6 events or nullptr) brackets the kernel classes.  The
 // events are recorded as external event nodes when the sequence is captured.
@@ -774,7 +790,7 @@ static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev, bool loop = fa
         if (ev && (e = cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_dir(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = launch_spmv(p, c->stream, dir_fuses_dz(p, 0))) != cudaSuccess) return e;
+        if ((e = spmv_direction(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = enqueue_search(c, p, loop)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[3], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
@@ -866,7 +882,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[0], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 0, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[1], c->stream));
-            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_spmv(p, c->stream, dir_fuses_dz(p, 0)); }));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return spmv_direction(p, 0, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[2], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 0, c->stream); }));
             c->launches += 3;
@@ -940,7 +956,7 @@ int mwu_direction(mwu_ctx *c, int64_t *n_positive) {
     if (rc != MWU_OK) return rc;
     if (c->st_host->status != ST_RUNNING) return fail(c, MWU_ERR_STATE, "probe not running (set a target or x first)");
     TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 1, c->stream); }));
-    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_spmv(p, c->stream); }));
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return spmv_direction(p, 1, c->stream); }));
     TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_cand(p, 1, c->stream); }));
     if ((rc = pull_state(c)) != MWU_OK) return rc;
     if (n_positive) *n_positive = c->st_host->n_pos;

@@ -158,6 +158,7 @@ struct Problem {
     int64_t n;          // variables
     T *x, *d, *g, *h;   // g, h may be nullptr (not kept)
     T *hacc;            // per-variable sums of k_h_scatter (option h_scatter), else nullptr
+    int32_t dv_scatter; // bit s: side s computes dv = A d by scatter (option dv_scatter)
     DevState *st;
     double *part_var;   // per-block records of variable-side kernels
     double *part_row;   // per-block records of row-side kernels
@@ -198,6 +199,8 @@ template <class T> bool dir_fuses_dz(const Problem<T> &p, int keep_gh) {
            p.side[1].rv.kind == RK_PAIRSUM;
 }
 template <class T> cudaError_t launch_cand(const Problem<T> &p, int external, cudaStream_t s);
+// a6 for a CSR side by scatter over the columns of the variables with d > 0 (option dv_scatter)
+template <class T> cudaError_t launch_spmv_scatter(const Problem<T> &p, int side, cudaStream_t s);
 // one-candidate Newton pass (captured iterations): returns at once unless the search is in its Newton phase
 template <class T> cudaError_t launch_cand_newton(const Problem<T> &p, cudaStream_t s);    // a7: one candidate pass
 template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s);                // a8

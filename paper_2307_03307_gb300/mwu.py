@@ -43,7 +43,8 @@ class mwu_options(C.Structure):
                 ("check_every", C.c_int32), ("group", C.c_int32), ("timing", C.c_int32),
                 ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p),
                 ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("batch_workers", C.c_int32),
-                ("drop_covered", C.c_int32), ("spmv_tiles", C.c_int32), ("h_scatter", C.c_int32)]
+                ("drop_covered", C.c_int32), ("spmv_tiles", C.c_int32), ("h_scatter", C.c_int32),
+                ("dv_scatter", C.c_int32)]
 
 
 class mwu_iter_stats(C.Structure):

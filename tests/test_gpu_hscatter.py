@@ -1,6 +1,8 @@
-"""The scatter form of h (option h_scatter: h = C^T w_c by one pass over C's
-rows with atomic adds; vertex cover's edge rows, the explicit CSR rows of
-dominating set and of generalized matching's lower bounds) against the oracle: one
+"""The scatter forms against the oracle: h = C^T w_c by one pass over C's rows
+with atomic adds (option h_scatter; vertex cover's edge rows, the explicit CSR
+rows of dominating set and of generalized matching's lower bounds), and
+dz = C d by a scatter over the columns of the moving variables (option
+dv_scatter; explicit CSR covering sides).  One
 iteration's quantities from the oracle chain, and whole solves against the
 exact LP and the oracle's solve.  The sums' order varies, so the bounds are
 those of the gather form (propagated FP32 error), not bit equality."""
@@ -15,11 +17,15 @@ from tests.test_gpu_parity import (M, wls, make_ctx, probe_target, vec, run_dire
 pytestmark = pytest.mark.gpu
 
 
+SCATTER = {"h": dict(h_scatter=1), "dv": dict(dv_scatter=1), "h+dv": dict(h_scatter=1, dv_scatter=1)}
+
+
 @pytest.mark.parametrize("prec", ["f32", "fp64"])
-@pytest.mark.parametrize("kind", ["vcover", "domset", "gmatch"])
-def test_h_scatter_iteration_matches_oracle(M, wls, kind, prec):
+@pytest.mark.parametrize("kind,opts", [("vcover", "h"), ("domset", "h"), ("gmatch", "h"),
+                                       ("domset", "dv"), ("gmatch", "dv"), ("domset", "h+dv")])
+def test_h_scatter_iteration_matches_oracle(M, wls, kind, opts, prec):
     wl = wls[kind]
-    ctx = make_ctx(M, wl, prec, h_scatter=1)
+    ctx = make_ctx(M, wl, prec, **SCATTER[opts])
     try:
         T = probe_target(wl)
         M.mwu_set_target(ctx, T)
@@ -36,10 +42,10 @@ def test_h_scatter_iteration_matches_oracle(M, wls, kind, prec):
 
 @pytest.mark.parametrize("step", ["kary", "newton"])
 @pytest.mark.parametrize("prec", ["f32", "fp64"])
-@pytest.mark.parametrize("kind", ["vcover", "domset"])
-def test_h_scatter_solve_matches_oracle_and_exact(M, wls, kind, prec, step):
+@pytest.mark.parametrize("kind,opts", [("vcover", "h"), ("domset", "h"), ("domset", "h+dv")])
+def test_h_scatter_solve_matches_oracle_and_exact(M, wls, kind, opts, prec, step):
     wl = wls[kind]
-    ctx = make_ctx(M, wl, prec, h_scatter=1, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY)
+    ctx = make_ctx(M, wl, prec, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY, **SCATTER[opts])
     try:
         res = M.mwu_solve(ctx)
         x = vec(M, ctx, M.VEC_X, H.n_vars(wl))
