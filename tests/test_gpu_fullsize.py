@@ -253,3 +253,43 @@ def test_fullsize_densest_rmat18_solve_bracket(M):
     lb = exact.densest_peel_lower_bound(n, u, v, delta=0.1)
     assert lb <= d_cert * (1 + 1e-9), (lb, d_cert)
     assert d_cert <= (1 + wl.eps) ** 2 * 2 * 1.1 * lb, (lb, d_cert)
+
+
+def test_fullsize_domset_rmat20_duality_bracket(M):
+    """C3 whole solve at full size through weak LP duality: the weighted
+    dominating-set LP (min c^T x, (I + A) x >= 1) and its dual packing LP
+    (max 1^T y, (I + A) y <= c, as diag(1/c)(I + A) y <= 1) are solved on the
+    GPU; their certified values, recomputed here in FP64 from the returned x
+    and y, bracket the common optimum, at most (1 + eps)^4 apart."""
+    import scipy.sparse as sp
+    from paper_2307_03307_gb300 import lpspec
+    wl = W.domset(20, seed=3, device="cuda")
+    g = wl.graph
+    n = g.n
+    kind, P, C, obj = lpspec.from_workload(wl)
+    ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps)
+    try:
+        res = M.mwu_solve(ctx)
+        x = vec(M, ctx, M.VEC_X, n)
+    finally:
+        M.mwu_destroy(ctx)
+    rowptr, col = wl.csr
+    c = wl.objective
+    Pd = M.csr_matrix(rowptr.int().contiguous(), col.int().contiguous(), None, n, n, row_bound=c.float().contiguous())
+    ctx = M.mwu_create(M.PACKING, Pd, None, None, eps=wl.eps)
+    try:
+        resp = M.mwu_solve(ctx)
+        y = vec(M, ctx, M.VEC_X, n)
+    finally:
+        M.mwu_destroy(ctx)
+    rp = rowptr.cpu().numpy().astype(np.int64)
+    ci = col.cpu().numpy().astype(np.int64)
+    A = sp.csr_matrix((np.ones(ci.size), ci, rp), shape=(n, n))
+    cw = c.cpu().numpy().astype(np.float64)
+    assert (x >= 0).all() and (y >= 0).all()
+    cert_c = float(cw @ x) / float((A @ x).min())
+    cert_p = float(y.sum()) / float(((A @ y) / cw).max())
+    assert cert_c == pytest.approx(res["objective"], rel=1e-4)
+    assert cert_p == pytest.approx(resp["objective"], rel=1e-4)
+    assert cert_p <= cert_c * (1 + 1e-9), (cert_p, cert_c)          # weak duality
+    assert cert_c <= (1 + wl.eps) ** 4 * cert_p, (cert_p, cert_c)
