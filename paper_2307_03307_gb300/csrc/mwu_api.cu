@@ -102,7 +102,6 @@ static int choose_G(double avg, int forced) {
     return std::max(1, std::min(32, g));
 }
 
-static int heavy_len_for(int G) { return std::max(256, 32 * G); }
 
 int mwu_default_options(mwu_options *o) {
     if (!o) return MWU_ERR_INVALID;
@@ -324,7 +323,6 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
             }
         }
     }
-    if (sb.cv.kind == CK_CSR) sb.cv.heavy_len = heavy_len_for(sb.cv.G);
     return MWU_OK;
 }
 
@@ -382,7 +380,6 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.G_var = G_var;
     p.heavy_var = heavy_var;
     p.n_heavy_var = n_heavy_var;
-    p.heavy_var_len = 0;
     p.med_var = med_var;
     p.n_med_var = n_med_var;
     p.hacc = nullptr;
@@ -698,7 +695,11 @@ static cudaError_t spmv_direction(const Prob &p, int keep_gh, cudaStream_t s) {
 // ------------------------------------------------------------ iterations
 // kernels of one iteration; ev (6 events or nullptr) brackets the kernel classes.  The
 // events are recorded as external event nodes when the sequence is captured.
-static int kernels_per_iteration(const mwu_ctx *c) { return 3 + c->opt.max_passes; }
+// kernels an eager iteration launches: direction, SpMV, update and max_passes
+// turns of the search (two kernels per turn with Newton's method)
+static int kernels_per_iteration(const mwu_ctx *c) {
+    return 3 + (c->opt.step == MWU_STEP_NEWTON ? 2 : 1) * c->opt.max_passes;
+}
 constexpr int EV_PER_IT = 5;
 
 // The step-size search of one iteration.  Captured (graph): a conditional WHILE

@@ -178,7 +178,6 @@ struct Problem {
     // sides): light ones (<= the views' heavy_len) take G_var lanes in the
     // main loop, medium ones (<= HEAVY_LEN) a warp each, heavy ones a block each
     int32_t G_var;
-    int32_t heavy_var_len;
     int32_t n_heavy_var;
     const int32_t *heavy_var;
     int32_t n_med_var;
