@@ -53,6 +53,8 @@ def test_default_options_host_only(lib):
     assert o.eta_factor == pytest.approx(10.0) and o.double_single == 1
     o2 = mwu.mwu_default_options(eps=0.05, K=4)
     assert o2.eps == pytest.approx(0.05) and o2.K == 4
+    # the reproducible defaults: every row kept, automatic tiles, gathers (no atomic sums)
+    assert (o.drop_covered, o.spmv_tiles, o.h_scatter, o.dv_scatter) == (0, 0, 0, 0)
 
 
 def test_struct_sizes_match_header(lib):
