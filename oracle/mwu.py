@@ -17,10 +17,17 @@ sparse products are scipy's.  Functions follow the paper's notation:
 * BinSearch step size .................................. Alg. 3, Sec. 4.2
 * K-candidate search (this library's generalisation of Alg. 3, defined here
   so that both sides compute the same alpha) ........... Sec. 4.2 + Prop. 4.2
+* Newton's method on f(alpha) = 1, Psi', Phi', the
+  (1 - eps)^p backoff and the covering step ............ Sec. 4.2 (+ Alg. 3's early exit)
+* dropping of satisfied covering rows (option) ......... Alg. 1 / Alg. 2, last step of the loop
 * objective embedding and the search over M or D ...... Sec. 2.2 (pure packing / covering), Sec. 3 (dense-sub)
+* the smoothed potential and its gradients ............. Sec. 4.1
 
 Readings of places where the paper is silent or inconsistent are marked
-"Reading:" in the docstrings.
+"Reading:" in the docstrings.  Every function above is pinned by
+``tests/test_oracle_pins.py`` to closed forms, exact optima, brute force or
+invariants; only the iterate trajectory as a whole is not (the GPU and the
+oracle iterate independently, and tests compare single steps and results).
 """
 from __future__ import annotations
 
