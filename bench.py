@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--rules", default="",
                     help="--step-table: comma-separated subset of the step rules (default: all)")
     ap.add_argument("--step-table", action="store_true",
-                    help="the step-rule comparison of Table 2 on rgg-18 (one probe per LP and rule) instead of a bench line")
+                    help="the step-rule comparison of Table 2 on rgg-18 (a whole solve per LP and rule) instead of a bench line")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying captured iterations (for "
                          "profilers that cannot see the kernel nodes of graphs with conditional nodes)")
