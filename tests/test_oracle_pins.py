@@ -523,6 +523,47 @@ def test_potential_gradients_central_fd():
 
 
 # ----------------------------------------------------------------------------
+# set-up of a probe (Alg. 1 / Alg. 2 before the loop, Sec. 2.2): eta, x0, c_d
+# ----------------------------------------------------------------------------
+
+# 3 x 4 packing matrix with an empty last column.  Column maxima by hand:
+# (1, 4, 2, -) -> x0 = eps / (n * colmax) with n = 4 and the empty column's
+# norm read as 1; its row maxima (2, 1, 4) differ from every column maximum.
+_P34 = np.array([[0.5, 0.0, 2.0, 0.0],
+                 [1.0, 0.25, 0.0, 0.0],
+                 [0.0, 4.0, 1.0, 0.0]])
+# 4 x 4 with row maxima (3, 5, 0.5, 2) and column maxima (2, 5, 3, 0.5):
+# same shape either way, so a row/column slip shows in the values
+_P44 = np.array([[2.0, 0.0, 3.0, 0.0],
+                 [0.0, 5.0, 0.0, 0.0],
+                 [0.0, 0.0, 0.0, 0.5],
+                 [1.0, 2.0, 0.0, 0.0]])
+
+
+def check_setup_hand_values(o=mwu):
+    # eta = 10 ln(m) / eps (Alg. 1) with m = m_P + m_C: m = 4 -> 100 ln 4
+    assert o.eta_of(4, 0.1) == pytest.approx(138.62943611198906, rel=1e-14)
+    # m = 3 + 1 + 1000 rows, eps = 0.25 -> 40 ln(1004) = 40 (3 ln 10 + ln 1.004)
+    #   = 40 (6.907755278982137 + 0.003992021269537453)
+    assert o.eta_of(1004, 0.25) == pytest.approx(276.46989201006697, rel=1e-14)
+    assert o.eta_of(4, 0.1, eta_factor=1.0) == pytest.approx(13.862943611198906, rel=1e-14)
+    # x0_i = eps / (n ||P_{:,i}||_inf)
+    x = o.x_init(sp.csr_matrix(_P34), 0.1)
+    np.testing.assert_allclose(x, [0.025, 0.00625, 0.0125, 0.025], rtol=1e-15)
+    x = o.x_init(sp.csr_matrix(_P44), 0.2)
+    np.testing.assert_allclose(x, [0.025, 0.01, 0.2 / 12, 0.1], rtol=1e-15)
+    # c_d = 1/(2 eta) (Alg. 2); 1/eta when one side is the single objective row (Sec. 2.2)
+    assert o.step_coefficient(3, 5, 100.0) == pytest.approx(0.005, rel=1e-15)
+    assert o.step_coefficient(3, 1, 100.0) == pytest.approx(0.01, rel=1e-15)
+    assert o.step_coefficient(1, 7, 100.0) == pytest.approx(0.01, rel=1e-15)
+    assert o.step_coefficient(3, 1, 100.0, double_single=False) == pytest.approx(0.005, rel=1e-15)
+
+
+def test_setup_hand_values():
+    check_setup_hand_values()
+
+
+# ----------------------------------------------------------------------------
 # planted mistakes: each pin above must catch a plausible slip in the oracle
 # ----------------------------------------------------------------------------
 
@@ -569,6 +610,29 @@ def _dphi_unweighted(z, dz, alpha, eta):
     return float(np.mean(dz))
 
 
+def _eta_log10(m, eps, eta_factor=10.0):
+    return eta_factor * math.log10(m) / eps
+
+
+def _x_init_rowmax(P, eps):
+    P = sp.csr_matrix(P)
+    rowmax = np.asarray(abs(P).max(axis=1).todense()).ravel()
+    rowmax[rowmax == 0] = 1.0
+    return eps / (P.shape[1] * rowmax)
+
+
+def _x_init_rows_as_n(P, eps):
+    return mwu.x_init(P, eps) * P.shape[1] / P.shape[0]
+
+
+def _step_coefficient_never_doubled(m_P, m_C, eta, double_single=True):
+    return 1.0 / (2.0 * eta)
+
+
+def _step_coefficient_halved(m_P, m_C, eta, double_single=True):
+    return 0.5 * mwu.step_coefficient(m_P, m_C, eta, double_single)
+
+
 @pytest.mark.parametrize("mutant,check", [
     (_Mutant(smin=_smin_wrong_sign), check_smax_closed_forms),
     (_Mutant(smax=_smax_no_eta), check_smax_closed_forms),
@@ -578,6 +642,11 @@ def _dphi_unweighted(z, dz, alpha, eta):
     (_Mutant(Psi=_psi_dropped_shift), check_phi_psi),
     (_Mutant(newton_update=_newton_wrong_sign), check_newton),
     (_Mutant(dPhi=_dphi_unweighted), check_newton),
+    (_Mutant(eta_of=_eta_log10), check_setup_hand_values),
+    (_Mutant(x_init=_x_init_rowmax), check_setup_hand_values),
+    (_Mutant(x_init=_x_init_rows_as_n), check_setup_hand_values),
+    (_Mutant(step_coefficient=_step_coefficient_never_doubled), check_setup_hand_values),
+    (_Mutant(step_coefficient=_step_coefficient_halved), check_setup_hand_values),
 ])
 def test_planted_mistake_is_caught(mutant, check):
     with pytest.raises(AssertionError):
