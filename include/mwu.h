@@ -165,6 +165,17 @@ typedef struct {
                                   SpMV: late in a probe few variables move, and only
                                   their columns are read.  Not bit-reproducible; 0
                                   (default): the SpMV                                       */
+    int32_t col_split;         /* covering side of edge rows (MWU_MAT_INCIDENCE_T, vertex
+                                  cover) without row bounds, edges sorted by first
+                                  endpoint, h_scatter off: 0 (default) keeps z_e = x_u +
+                                  x_v exactly (the update rebuilds z from the updated x)
+                                  and computes h_i, the sum over the edges at i of
+                                  e^{-eta (z_e - s_c)}, from two contiguous streams -- z
+                                  over the edges whose first endpoint is i, and x_i + x_u
+                                  over a list of the first endpoints u of the edges whose
+                                  second endpoint is i -- with no atomics (deterministic);
+                                  -1 keeps z incremental (z += alpha dz, Alg. 2) and
+                                  gathers z over every vertex's incident edge ids           */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
@@ -253,6 +264,29 @@ int mwu_set_target(mwu_ctx *ctx, double target);
  * recompute y = Px, z = Cx and their reductions.  Keeps eta and the target. */
 int mwu_set_x(mwu_ctx *ctx, const void *x, int32_t x_is_fp64);
 
+/* Stage hooks that load the constraint vectors themselves, so that each kernel
+ * of an iteration can be checked on inputs identical to a reference's rather
+ * than on values that earlier kernels produced.
+ *
+ * mwu_set_state loads y (m_P entries), z (m_C entries), dy, dz (host or device
+ * arrays, float32 or float64 per is_fp64; NULL leaves that vector as it is;
+ * a side that is the single objective row takes one entry).  Values are
+ * rounded once to the form's precision.  When y or z is given, the probe is
+ * reset to RUNNING (eta, the target and x are kept) and the log-sum-exp
+ * reductions of Sec. 2.2 (shifts s_p = max y, s_c = min z and the shifted sums
+ * S_p, S_c, read with mwu_get_scalars) are recomputed by the reduction kernel,
+ * followed by Alg. 2's stopping test; mwu_direction then computes g, h, d from
+ * these y, z and the current x.  When dy or dz is given, mwu_eval_candidates,
+ * mwu_eval_newton and mwu_search use them as the last direction's products
+ * (Sec. 4.1 / 4.2).  Returns MWU_ERR_NUMERIC when a reduction is not finite.
+ *
+ * mwu_set_direction loads d (n entries, same conventions) and computes
+ * dy = Pd, dz = Cd with the forward products of the iteration (a6 of Alg. 2:
+ * the row-binned or staged SpMV, or the column scatter with dv_scatter); read
+ * them with mwu_get_vector.  Requires a running probe (MWU_ERR_STATE). */
+int mwu_set_state(mwu_ctx *ctx, const void *y, const void *z, const void *dy, const void *dz, int32_t is_fp64);
+int mwu_set_direction(mwu_ctx *ctx, const void *d, int32_t is_fp64);
+
 /* Run up to n_iters iterations of Alg. 2 (gradients, direction, d = 0 test,
  * dy = Pd, dz = Cd, step-size search, update, stopping test).  Returns the
  * probe status: FEASIBLE, INFEASIBLE, MAX_ITER or RUNNING; or an error.
@@ -325,11 +359,14 @@ int mwu_potential(mwu_ctx *ctx, const float *x, double *pot,
                   float *grad_x, float *grad_obj, float *grad_vals);
 
 /* ------------------------------------------- allocation-free evaluation */
-/* For callers that cannot allocate device memory -- code running where
- * cudaMalloc is unavailable or forbidden (inside a graph-capture region, a
- * custom allocator's own hooks, embedded runtimes with a fixed memory budget)
- * -- this entry point evaluates step-size candidates of one constraint side
- * without allocating anything and without a context.  The paper has no
+/* For callers that must not allocate device memory: code that runs inside a
+ * custom device allocator's own hooks (an allocation from there would re-enter
+ * the allocator), processes whose device memory a framework's caching
+ * allocator has already reserved up to a fixed budget, and latency-critical
+ * runtimes that forbid cudaMalloc after start-up because it synchronises the
+ * device.  This entry point evaluates step-size candidates of one constraint
+ * side without a context and without allocating anything: it calls no
+ * cudaMalloc, cudaFree or allocating library routine.  The paper has no
  * counterpart to it; it computes the same values as mwu_eval_candidates.
  *
  *   v, dv   : device float32 arrays of m rows (y and dy of a packing side,
@@ -340,18 +377,23 @@ int mwu_potential(mwu_ctx *ctx, const float *x, double *pot,
  *   alphas  : host array of K (1..8) candidate step sizes
  *   val     : host output, K doubles: Psi(alpha_k) = smax(v + a dv) - smax(v)
  *             for sign +1, Phi(alpha_k) = smin(v + a dv) - smin(v) for -1
- *   vmin    : host output or NULL, K doubles: min(v + alpha_k dv)
+ *   vmin    : host output or NULL, K doubles: min(v + alpha_k dv) for
+ *             sign = -1 (the covering side's minimum, Alg. 3's early-exit
+ *             test); +inf for sign = +1
  *   stream  : cudaStream_t or NULL (legacy default stream); the call waits
- *             for its results
- * Scratch lives in one static device array of MWU_STATIC_MAX_BLOCKS per-block
- * records (256 KiB) that every GPU loading the library keeps until exit; m is
- * limited to MWU_STATIC_MAX_ROWS (blocks x rows per block) and larger m returns
- * MWU_ERR_INVALID.  The first call on each device looks the array up and
- * clears its completion ticket (cudaGetSymbolAddress, cudaMemset); make that
- * first call before any stream capture.  All calls share the array, so calls
- * that overlap on the GPU (several streams or threads at once) race and must
- * be serialised by the caller.  Errors: MWU_ERR_INVALID (bad argument, size
- * beyond the maximum), MWU_ERR_CUDA; mwu_last_error(NULL) describes them. */
+ *             for its results (cudaStreamSynchronize on that stream)
+ * Scratch lives in one file-scope static device array of
+ * MWU_STATIC_MAX_BLOCKS per-block records (256 KiB) that every GPU loading the
+ * library keeps until the process exits; m is limited to MWU_STATIC_MAX_ROWS
+ * (blocks x rows per block) and larger m returns MWU_ERR_INVALID.  The first
+ * call on each device does a one-time set-up with that device current: it
+ * looks up the array's device address (cudaGetSymbolAddress) and clears its
+ * completion ticket; make that first call before any stream capture.  Every
+ * call shares the array and leaves the last call's records in it (the ticket
+ * returns to zero at the end of each call), so calls that overlap on the GPU
+ * (several streams or host threads at once) race and must be serialised by
+ * the caller.  Errors: MWU_ERR_INVALID (bad argument, size beyond the
+ * maximum), MWU_ERR_CUDA; mwu_last_error(NULL) describes them. */
 #define MWU_STATIC_MAX_BLOCKS 1024
 #define MWU_STATIC_ROWS_PER_BLOCK 16384
 #define MWU_STATIC_MAX_ROWS ((int64_t)MWU_STATIC_MAX_BLOCKS * MWU_STATIC_ROWS_PER_BLOCK)

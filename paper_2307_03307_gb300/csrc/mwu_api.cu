@@ -127,6 +127,7 @@ int mwu_default_options(mwu_options *o) {
     o->spmv_tiles = 0;     // automatic
     o->h_scatter = 0;
     o->dv_scatter = 0;
+    o->col_split = 0;
     o->timing = 0;
     o->stop_rule = 0;
     o->grad_tol = -1.0;   // precision default
@@ -249,6 +250,18 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
             sb.cv = ColView{CK_CSR, choose_G(avg, forced_G), vptr, eids, nullptr, rdiv, nullptr, 0, 0, nullptr};
             sb.m = E;
             sb.nvar = nv;
+            if (sign < 0 && !rdiv && c->opt.col_split >= 0 && !c->opt.h_scatter) {
+                int32_t *cptr = nullptr, *vp2 = nullptr, *u2 = nullptr;
+                int sorted = 0;
+                TRY_CUDA(c, build_split_view(c->ar, edges, E, nv, &cptr, &vp2, &u2, &sorted, s));
+                if (sorted) {
+                    sb.cv.kind = CK_SPLIT2;
+                    sb.cv.ptr = cptr;
+                    sb.cv.idx = nullptr;
+                    sb.cv.ptr2 = vp2;
+                    sb.cv.idx2 = u2;
+                }
+            }
         } else if (A->kind == MWU_MAT_PAIR) {
             if ((rc = load_bounds(nv)) != MWU_OK) return rc;
             sb.rv = RowView{RK_CSR, choose_G(avg, forced_G), nv, 2 * E, vptr, slots, nullptr, rdiv};
@@ -335,6 +348,40 @@ static void dense_side(SideBuild &sb, const float *c, int32_t sign) {
     sb.nvar = -1;
 }
 
+// Segments of SEG_LEN entries over the combined columns of the heavy
+// variables of a CK_SPLIT2 side (host-built tables, uploaded once).
+static int split_segments(mwu_ctx *c, ColView &cv, const int32_t *hv, int32_t nhv) {
+    cudaStream_t s = c->stream;
+    std::vector<int32_t> h_hv(nhv), h_ptr((size_t)c->n + 1);
+    TRY_CUDA(c, cudaMemcpyAsync(h_hv.data(), hv, sizeof(int32_t) * nhv, cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(c, cudaMemcpyAsync(h_ptr.data(), cv.ptr, sizeof(int32_t) * ((size_t)c->n + 1), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(c, cudaStreamSynchronize(s));
+    std::vector<int32_t> first(nhv + 1), var, beg;
+    for (int32_t h = 0; h < nhv; ++h) {
+        first[h] = (int32_t)var.size();
+        const int32_t i = h_hv[h];
+        for (int32_t k = h_ptr[i]; k < h_ptr[i + 1]; k += SEG_LEN) {
+            var.push_back(i);
+            beg.push_back(k);
+        }
+    }
+    first[nhv] = (int32_t)var.size();
+    const int32_t ns = (int32_t)var.size();
+    int32_t *d_first = c->ar.alloc<int32_t>(nhv + 1), *d_var = c->ar.alloc<int32_t>(ns), *d_beg = c->ar.alloc<int32_t>(ns);
+    if (!d_first || !d_var || !d_beg) return fail(c, MWU_ERR_OOM, "allocating column segment tables");
+    TRY_CUDA(c, cudaMemcpyAsync(d_first, first.data(), sizeof(int32_t) * (nhv + 1), cudaMemcpyHostToDevice, s));
+    if (ns > 0) {
+        TRY_CUDA(c, cudaMemcpyAsync(d_var, var.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s));
+        TRY_CUDA(c, cudaMemcpyAsync(d_beg, beg.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s));
+    }
+    TRY_CUDA(c, cudaStreamSynchronize(s));
+    cv.n_cseg = ns;
+    cv.cseg_first = d_first;
+    cv.cseg_var = d_var;
+    cv.cseg_beg = d_beg;
+    return MWU_OK;
+}
+
 template <class T>
 static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32_t *heavy_var, int32_t n_heavy_var,
                          int32_t *med_var, int32_t n_med_var, int G_var, int var_bps, int row_bps, int upd_bps) {
@@ -383,6 +430,17 @@ static int alloc_problem(mwu_ctx *c, Problem<T> &p, const SideBuild sb[2], int32
     p.med_var = med_var;
     p.n_med_var = n_med_var;
     p.hacc = nullptr;
+    p.cseg_part = nullptr;
+    if (p.side[1].cv.kind == CK_SPLIT2 && p.side[1].cv.n_cseg > 0) {
+        p.cseg_part = c->ar.alloc<T>(p.side[1].cv.n_cseg);
+        if (!p.cseg_part) return fail(c, MWU_ERR_OOM, "allocating column segment partials");
+    }
+    p.x_eager = 0;
+    for (int s = 0; s < 2; ++s)
+        if (p.side[s].cv.kind == CK_SPLIT2) {
+            p.side[s].cv.xsrc = p.x;
+            p.x_eager = 1;
+        }
     p.dv_scatter = (c->opt.dv_scatter && sb[1].rv.kind == RK_CSR && sb[1].cv.kind == CK_CSR) ? 2 : 0;
     if (c->opt.h_scatter && (sb[1].rv.kind == RK_FIXED2 || sb[1].rv.kind == RK_CSR) && sb[1].cv.kind == CK_CSR) {
         p.hacc = c->ar.alloc<T>(c->n);
@@ -510,8 +568,11 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     // each), heavy beyond (a block each)
     int G_var = 1;
     int32_t *hv = nullptr, nhv = 0, *mv = nullptr, nmv = 0;
-    const int32_t *cp0 = sb[0].cv.kind == CK_CSR ? sb[0].cv.ptr : nullptr;
-    const int32_t *cp1 = sb[1].cv.kind == CK_CSR ? sb[1].cv.ptr : nullptr;
+    auto col_lengths = [&](const SideBuild &b) -> const int32_t * {
+        return (b.cv.kind == CK_CSR || b.cv.kind == CK_SPLIT2) ? b.cv.ptr : nullptr;
+    };
+    const int32_t *cp0 = col_lengths(sb[0]);
+    const int32_t *cp1 = col_lengths(sb[1]);
     if (cp0 || cp1) {
         int lq = 1;
         cudaError_t e = length_quantile2(c->ar, cp0, cp1, c->n, 0.75, &lq, c->stream);
@@ -519,10 +580,12 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         G_var = c->opt.group > 0 ? c->opt.group : std::max(1, std::min(32, pow2_ceil((lq + 3) / 4)));
         const int light = std::min(16 * G_var, HEAVY_LEN);
         for (int s = 0; s < 2; ++s)
-            if (sb[s].cv.kind == CK_CSR) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = light; }
+            if (sb[s].cv.kind == CK_CSR || sb[s].cv.kind == CK_SPLIT2) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = light; }
         e = heavy_list2(c->ar, cp0, HEAVY_LEN, cp1, HEAVY_LEN, c->n, &hv, &nhv, c->stream);
         if (e == cudaSuccess) e = range_list2(c->ar, cp0, cp1, c->n, light, HEAVY_LEN, &mv, &nmv, c->stream);
         if (e != cudaSuccess) { fail_cuda(c, e, "variable length classes"); return bail(MWU_ERR_CUDA); }
+        if (sb[1].cv.kind == CK_SPLIT2 && nhv > 0 && (rc = split_segments(c, sb[1].cv, hv, nhv)) != MWU_OK)
+            return bail(rc);
     }
     // device state
     c->st_dev = c->ar.alloc<DevState>(1);
@@ -692,13 +755,109 @@ static cudaError_t spmv_direction(const Prob &p, int keep_gh, cudaStream_t s) {
     return launch_spmv(p, s, skip_c ? 1 : 0);
 }
 
+// Copy n entries of src (host or device memory, float32 or float64 per
+// src_fp64) into the context's vector dst of type T, converting on the device.
+template <class T>
+static int load_vec(mwu_ctx *c, T *dst, const void *src, int64_t n, int32_t src_fp64) {
+    cudaPointerAttributes at{};
+    const void *from = src;
+    void *tmp = nullptr;
+    const size_t nb = (size_t)n * (src_fp64 ? 8 : 4);
+    if (cudaPointerGetAttributes(&at, src) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        TRY_CUDA(c, cudaMalloc(&tmp, nb));
+        cudaError_t e = cudaMemcpyAsync(tmp, src, nb, cudaMemcpyDefault, c->stream);
+        if (e != cudaSuccess) { cudaFree(tmp); return fail_cuda(c, e, "copy vector in"); }
+        from = tmp;
+    }
+    cudaError_t e = src_fp64 ? launch_convert_in<T>((const double *)from, dst, n, c->stream)
+                             : launch_convert_in<T>((const float *)from, dst, n, c->stream);
+    if (tmp) { cudaStreamSynchronize(c->stream); cudaFree(tmp); }
+    if (e != cudaSuccess) return fail_cuda(c, e, "convert vector in");
+    return MWU_OK;
+}
+
+// One entry of src (host or device) as a double: the value of a side that is
+// the single objective row.
+static int load_scalar(mwu_ctx *c, const void *src, int32_t src_fp64, double *out) {
+    if (src_fp64) {
+        TRY_CUDA(c, cudaMemcpy(out, src, 8, cudaMemcpyDefault));
+    } else {
+        float f = 0.0f;
+        TRY_CUDA(c, cudaMemcpy(&f, src, 4, cudaMemcpyDefault));
+        *out = (double)f;
+    }
+    return std::isfinite(*out) ? MWU_OK : fail(c, MWU_ERR_INVALID, "non-finite value loaded");
+}
+
+int mwu_set_state(mwu_ctx *c, const void *y, const void *z, const void *dy, const void *dz, int32_t is_fp64) {
+    if (!c) return MWU_ERR_INVALID;
+    if (!y && !z && !dy && !dz) return MWU_OK;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    DevState &h = *c->st_host;
+    const void *vals[2] = {y, z}, *dirs[2] = {dy, dz};
+    const bool rows = y || z;
+    if (rows) reset_probe_fields(h);
+    auto side_of = [&](auto &p, int s) -> auto & { return p.side[s]; };
+    for (int s = 0; s < 2; ++s) {
+        const bool dense = c->fp64 ? side_of(c->pd, s).rv.kind == RK_DENSE1 : side_of(c->pf, s).rv.kind == RK_DENSE1;
+        const int64_t m = c->fp64 ? side_of(c->pd, s).m : side_of(c->pf, s).m;
+        for (int w = 0; w < 2; ++w) {
+            const void *src = w == 0 ? vals[s] : dirs[s];
+            if (!src) continue;
+            if (dense) {
+                double v = 0.0;
+                if ((rc = load_scalar(c, src, is_fp64, &v)) != MWU_OK) return rc;
+                (w == 0 ? h.dense_v : h.dense_dv)[s] = v;
+                continue;
+            }
+            if (c->fp64) {
+                auto &sd = side_of(c->pd, s);
+                rc = load_vec<double>(c, w == 0 ? sd.v : sd.dv, src, m, is_fp64);
+            } else {
+                auto &sd = side_of(c->pf, s);
+                rc = load_vec<float>(c, w == 0 ? sd.v : sd.dv, src, m, is_fp64);
+            }
+            if (rc != MWU_OK) return rc;
+        }
+    }
+    if ((rc = push_state(c)) != MWU_OK) return rc;
+    if (rows) {
+        TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_rows_reduce(p, c->stream); }));
+        c->launches += 1;
+    }
+    if (dy || dz) c->have_direction = true;
+    else if (rows) c->have_direction = false;
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    return probe_status(h) == MWU_ERR_NUMERIC ? fail(c, MWU_ERR_NUMERIC, "NaN/Inf in the reductions of y, z")
+                                              : MWU_OK;
+}
+
+int mwu_set_direction(mwu_ctx *c, const void *d, int32_t is_fp64) {
+    if (!c || !d) return MWU_ERR_INVALID;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    if (c->st_host->status != ST_RUNNING) return fail(c, MWU_ERR_STATE, "probe not running (set a target or x first)");
+    if (c->fp64) rc = load_vec<double>(c, c->pd.d, d, c->n, is_fp64);
+    else rc = load_vec<float>(c, c->pf.d, d, c->n, is_fp64);
+    if (rc != MWU_OK) return rc;
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dense_dir(p, c->stream); }));
+    TRY_CUDA(c, with_prob(c, [&](auto &p) { return spmv_direction(p, 1, c->stream); }));
+    if ((rc = pull_state(c)) != MWU_OK) return rc;
+    c->have_direction = true;
+    return MWU_OK;
+}
+
+
 // ------------------------------------------------------------ iterations
 // kernels of one iteration; ev (6 events or nullptr) brackets the kernel classes.  The
 // events are recorded as external event nodes when the sequence is captured.
 // kernels an eager iteration launches: direction, SpMV, update and max_passes
 // turns of the search (two kernels per turn with Newton's method)
 static int kernels_per_iteration(const mwu_ctx *c) {
-    return 3 + (c->opt.step == MWU_STEP_NEWTON ? 2 : 1) * c->opt.max_passes;
+    const int extra = (c->fp64 ? c->pd.x_eager : c->pf.x_eager) + (c->fp64 ? c->pd.hacc != nullptr : c->pf.hacc != nullptr);
+    return 3 + extra + (c->opt.step == MWU_STEP_NEWTON ? 2 : 1) * c->opt.max_passes;
 }
 constexpr int EV_PER_IT = 5;
 
@@ -900,7 +1059,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[3], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_update(p, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[4], c->stream));
-            c->launches += 1;
+            c->launches += 1 + c->pd.x_eager;
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             if (c->opt.timing && (rc = accumulate_timing(c, ev, c->st_host->iter - iter0)) != MWU_OK) return rc;
             done += 1;
@@ -911,7 +1070,8 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             // direction, SpMV and update per captured iteration, plus the kernels
             // the search loops ran (counted on the device)
-            c->launches += (int64_t)n * (3 + (c->fp64 ? c->pd.hacc != nullptr : c->pf.hacc != nullptr)) +
+            c->launches += (int64_t)n * (3 + (c->fp64 ? c->pd.hacc != nullptr : c->pf.hacc != nullptr) +
+                                         (c->fp64 ? c->pd.x_eager : c->pf.x_eager)) +
                            (c->st_host->loop_launches - loop0);
             if (c->opt.timing &&
                 (rc = accumulate_timing(c, chunk ? c->ev : c->ev_one, c->st_host->iter - iter0)) != MWU_OK)

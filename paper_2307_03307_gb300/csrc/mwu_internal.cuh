@@ -37,7 +37,13 @@ enum ColKind : int32_t {
     CK_FIXED2 = 2,   // variable i = edge (u,v): rows u and v (incidence M)
     CK_FIXED1 = 3,   // variable i = slot: row idx[i] (pair matrix O)
     CK_HALF1 = 4,    // variable i = slot: row i/2 (interweaved W)
-    CK_DENSE1 = 5    // single objective row: coefficient c[i]
+    CK_DENSE1 = 5,   // single objective row: coefficient c[i]
+    CK_SPLIT2 = 6    // incidence transpose with edges sorted by first endpoint: variable i
+                     // = vertex; its edges with first endpoint i are the contiguous rows
+                     // [ptr[i] - ptr2[i], ptr[i+1] - ptr2[i+1]) (weights from the stored
+                     // z), those with second endpoint i are listed through their first
+                     // endpoints idx2[ptr2[i] .. ptr2[i+1]) (weights from x_i + x_u, equal
+                     // to the stored z_e since that side keeps z = x_u + x_v exactly)
 };
 
 struct RowView {
@@ -86,6 +92,19 @@ struct ColView {
     int32_t n_heavy;
     int32_t heavy_len;
     const int32_t *heavy;
+    // CK_SPLIT2: ptr holds the combined column lengths (first-endpoint range
+    // plus second-endpoint list), ptr2/idx2 the second-endpoint lists, xsrc
+    // the variables x (type T of the problem)
+    const int32_t *ptr2 = nullptr;
+    const int32_t *idx2 = nullptr;
+    const void *xsrc = nullptr;
+    // CK_SPLIT2 columns of the problem's heavy variables (heavy_var, longer than
+    // HEAVY_LEN on either side) cut into SEG_LEN-entry segments of the combined
+    // column: heavy variable h owns segments [cseg_first[h], cseg_first[h+1]),
+    // segment q covers combined entries [cseg_beg[q], min(cseg_beg[q] + SEG_LEN,
+    // ptr[cseg_var[q] + 1])); k_split_seg writes one partial sum per segment
+    int32_t n_cseg = 0;
+    const int32_t *cseg_first = nullptr, *cseg_var = nullptr, *cseg_beg = nullptr;
 };
 
 template <class T>
@@ -158,7 +177,10 @@ struct Problem {
     int64_t n;          // variables
     T *x, *d, *g, *h;   // g, h may be nullptr (not kept)
     T *hacc;            // per-variable sums of k_h_scatter (option h_scatter), else nullptr
+    T *cseg_part;       // per-segment partial sums of the heavy CK_SPLIT2 columns (k_split_seg)
     int32_t dv_scatter; // bit s: side s computes dv = A d by scatter (option dv_scatter)
+    int32_t x_eager;    // x += alpha d runs before the update (which then rebuilds the edge
+                        // rows of a CK_SPLIT2 side as z_e = x_u + x_v), not in the next k_dir
     DevState *st;
     double *part_var;   // per-block records of variable-side kernels
     double *part_row;   // per-block records of row-side kernels
@@ -189,6 +211,10 @@ struct Problem {
 template <class T> cudaError_t launch_x_init(const Problem<T> &p, cudaStream_t s);                // a0: x0 + dense dots
 template <class T> cudaError_t launch_x_set(const Problem<T> &p, const void *x, int fp64, cudaStream_t s);
 template <class T> cudaError_t launch_rows_eval(const Problem<T> &p, cudaStream_t s);             // a1-a3 at a new x
+// a2, a3 of the stored y, z (loaded by the stage hook), dense rows as the state holds them
+template <class T> cudaError_t launch_rows_reduce(const Problem<T> &p, cudaStream_t s);
+// single objective row applied to d (dense_dv), for a direction loaded by the stage hook
+template <class T> cudaError_t launch_dense_dir(const Problem<T> &p, cudaStream_t s);
 template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cudaStream_t s);      // a4-a5 (+ fused x update)
 // a6: dy = Pd, dz = Cd; skip_c: dz was already written by the direction kernel
 template <class T> cudaError_t launch_spmv(const Problem<T> &p, cudaStream_t s, int skip_c = 0);
@@ -208,6 +234,8 @@ template <class T> cudaError_t launch_search_begin(const Problem<T> &p, cudaStre
 template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const float *x, float *gx, float *gobj,
                                                       float *gvals_p, float *gvals_c, cudaStream_t s);
 template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t n, int fp64, cudaStream_t s);
+// dst[i] = (T) src[i] (device arrays)
+template <class T, class U> cudaError_t launch_convert_in(const U *src, T *dst, int64_t n, cudaStream_t s);
 
 // Message for mwu_last_error(NULL) from entry points without a context.
 void set_global_error(const char *msg);

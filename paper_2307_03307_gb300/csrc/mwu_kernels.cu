@@ -243,7 +243,46 @@ template <class T> struct WeightFn {
         if (rdiv) w /= (T)rdiv[j];
         return w;
     }
+    // the weight of a row whose value vj is recomputed rather than loaded (no row bound)
+    __device__ __forceinline__ T of_value(T vj) const {
+        if (!(vj < hi)) return T(0);
+        return t_exp(eta_sgn * (vj - s));
+    }
 };
+
+// Column of vertex i in the split view of an incidence transpose (CK_SPLIT2,
+// built only for a covering side, whose scale is 1, without row bounds):
+// the weights of the edges whose first endpoint is i, rows [b1, e1) of the
+// stored z (a contiguous stream), plus those of the edges whose second
+// endpoint is i, from z_e = x_i + x_u with their first endpoints u listed in
+// idx2[q0, q1) (one gather of x each; the side keeps z = x_u + x_v exactly, and
+// floating-point addition commutes, so both give the weight of the same z_e).
+// Strided over `step` lanes starting at `lane`, four loads in flight.
+template <class T, class F>
+__device__ __forceinline__ T split_gather(const ColView &cv, int64_t i, int b1, int e1, int q0, int q1, int lane,
+                                          int step, const F &w) {
+    // z and the endpoint lists are streamed once (evict-first loads), so that
+    // x, gathered at random, stays in L2
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    const T *z = w.v;
+    int k = b1 + lane;
+    for (; k + 3 * step < e1; k += 4 * step) {
+        const T z0 = __ldcs(z + k), z1 = __ldcs(z + k + step), z2 = __ldcs(z + k + 2 * step), z3 = __ldcs(z + k + 3 * step);
+        a0 += w.of_value(z0); a1 += w.of_value(z1); a2 += w.of_value(z2); a3 += w.of_value(z3);
+    }
+    for (; k < e1; k += step) a0 += w.of_value(__ldcs(z + k));
+    const T *xx = static_cast<const T *>(cv.xsrc);
+    const T xi = xx[i];
+    k = q0 + lane;
+    for (; k + 3 * step < q1; k += 4 * step) {
+        const int u0 = __ldcs(cv.idx2 + k), u1 = __ldcs(cv.idx2 + k + step), u2 = __ldcs(cv.idx2 + k + 2 * step),
+                  u3 = __ldcs(cv.idx2 + k + 3 * step);
+        const T x0 = __ldg(xx + u0), x1 = __ldg(xx + u1), x2 = __ldg(xx + u2), x3 = __ldg(xx + u3);
+        a0 += w.of_value(xi + x0); a1 += w.of_value(xi + x1); a2 += w.of_value(xi + x2); a3 += w.of_value(xi + x3);
+    }
+    for (; k < q1; k += step) a0 += w.of_value(xi + __ldg(xx + __ldcs(cv.idx2 + k)));
+    return (a0 + a1) + (a2 + a3);
+}
 
 // Column-view gather for variable i: sum_j A_ji w_j (without the side's scale).
 // Simple kinds are computed by lane 0 of the group only.  Unless ALL, a CSR
@@ -272,6 +311,13 @@ __device__ __forceinline__ T col_gather(const ColView &cv, int64_t i, int lane, 
             a0 += t;
         }
         acc = (a0 + a1) + (a2 + a3);
+        break;
+    }
+    case CK_SPLIT2: {
+        const int c0 = cv.ptr[i], c1 = cv.ptr[i + 1];
+        if (!ALL && c1 - c0 > cv.heavy_len) return T(0);
+        const int q0 = cv.ptr2[i], q1 = cv.ptr2[i + 1];
+        acc = split_gather<T>(cv, i, c0 - q0, c1 - q1, q0, q1, lane, G, w);
         break;
     }
     case CK_FIXED2:
@@ -625,6 +671,34 @@ __device__ void dir_finish(DevState *st, double np_t, double dd0, double dd1) {
 }
 
 
+// Heavy columns of a CK_SPLIT2 covering side: one warp per SEG_LEN-entry
+// segment of the combined column (first-endpoint rows of z, then the x list of
+// the second-endpoint edges), one partial sum each; k_dir adds a heavy
+// variable's partials in segment order.  Balances the hub vertices of
+// power-law graphs over the whole grid.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_split_seg(Problem<T> p, int potential_mode) {
+    DevState *st = p.st;
+    if (!potential_mode && st->status != ST_RUNNING) return;
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const Side<T> &C = p.side[1];
+    const ColView &cv = C.cv;
+    WeightFn<T> wc{C.v, nullptr, -K0.eta, K0.s1, potential_mode ? t_inf<T>() : K0.hi};
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < cv.n_cseg; q += nw) {
+        const int i = cv.cseg_var[q];
+        const int c0 = cv.ptr[i], c1 = cv.ptr[i + 1], q0 = cv.ptr2[i], q1 = cv.ptr2[i + 1];
+        const int cz = c0 + ((c1 - q1) - (c0 - q0));   // combined index where the x list starts
+        const int kb = cv.cseg_beg[q], ke = min(kb + SEG_LEN, c1);
+        const int zb = (c0 - q0) + (min(max(kb, c0), cz) - c0), ze = (c0 - q0) + (min(ke, cz) - c0);
+        const int xb = q0 + (max(kb, cz) - cz), xe = q0 + (max(ke, cz) - cz);
+        T sum = split_gather<T>(cv, i, zb, max(zb, ze), xb, max(xb, xe), lane, 32, wc);
+        sum = group_sum(sum, 32);
+        if (lane == 0) p.cseg_part[q] = sum;
+    }
+}
+
 // a4, a5 with the deferred x update of the previous iteration fused in.
 template <class T>
 __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int potential_mode, float *grad_obj) {
@@ -677,6 +751,13 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
         else { sg = col_gather<T>(P.cv, i, threadIdx.x, 1 << 30, wp, T(1)); sg = block_sum(threadIdx.x == 0 ? sg : T(0), sm); }
         if (hacc) { sh = hacc[i]; }
         else if (C.cv.kind == CK_CSR) sh = heavy_col_gather<T>(C.cv, i, wc, sm);
+        else if (C.cv.kind == CK_SPLIT2) {
+            // the segments' partial sums (k_split_seg), added in a fixed order
+            T a = T(0);
+            for (int q = C.cv.cseg_first[hh] + (int)threadIdx.x; q < C.cv.cseg_first[hh + 1]; q += (int)blockDim.x)
+                a += p.cseg_part[q];
+            sh = block_sum(a, sm);
+        }
         else { sh = col_gather<T>(C.cv, i, threadIdx.x, 1 << 30, wc, T(1)); sh = block_sum(threadIdx.x == 0 ? sh : T(0), sm); }
         if (threadIdx.x == 0) {
             if (hacc) hacc[i] = T(0);
@@ -708,8 +789,8 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
         T sg = T(0), sh = T(0);
         bool heavy = false;
         if (live) {
-            heavy = (P.cv.kind == CK_CSR && P.cv.ptr[i + 1] - P.cv.ptr[i] > P.cv.heavy_len) ||
-                    (C.cv.kind == CK_CSR && C.cv.ptr[i + 1] - C.cv.ptr[i] > C.cv.heavy_len);
+            heavy = ((P.cv.kind == CK_CSR || P.cv.kind == CK_SPLIT2) && P.cv.ptr[i + 1] - P.cv.ptr[i] > P.cv.heavy_len) ||
+                    ((C.cv.kind == CK_CSR || C.cv.kind == CK_SPLIT2) && C.cv.ptr[i + 1] - C.cv.ptr[i] > C.cv.heavy_len);
             if (!heavy) {
                 sg = col_gather<T>(P.cv, i, lane, G, wp, T(1));
                 sh = hacc ? (lane == 0 ? hacc[i] : T(0)) : col_gather<T>(C.cv, i, lane, G, wc, T(1));
@@ -1563,9 +1644,11 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_tiled(Problem<T> p, const T *__r
 }
 
 // Log-sum-exp reductions of y and z at a new x (a2, a3): a stream over both
-// sides, then the dense rows from k_x_prep's records and the stopping test.
+// sides, then the dense rows from k_x_prep's records (dense_keep = 0) or as
+// the state holds them (dense_keep = 1: y and z loaded by the stage hook), and
+// the stopping test.
 template <class T>
-__global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb_var) {
+__global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb_var, int dense_keep) {
     DevState *st = p.st;
     const int s = (blockIdx.x < gP) ? 0 : 1;
     const int bid = s == 0 ? blockIdx.x : blockIdx.x - gP;
@@ -1585,7 +1668,7 @@ __global__ void __launch_bounds__(BLOCK) k_rows_lse(Problem<T> p, int gP, int nb
     }
     lse_block_record(p, acc, eta_sgn, sd.sign, vmin);
     if (last_block_done(&st->counter[0])) {
-        finalize_reductions(p, gP, gridDim.x, nb_var, true, 0.0);
+        finalize_reductions(p, gP, gridDim.x, nb_var, !dense_keep, 0.0);
         if (threadIdx.x == 0) st->counter[0] = 0;
     }
 }
@@ -1916,7 +1999,44 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
     const T hi = sd.sign > 0 ? t_inf<T>() : K0.hi;   // dropped covering rows leave the sums
     T vmin = t_inf<T>();
     Lse<T> acc{T(0), T(0)};
-    if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
+    if (sd.cv.kind == CK_SPLIT2) {
+        // edge rows kept exact: z_e = x_u + x_v from the x that k_xstep has just
+        // updated (the same sum the direction kernel forms for the second endpoint)
+        const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x, nthr = (int64_t)nbs * blockDim.x;
+        const int2 *ed = reinterpret_cast<const int2 *>(sd.rv.idx);
+        const T scale = s == 0 ? K0.scale0 : K0.scale1;
+        for (int64_t j0 = 4 * tid; j0 < sd.m; j0 += 4 * nthr) {
+            const int nr = (int)min((int64_t)4, sd.m - j0);
+            T vv[4];
+            if (nr == 4) {
+                const int4 e01 = __ldcs(reinterpret_cast<const int4 *>(ed + j0));
+                const int4 e23 = __ldcs(reinterpret_cast<const int4 *>(ed + j0 + 2));
+                vv[0] = (p.x[e01.x] + p.x[e01.y]) * scale;
+                vv[1] = (p.x[e01.z] + p.x[e01.w]) * scale;
+                vv[2] = (p.x[e23.x] + p.x[e23.y]) * scale;
+                vv[3] = (p.x[e23.z] + p.x[e23.w]) * scale;
+                if (sizeof(T) == 4) {
+                    __stcs(reinterpret_cast<float4 *>(sd.v + j0),
+                           make_float4((float)vv[0], (float)vv[1], (float)vv[2], (float)vv[3]));
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) sd.v[j0 + r] = vv[r];
+                }
+            } else {
+                for (int r = 0; r < nr; ++r) {
+                    const int2 e = ed[j0 + r];
+                    vv[r] = (p.x[e.x] + p.x[e.y]) * scale;
+                    sd.v[j0 + r] = vv[r];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r >= nr) break;
+                vmin = fmin(vmin, vv[r]);
+                if (vv[r] < hi) lse_push(acc, vv[r], eta_sgn, sd.sign);
+            }
+        }
+    } else if (sd.rv.kind != RK_DENSE1 && sd.rv.kind != RK_NONE) {
         const int64_t tid = (int64_t)bid * blockDim.x + threadIdx.x, nthr = (int64_t)nbs * blockDim.x;
         for (int64_t j0 = 4 * tid; j0 < sd.m; j0 += 4 * nthr) {
             const int nr = (int)min((int64_t)4, sd.m - j0);
@@ -1949,7 +2069,7 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
     if (last_block_done(&st->counter[3])) {
         if (threadIdx.x == 0) {
             st->iter += 1;
-            st->pending = 1;
+            st->pending = p.x_eager ? 0 : 1;   // k_xstep has already applied x += alpha d
             st->alpha_prev = alpha;
         }
         __syncthreads();
@@ -1969,6 +2089,17 @@ __global__ void __launch_bounds__(BLOCK) k_flush(Problem<T> p) {
     if (last_block_done(&st->counter[4])) {
         if (threadIdx.x == 0) { st->pending = 0; st->counter[4] = 0; }
     }
+}
+
+// x += alpha d before the update of a problem whose update rebuilds edge rows
+// from x (p.x_eager); runs exactly when k_update does.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_xstep(Problem<T> p) {
+    const DevState *st = p.st;
+    if (st->status != ST_RUNNING || st->phase != PH_DONE || !(st->alpha_acc >= 1.0)) return;
+    const T a = (T)st->alpha_acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x)
+        p.x[i] += a * p.d[i];
 }
 
 // d pot / d val for the explicit CSR values of one side: sign * coef_j * w_j * x_i
@@ -1991,6 +2122,39 @@ template <class T, class U>
 __global__ void k_convert(const T *src, U *dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (U)src[i];
+}
+
+// Single objective row of a side applied to a loaded direction (the stage
+// hook mwu_set_direction): dense_dv[s] = scale_s c^T d, the value the direction
+// kernel otherwise accumulates with d.  Per-block FP64 sums, the last block
+// adds them in block order.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_dense_dot(Problem<T> p, const T *vec) {
+    __shared__ double sm_d[32];
+    DevState *st = p.st;
+    double dot[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int s = 0; s < 2; ++s)
+            if (p.side[s].cv.kind == CK_DENSE1)
+                dot[s] += (p.side[s].cv.cvec ? (double)p.side[s].cv.cvec[i] : 1.0) * (double)vec[i];
+    const double t0 = block_sum(dot[0], sm_d);
+    const double t1 = block_sum(dot[1], sm_d);
+    if (threadIdx.x == 0) {
+        p.part_var[(size_t)blockIdx.x * REC + 0] = t0;
+        p.part_var[(size_t)blockIdx.x * REC + 1] = t1;
+    }
+    if (last_block_done(&st->counter[6])) {
+        double a0 = 0.0, a1 = 0.0;
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < (int)gridDim.x; ++b) {
+                a0 += p.part_var[(size_t)b * REC + 0];
+                a1 += p.part_var[(size_t)b * REC + 1];
+            }
+            if (p.side[0].rv.kind == RK_DENSE1) st->dense_dv[0] = st->scale[0] * a0;
+            if (p.side[1].rv.kind == RK_DENSE1) st->dense_dv[1] = st->scale[1] * a1;
+            st->counter[6] = 0;
+        }
+    }
 }
 
 // ============================================================ launchers
@@ -2072,7 +2236,20 @@ template <class T> static cudaError_t rows_at_x(const Problem<T> &p, int nb_var,
     if (e != cudaSuccess) return e;
     int gP, gC;
     split_rows(p, &gP, &gC, false);
-    k_rows_lse<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, nb_var);
+    k_rows_lse<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, nb_var, 0);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_rows_reduce(const Problem<T> &p, cudaStream_t s) {
+    int gP, gC;
+    split_rows(p, &gP, &gC, false);
+    k_rows_lse<T><<<gP + gC, BLOCK, 0, s>>>(p, gP, 0, 1);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_dense_dir(const Problem<T> &p, cudaStream_t s) {
+    if (p.side[0].rv.kind != RK_DENSE1 && p.side[1].rv.kind != RK_DENSE1) return cudaSuccess;
+    k_dense_dot<T><<<grid_for(p.n, p.grid_var), BLOCK, 0, s>>>(p, p.d);
     return cudaGetLastError();
 }
 
@@ -2108,6 +2285,13 @@ template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cuda
                                                 : p.side[1].m;
         const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((items + BLOCK - 1) / BLOCK, p.grid_upd));
         k_h_scatter<T><<<gs, BLOCK, 0, s>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (p.side[1].cv.kind == CK_SPLIT2 && p.side[1].cv.n_cseg > 0) {
+        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)p.side[1].cv.n_cseg * 32 + BLOCK - 1) / BLOCK,
+                                                                    p.grid_var));
+        k_split_seg<T><<<gs, BLOCK, 0, s>>>(p, 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -2153,6 +2337,11 @@ template <class T> cudaError_t launch_update(const Problem<T> &p, cudaStream_t s
         gC = std::min(gC, need(mC));
     }
     if (gP + gC == 0) gP = 1;
+    if (p.x_eager) {
+        k_xstep<T><<<grid_for(p.n, p.grid_var), BLOCK, 0, s>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_update<T><<<gP + gC, BLOCK, 0, s>>>(p, gP);
     return cudaGetLastError();
 }
@@ -2167,6 +2356,13 @@ template <class T> cudaError_t launch_search_begin(const Problem<T> &, cudaStrea
 template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const float *x, float *gx, float *gobj,
                                                       float *gvals_p, float *gvals_c, cudaStream_t s) {
     (void)x;
+    if (p.side[1].cv.kind == CK_SPLIT2 && p.side[1].cv.n_cseg > 0) {
+        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)p.side[1].cv.n_cseg * 32 + BLOCK - 1) / BLOCK,
+                                                                    p.grid_var));
+        k_split_seg<T><<<gs, BLOCK, 0, s>>>(p, 1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     int64_t per_block = BLOCK / p.G_var;
     int64_t need = std::max<int64_t>((p.n + per_block - 1) / per_block, p.n_heavy_var);
     int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, p.grid_var));
@@ -2194,6 +2390,15 @@ template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t 
     else k_convert<T, float><<<g, BLOCK, 0, s>>>(src, (float *)dst, n);
     return cudaGetLastError();
 }
+
+template <class T, class U> cudaError_t launch_convert_in(const U *src, T *dst, int64_t n, cudaStream_t s) {
+    k_convert<U, T><<<grid_for(n, 4096), BLOCK, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert_in<float, float>(const float *, float *, int64_t, cudaStream_t);
+template cudaError_t launch_convert_in<float, double>(const double *, float *, int64_t, cudaStream_t);
+template cudaError_t launch_convert_in<double, float>(const float *, double *, int64_t, cudaStream_t);
+template cudaError_t launch_convert_in<double, double>(const double *, double *, int64_t, cudaStream_t);
 
 template <class T> int sweep_blocks_per_sm(int *var_bps, int *row_bps, int *upd_bps) {
     int a = 0, b = 0, c = 0;
@@ -2232,6 +2437,8 @@ template <class T> int tiled_blocks_per_sm() {
     template cudaError_t launch_x_init<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_x_set<T>(const Problem<T> &, const void *, int, cudaStream_t);                 \
     template cudaError_t launch_rows_eval<T>(const Problem<T> &, cudaStream_t);                                \
+    template cudaError_t launch_rows_reduce<T>(const Problem<T> &, cudaStream_t);                              \
+    template cudaError_t launch_dense_dir<T>(const Problem<T> &, cudaStream_t);                                \
     template cudaError_t launch_dir<T>(const Problem<T> &, int, cudaStream_t);                                 \
     template cudaError_t launch_spmv<T>(const Problem<T> &, cudaStream_t, int);                                \
     template cudaError_t launch_cand<T>(const Problem<T> &, int, cudaStream_t);                                \
@@ -2313,14 +2520,15 @@ __global__ void __launch_bounds__(BLOCK) k_cand_static(Scratch *scr, const float
         for (int b = 0; b < (int)gridDim.x; ++b)
             cand_merge1<float, double>(mx, R, Tt, zm, scr->rec[b][k][0], scr->rec[b][k][1], scr->rec[b][k][2],
                                        scr->rec[b][k][3], sign);
-        const double lS0 = (double)logf((float)S);
+        // the final combination (one thread per candidate) runs in FP64
+        const double lS0 = log(S);
         double val;
         if (sign > 0) {
-            double lq = mx + (double)logf((float)Tt) - lS0;
-            val = (lq < 0.0) ? (double)log1pf(expf((float)lq)) / eta : (mx + (double)logf((float)R) - lS0) / eta;
+            double lq = mx + log(Tt) - lS0;
+            val = (lq < 0.0) ? log1p(exp(lq)) / eta : (mx + log(R) - lS0) / eta;
         } else {
             double qv = Tt / S;
-            val = (qv <= 0.5) ? -(double)log1pf((float)(-qv)) / eta : -(mx + (double)logf((float)R) - lS0) / eta;
+            val = (qv <= 0.5) ? -log1p(-qv) / eta : -(mx + log(R) - lS0) / eta;
         }
         scr->out[k][0] = val;
         scr->out[k][1] = zm;

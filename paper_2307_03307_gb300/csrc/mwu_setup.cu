@@ -223,6 +223,68 @@ cudaError_t slots_to_edges(Arena &ar, const int32_t *slots, int64_t ns, int32_t 
     return cudaGetLastError();
 }
 
+// flag[0] = 1 when the edge list's first endpoints decrease anywhere
+__global__ void k_first_sorted(const int32_t *edges, int64_t m, int *flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e + 1 < m; e += (int64_t)gridDim.x * blockDim.x)
+        if (edges[2 * (e + 1)] < edges[2 * e]) atomicMax(flag, 1);
+}
+__global__ void k_count_endpoint(const int32_t *edges, int64_t m, int b, int32_t *cnt) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[edges[2 * e + b]], 1);
+}
+__global__ void k_endpoint(const int32_t *edges, int64_t m, int b, int32_t *out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = edges[2 * e + b];
+}
+__global__ void k_first_of(const int32_t *edges, const int32_t *perm, int64_t m, int32_t *out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = edges[2 * (int64_t)perm[k]];
+}
+__global__ void k_add_ptr(const int32_t *a, const int32_t *b, int64_t n, int32_t *out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = a[k] + b[k];
+}
+
+cudaError_t build_split_view(Arena &ar, const int32_t *edges, int64_t m, int32_t nv, int32_t **cptr_out,
+                             int32_t **vptr_out, int32_t **u2_out, int *sorted, cudaStream_t s) {
+    *sorted = 0;
+    int *flag = (int *)ar.scratch_keep(sizeof(int));
+    if (!flag) return cudaErrorMemoryAllocation;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return e;
+    k_first_sorted<<<g1d(m), 256, 0, s>>>(edges, m, flag);
+    int h = 0;
+    if ((e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (h != 0) return cudaSuccess;   // not sorted by first endpoint: the caller keeps the gather view
+    int32_t *cptr = ar.alloc<int32_t>(nv + 1);
+    int32_t *vptr = ar.alloc<int32_t>(nv + 1);
+    int32_t *u2 = ar.alloc<int32_t>(m);
+    int32_t *uptr = ar.alloc_tmp<int32_t>(nv + 1);
+    int32_t *cnt = ar.alloc_tmp<int32_t>(nv);
+    int32_t *keys = ar.alloc_tmp<int32_t>(m);
+    int32_t *kout = ar.alloc_tmp<int32_t>(m);
+    int32_t *iota = ar.alloc_tmp<int32_t>(m);
+    int32_t *perm = ar.alloc_tmp<int32_t>(m);
+    if (!cptr || !vptr || !u2 || !uptr || !cnt || !keys || !kout || !iota || !perm) return cudaErrorMemoryAllocation;
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)nv, s)) != cudaSuccess) return e;
+        k_count_endpoint<<<g1d(m), 256, 0, s>>>(edges, m, b, cnt);
+        if ((e = scan_counts(ar, cnt, b == 0 ? uptr : vptr, nv, s)) != cudaSuccess) return e;
+    }
+    k_add_ptr<<<g1d(nv + 1), 256, 0, s>>>(uptr, vptr, nv + 1, cptr);
+    k_endpoint<<<g1d(m), 256, 0, s>>>(edges, m, 1, keys);
+    k_iota<<<g1d(m), 256, 0, s>>>(iota, m);
+    if ((e = sort_pairs(ar, keys, kout, iota, perm, m, bits_for(nv), s)) != cudaSuccess) return e;
+    k_first_of<<<g1d(m), 256, 0, s>>>(edges, perm, m, u2);
+    ar.release_tmp();
+    *cptr_out = cptr;
+    *vptr_out = vptr;
+    *u2_out = u2;
+    *sorted = 1;
+    return cudaGetLastError();
+}
+
 cudaError_t csr_transpose(Arena &ar, const int32_t *ptr, const int32_t *idx, const float *val, int64_t rows,
                           int64_t cols, int64_t nnz, int32_t **tptr, int32_t **tidx, float **tval, cudaStream_t s) {
     int32_t *P = ar.alloc<int32_t>(cols + 1);
@@ -410,6 +472,9 @@ __global__ void k_colstats(ColView cv, int64_t n, const float *c, double *part) 
         }
         case CK_FIXED1: put(cv.rdiv ? 1.0 / (double)cv.rdiv[cv.idx[i]] : 1.0); break;
         case CK_HALF1: put(cv.rdiv ? 1.0 / (double)cv.rdiv[i >> 1] : 1.0); break;
+        case CK_SPLIT2:   // entries all 1 (no row bounds); empty for an isolated vertex
+            if (cv.ptr[i + 1] > cv.ptr[i]) put(1.0);
+            break;
         default: put(1.0);
         }
         double ci = c ? (double)c[i] : 1.0;
@@ -417,7 +482,7 @@ __global__ void k_colstats(ColView cv, int64_t n, const float *c, double *part) 
             s_min += ci / mn;   // sum_i c_i max_j 1/a_ji
             s_max += ci / mx;   // sum_i c_i / max_j a_ji
         }
-        if (cv.kind == CK_CSR) deg_max = fmax(deg_max, (double)(cv.ptr[i + 1] - cv.ptr[i]));
+        if (cv.kind == CK_CSR || cv.kind == CK_SPLIT2) deg_max = fmax(deg_max, (double)(cv.ptr[i + 1] - cv.ptr[i]));
     }
     sh[0][threadIdx.x] = s_min;
     sh[1][threadIdx.x] = s_max;

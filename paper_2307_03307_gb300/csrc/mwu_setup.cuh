@@ -71,6 +71,15 @@ cudaError_t validate_nonneg(const float *v, int64_t n, int code, int *d_err, cud
 
 cudaError_t build_vertex_slots(Arena &ar, const int32_t *edges, int64_t m, int32_t nv, int32_t **ptr_out,
                                int32_t **slots_out, cudaStream_t s);
+// Split column view of an incidence transpose M^T (rows = edges (u_e, v_e),
+// sorted by first endpoint u_e): per vertex i, the edges whose first endpoint
+// is i form the contiguous range [cptr[i] - vptr[i], cptr[i+1] - vptr[i+1]),
+// and the edges whose second endpoint is i are listed, by increasing edge id,
+// through their first endpoints u2[vptr[i] .. vptr[i+1]).  cptr = uptr + vptr
+// (the combined column lengths).  *sorted = 0 (nothing built) when the edge
+// list is not sorted by first endpoint.
+cudaError_t build_split_view(Arena &ar, const int32_t *edges, int64_t m, int32_t nv, int32_t **cptr,
+                             int32_t **vptr, int32_t **u2, int *sorted, cudaStream_t s);
 cudaError_t slots_to_edges(Arena &ar, const int32_t *slots, int64_t ns, int32_t **out, cudaStream_t s);
 cudaError_t csr_transpose(Arena &ar, const int32_t *ptr, const int32_t *idx, const float *val, int64_t rows,
                           int64_t cols, int64_t nnz, int32_t **tptr, int32_t **tidx, float **tval, cudaStream_t s);

@@ -44,7 +44,7 @@ class mwu_options(C.Structure):
                 ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p),
                 ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("batch_workers", C.c_int32),
                 ("drop_covered", C.c_int32), ("spmv_tiles", C.c_int32), ("h_scatter", C.c_int32),
-                ("dv_scatter", C.c_int32)]
+                ("dv_scatter", C.c_int32), ("col_split", C.c_int32)]
 
 
 class mwu_iter_stats(C.Structure):
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH):
         "mwu_last_error": (C.c_char_p, [V]),
         "mwu_set_target": (C.c_int, [V, D]),
         "mwu_set_x": (C.c_int, [V, V, I32]),
+        "mwu_set_state": (C.c_int, [V, V, V, V, V, I32]),
+        "mwu_set_direction": (C.c_int, [V, V, I32]),
         "mwu_iterate": (C.c_int, [V, I32, P(mwu_iter_stats)]),
         "mwu_direction": (C.c_int, [V, P(I64)]),
         "mwu_eval_candidates": (C.c_int, [V, P(D), I32, P(D), P(D), P(D)]),
@@ -129,7 +131,7 @@ def load(path: str = LIB_PATH):
 def exported_symbols():
     """Names of the C entry points this binding expects the library to export."""
     return ["mwu_default_options", "mwu_create", "mwu_destroy", "mwu_last_error", "mwu_set_target",
-            "mwu_set_x", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_eval_newton", "mwu_search",
+            "mwu_set_x", "mwu_set_state", "mwu_set_direction", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_eval_newton", "mwu_search",
             "mwu_solve",
             "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_spmv_tiles", "mwu_potential",
             "mwu_candidates_static", "mwu_create_batch", "mwu_solve_batch", "mwu_diag_one_minus_exp_neg"]
@@ -233,6 +235,24 @@ def mwu_set_target(ctx, target):
 def mwu_set_x(ctx, x):
     fp64 = 1 if str(getattr(x, "dtype", "")).endswith("float64") else 0
     return _check(ctx, load().mwu_set_x(ctx, _ptr(x), fp64))
+
+
+def _fp64_of(*arrays):
+    kinds = {str(getattr(a, "dtype", "")).endswith("float64") for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise ValueError("arrays of one call must share a dtype (float32 or float64)")
+    return 1 if kinds == {True} else 0
+
+
+def mwu_set_state(ctx, y=None, z=None, dy=None, dz=None):
+    """Load y, z, dy, dz (None keeps a vector); see mwu.h."""
+    fp64 = _fp64_of(y, z, dy, dz)
+    return _check(ctx, load().mwu_set_state(ctx, _ptr(y), _ptr(z), _ptr(dy), _ptr(dz), fp64))
+
+
+def mwu_set_direction(ctx, d):
+    """Load d and compute dy = Pd, dz = Cd on the device."""
+    return _check(ctx, load().mwu_set_direction(ctx, _ptr(d), _fp64_of(d)))
 
 
 def mwu_iterate(ctx, n_iters):

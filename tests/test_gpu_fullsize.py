@@ -225,36 +225,6 @@ def test_fullsize_vcover_rmat24_duality_bracket(M):
     assert cert_vc <= (1 + wl.eps) ** 4 * cert_m, (cert_m, cert_vc)
 
 
-def test_fullsize_densest_rmat18_solve_bracket(M):
-    """C2 whole solve at full size: the GPU's certified density D (an upper
-    bound on the max density: z / min(Wz) is dual feasible), recomputed here in
-    FP64 on the host from the returned z, lies above the density of a real
-    subgraph found by the oracle's peeling (a lower bound), and within
-    (1 + eps)^2 x 2 (1 + delta) of it (the two guarantees)."""
-    from oracle import exact
-    from paper_2307_03307_gb300 import lpspec
-    wl = W.densest(18, seed=2, device="cuda")
-    g = wl.graph
-    n, E = g.n, g.m
-    kind, P, C, obj = lpspec.from_workload(wl)
-    ctx = M.mwu_create(kind, P, C, obj, eps=wl.eps, step=M.STEP_NEWTON)
-    try:
-        res = M.mwu_solve(ctx)
-        z = vec(M, ctx, M.VEC_X, 2 * E)
-    finally:
-        M.mwu_destroy(ctx)
-    u = g.u.cpu().numpy()
-    v = g.v.cpu().numpy()
-    assert (z >= 0).all()
-    oz = np.bincount(u, weights=z[0::2], minlength=n) + np.bincount(v, weights=z[1::2], minlength=n)
-    wz = z[0::2] + z[1::2]
-    d_cert = float(oz.max()) / float(wz.min())
-    assert d_cert == pytest.approx(res["objective"], rel=1e-4)
-    lb = exact.densest_peel_lower_bound(n, u, v, delta=0.1)
-    assert lb <= d_cert * (1 + 1e-9), (lb, d_cert)
-    assert d_cert <= (1 + wl.eps) ** 2 * 2 * 1.1 * lb, (lb, d_cert)
-
-
 def test_fullsize_domset_rmat20_duality_bracket(M):
     """C3 whole solve at full size through weak LP duality: the weighted
     dominating-set LP (min c^T x, (I + A) x >= 1) and its dual packing LP

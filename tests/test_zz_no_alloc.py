@@ -1,11 +1,13 @@
 """The allocation-free entry point mwu_candidates_static (collected last).
 
-Callers that cannot allocate device memory (code inside graph capture,
-allocator hooks, fixed-budget runtimes) evaluate step candidates with it; its
+Callers that must not allocate device memory (a custom allocator's own hooks,
+processes whose memory a caching allocator holds to a fixed budget, runtimes
+that forbid cudaMalloc after start-up) evaluate step candidates with it; its
 scratch is a static device array.  Its values must equal those of the
-context-based mwu_eval_candidates on the same vectors, on two calls in a row
-(the array keeps the previous call's contents), and it must refuse sizes
-beyond its fixed capacity.
+context-based mwu_eval_candidates on the same vectors and the oracle's Psi and
+Phi on host-seeded vectors, on two calls in a row (the array keeps the
+previous call's contents), also over many blocks with a ragged last block
+followed by a smaller grid, and it must refuse sizes beyond its fixed capacity.
 """
 import numpy as np
 import pytest
@@ -54,6 +56,38 @@ def test_static_candidates_match_eval_candidates(M):
             H.assert_rel(mc, zmin, 1e-6, what="min(z + a dz)")
     finally:
         M.mwu_destroy(ctx)
+
+
+def test_static_candidates_many_blocks_against_oracle(M):
+    """Host-seeded v, dv over 43 blocks of 16384 rows (the last one ragged),
+    then over 2 blocks: the cross-block merge of the static records and the
+    ticket's reset between grids of different sizes.  Psi / Phi against the
+    oracle's definitions on the same float32 values in float64."""
+    from oracle import mwu as om
+    rng = np.random.default_rng(77)
+    eta = 1200.0
+    alphas = [1.0, 2.0, 5.0, 30.0, 250.0]
+    for m in (700_001, 20_000):
+        for sign in (+1, -1):
+            edge = 0.9 if sign > 0 else 0.2
+            v = rng.uniform(0.2, 0.9, m)
+            near = rng.random(m) < 0.5
+            v[near] = edge - sign * rng.uniform(0.0, 40.0 / eta, int(near.sum()))
+            v = v.astype(np.float32)
+            dv = rng.uniform(0.0, 3.0 / eta, m).astype(np.float32)
+            vo, dvo = v.astype(np.float64), dv.astype(np.float64)
+            shift, S = om.lse_shift_sum(vo, eta, sign)
+            fn = om.Psi if sign > 0 else om.Phi
+            want = [fn(vo, dvo, a, eta) for a in alphas]
+            wmin = [float(np.min(vo + a * dvo)) for a in alphas]
+            vt, dvt = torch.from_numpy(v).cuda(), torch.from_numpy(dv).cuda()
+            for _call in range(2):
+                got, gmin = M.mwu_candidates_static(vt, dvt, sign, eta, shift, S, alphas)
+                H.assert_rel(got, want, 1e-5, abs_=1e-8 / eta, what=f"m={m} sign={sign}")
+                if sign < 0:   # the minimum is that of the covering side (Alg. 3's early exit)
+                    H.assert_rel(gmin, wmin, 1e-6, what=f"min m={m} sign={sign}")
+                else:
+                    assert all(v == float("inf") for v in gmin)
 
 
 def test_static_candidates_reject_sizes_beyond_capacity(M):
