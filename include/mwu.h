@@ -173,9 +173,11 @@ typedef struct {
                                   e^{-eta (z_e - s_c)}, from two contiguous streams -- z
                                   over the edges whose first endpoint is i, and x_i + x_u
                                   over a list of the first endpoints u of the edges whose
-                                  second endpoint is i -- with no atomics (deterministic);
-                                  -1 keeps z incremental (z += alpha dz, Alg. 2) and
-                                  gathers z over every vertex's incident edge ids           */
+                                  second endpoint is i (one gather of x each) -- with no
+                                  atomics (deterministic); columns longer than 256
+                                  entries are summed in 256-entry segments.  -1 keeps z
+                                  incremental (z += alpha dz, Alg. 2) and gathers z over
+                                  every vertex's incident edge ids                      */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */

@@ -348,7 +348,7 @@ static void dense_side(SideBuild &sb, const float *c, int32_t sign) {
     sb.nvar = -1;
 }
 
-// Segments of SEG_LEN entries over the combined columns of the heavy
+// Segments of SPLIT_SEG entries over the combined columns of the heavy
 // variables of a CK_SPLIT2 side (host-built tables, uploaded once).
 static int split_segments(mwu_ctx *c, ColView &cv, const int32_t *hv, int32_t nhv) {
     cudaStream_t s = c->stream;
@@ -360,7 +360,7 @@ static int split_segments(mwu_ctx *c, ColView &cv, const int32_t *hv, int32_t nh
     for (int32_t h = 0; h < nhv; ++h) {
         first[h] = (int32_t)var.size();
         const int32_t i = h_hv[h];
-        for (int32_t k = h_ptr[i]; k < h_ptr[i + 1]; k += SEG_LEN) {
+        for (int32_t k = h_ptr[i]; k < h_ptr[i + 1]; k += SPLIT_SEG) {
             var.push_back(i);
             beg.push_back(k);
         }
@@ -580,9 +580,13 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         G_var = c->opt.group > 0 ? c->opt.group : std::max(1, std::min(32, pow2_ceil((lq + 3) / 4)));
         const int light = std::min(16 * G_var, HEAVY_LEN);
         for (int s = 0; s < 2; ++s)
-            if (sb[s].cv.kind == CK_CSR || sb[s].cv.kind == CK_SPLIT2) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = light; }
-        e = heavy_list2(c->ar, cp0, HEAVY_LEN, cp1, HEAVY_LEN, c->n, &hv, &nhv, c->stream);
-        if (e == cudaSuccess) e = range_list2(c->ar, cp0, cp1, c->n, light, HEAVY_LEN, &mv, &nmv, c->stream);
+            if (sb[s].cv.kind == CK_CSR) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = light; }
+            else if (sb[s].cv.kind == CK_SPLIT2) { sb[s].cv.G = G_var; sb[s].cv.heavy_len = std::min(light, SPLIT_HEAVY); }
+        // a split view sends every column above SPLIT_HEAVY entries through the
+        // balanced segment pre-pass
+        const int heavy = (sb[1].cv.kind == CK_SPLIT2 && !cp0) ? SPLIT_HEAVY : HEAVY_LEN;
+        e = heavy_list2(c->ar, cp0, heavy, cp1, heavy, c->n, &hv, &nhv, c->stream);
+        if (e == cudaSuccess) e = range_list2(c->ar, cp0, cp1, c->n, light, std::max(light, heavy), &mv, &nmv, c->stream);
         if (e != cudaSuccess) { fail_cuda(c, e, "variable length classes"); return bail(MWU_ERR_CUDA); }
         if (sb[1].cv.kind == CK_SPLIT2 && nhv > 0 && (rc = split_segments(c, sb[1].cv, hv, nhv)) != MWU_OK)
             return bail(rc);

@@ -76,6 +76,10 @@ constexpr int TILE_SMEM = 48 * 1024;   // shared memory of one tile's input wind
 constexpr int HEAVY_LEN = 4096;        // columns longer than this take a whole block in the direction kernel
 template <class T> constexpr int tile_wmax() { return TILE_SMEM / (int)sizeof(T); }
 
+// split view (CK_SPLIT2): columns longer than SPLIT_HEAVY entries go through
+// the segment pre-pass in SPLIT_SEG-entry pieces (one warp each)
+constexpr int SPLIT_HEAVY = 256;
+constexpr int SPLIT_SEG = 256;
 constexpr int SHORT_LEN = 16;
 constexpr int MED_LEN = 256;
 constexpr int MED_LANES = 16;
@@ -99,9 +103,9 @@ struct ColView {
     const int32_t *idx2 = nullptr;
     const void *xsrc = nullptr;
     // CK_SPLIT2 columns of the problem's heavy variables (heavy_var, longer than
-    // HEAVY_LEN on either side) cut into SEG_LEN-entry segments of the combined
-    // column: heavy variable h owns segments [cseg_first[h], cseg_first[h+1]),
-    // segment q covers combined entries [cseg_beg[q], min(cseg_beg[q] + SEG_LEN,
+    // SPLIT_HEAVY) cut into SPLIT_SEG-entry segments of the combined column:
+    // heavy variable h owns segments [cseg_first[h], cseg_first[h+1]), segment q
+    // covers combined entries [cseg_beg[q], min(cseg_beg[q] + SPLIT_SEG,
     // ptr[cseg_var[q] + 1])); k_split_seg writes one partial sum per segment
     int32_t n_cseg = 0;
     const int32_t *cseg_first = nullptr, *cseg_var = nullptr, *cseg_beg = nullptr;

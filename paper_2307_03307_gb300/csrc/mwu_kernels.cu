@@ -262,25 +262,33 @@ template <class T, class F>
 __device__ __forceinline__ T split_gather(const ColView &cv, int64_t i, int b1, int e1, int q0, int q1, int lane,
                                           int step, const F &w) {
     // z and the endpoint lists are streamed once (evict-first loads), so that
-    // x, gathered at random, stays in L2
+    // x, gathered at random, stays in L2.  Each round issues up to four z loads
+    // and four endpoint loads together, then the four x gathers, so a short
+    // column costs two dependent memory latencies, not one per entry.
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
     const T *z = w.v;
-    int k = b1 + lane;
-    for (; k + 3 * step < e1; k += 4 * step) {
-        const T z0 = __ldcs(z + k), z1 = __ldcs(z + k + step), z2 = __ldcs(z + k + 2 * step), z3 = __ldcs(z + k + 3 * step);
-        a0 += w.of_value(z0); a1 += w.of_value(z1); a2 += w.of_value(z2); a3 += w.of_value(z3);
-    }
-    for (; k < e1; k += step) a0 += w.of_value(__ldcs(z + k));
     const T *xx = static_cast<const T *>(cv.xsrc);
-    const T xi = xx[i];
-    k = q0 + lane;
-    for (; k + 3 * step < q1; k += 4 * step) {
-        const int u0 = __ldcs(cv.idx2 + k), u1 = __ldcs(cv.idx2 + k + step), u2 = __ldcs(cv.idx2 + k + 2 * step),
-                  u3 = __ldcs(cv.idx2 + k + 3 * step);
-        const T x0 = __ldg(xx + u0), x1 = __ldg(xx + u1), x2 = __ldg(xx + u2), x3 = __ldg(xx + u3);
-        a0 += w.of_value(xi + x0); a1 += w.of_value(xi + x1); a2 += w.of_value(xi + x2); a3 += w.of_value(xi + x3);
+    const T xi = __ldg(xx + i);
+    for (int kz = b1 + lane, kx = q0 + lane; kz < e1 || kx < q1; kz += 4 * step, kx += 4 * step) {
+        T zv[4];
+        int ui[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int jz = kz + r * step, jx = kx + r * step;
+            zv[r] = jz < e1 ? __ldcs(z + jz) : T(0);
+            ui[r] = jx < q1 ? __ldcs(cv.idx2 + jx) : -1;
+        }
+        T xv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) xv[r] = ui[r] >= 0 ? __ldg(xx + ui[r]) : T(0);
+        T t[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            t[r] = (kz + r * step < e1) ? w.of_value(zv[r]) : T(0);
+            if (ui[r] >= 0) t[r] += w.of_value(xi + xv[r]);
+        }
+        a0 += t[0]; a1 += t[1]; a2 += t[2]; a3 += t[3];
     }
-    for (; k < q1; k += step) a0 += w.of_value(xi + __ldg(xx + __ldcs(cv.idx2 + k)));
     return (a0 + a1) + (a2 + a3);
 }
 
@@ -690,7 +698,7 @@ __global__ void __launch_bounds__(BLOCK) k_split_seg(Problem<T> p, int potential
         const int i = cv.cseg_var[q];
         const int c0 = cv.ptr[i], c1 = cv.ptr[i + 1], q0 = cv.ptr2[i], q1 = cv.ptr2[i + 1];
         const int cz = c0 + ((c1 - q1) - (c0 - q0));   // combined index where the x list starts
-        const int kb = cv.cseg_beg[q], ke = min(kb + SEG_LEN, c1);
+        const int kb = cv.cseg_beg[q], ke = min(kb + SPLIT_SEG, c1);
         const int zb = (c0 - q0) + (min(max(kb, c0), cz) - c0), ze = (c0 - q0) + (min(ke, cz) - c0);
         const int xb = q0 + (max(kb, cz) - cz), xe = q0 + (max(ke, cz) - cz);
         T sum = split_gather<T>(cv, i, zb, max(zb, ze), xb, max(xb, xe), lane, 32, wc);
@@ -701,7 +709,7 @@ __global__ void __launch_bounds__(BLOCK) k_split_seg(Problem<T> p, int potential
 
 // a4, a5 with the deferred x update of the previous iteration fused in.
 template <class T>
-__global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int potential_mode, float *grad_obj) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 4) k_dir(Problem<T> p, int keep_gh, int potential_mode, float *grad_obj) {
     __shared__ T sm[32];
     __shared__ double smd[32];
     DevState *st = p.st;
@@ -743,8 +751,24 @@ __global__ void __launch_bounds__(BLOCK) k_dir(Problem<T> p, int keep_gh, int po
                 kahan_add(dense_dot[s], dense_cmp[s], (p.side[s].cv.cvec ? (T)p.side[s].cv.cvec[i] : T(1)) * di);
     };
 
+    // heavy split columns (P without CSR columns): their segment partials,
+    // a warp per variable, added in segment order by the fixed shuffle tree
+    const bool split_heavy = C.cv.kind == CK_SPLIT2 && P.cv.kind != CK_CSR && !hacc;
+    if (split_heavy) {
+        const int wl = threadIdx.x & 31;
+        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t hh = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; hh < p.n_heavy_var; hh += nw) {
+            const int64_t i = p.heavy_var[hh];
+            T a = T(0);
+            for (int q = C.cv.cseg_first[hh] + wl; q < C.cv.cseg_first[hh + 1]; q += 32) a += p.cseg_part[q];
+            a = group_sum(a, 32);
+            T sg = col_gather<T, true>(P.cv, i, wl, 32, wp, T(1));
+            sg = group_sum(sg, 32);
+            if (wl == 0) finish(i, sg, a);
+        }
+    }
     // heavy variables (long CSR columns): whole block
-    for (int hh = blockIdx.x; hh < p.n_heavy_var; hh += gridDim.x) {
+    for (int hh = split_heavy ? p.n_heavy_var : blockIdx.x; hh < p.n_heavy_var; hh += gridDim.x) {
         int64_t i = p.heavy_var[hh];
         T sg, sh;
         if (P.cv.kind == CK_CSR) sg = heavy_col_gather<T>(P.cv, i, wp, sm);
@@ -2290,7 +2314,7 @@ template <class T> cudaError_t launch_dir(const Problem<T> &p, int keep_gh, cuda
     }
     if (p.side[1].cv.kind == CK_SPLIT2 && p.side[1].cv.n_cseg > 0) {
         const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)p.side[1].cv.n_cseg * 32 + BLOCK - 1) / BLOCK,
-                                                                    p.grid_var));
+                                                                    p.grid_spmv));
         k_split_seg<T><<<gs, BLOCK, 0, s>>>(p, 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -2358,7 +2382,7 @@ template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const
     (void)x;
     if (p.side[1].cv.kind == CK_SPLIT2 && p.side[1].cv.n_cseg > 0) {
         const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)p.side[1].cv.n_cseg * 32 + BLOCK - 1) / BLOCK,
-                                                                    p.grid_var));
+                                                                    p.grid_spmv));
         k_split_seg<T><<<gs, BLOCK, 0, s>>>(p, 1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

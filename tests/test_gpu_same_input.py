@@ -91,6 +91,7 @@ class Inputs:
             g = wl.graph
             self.x = (0.1 + rng.uniform(0.0, 20.0 / eta, self.n)).astype(dt)
             self.z = (self.x[g.u.numpy()] + self.x[g.v.numpy()]).astype(dt)
+
         self.dy = (rng.uniform(0.0, 3.0 / eta, self.mP)).astype(dt)
         self.dz = (rng.uniform(0.0, 3.0 / eta, self.mC)).astype(dt)
         d = rng.uniform(0.0, 1.0, self.n) * self.x.astype(np.float64)
