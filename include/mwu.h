@@ -337,7 +337,9 @@ int mwu_get_vector(mwu_ctx *ctx, int32_t which, void *dst, int64_t n, int32_t as
 /* Copy the current scalars. */
 int mwu_get_scalars(mwu_ctx *ctx, mwu_scalars *out);
 
-/* Accumulated per-kernel-class times (see mwu_timing); reset != 0 clears them. */
+/* Accumulated per-kernel-class times (see mwu_timing); reset != 0 clears them.
+ * For a batch context, the sums over its instances (which run concurrently,
+ * so the sum exceeds the wall time of the batch). */
 int mwu_get_timing(mwu_ctx *ctx, mwu_timing *out, int32_t reset);
 
 /* Tiles of the staged forward SpMV of each side (opt.spmv_tiles): *tiles_p and

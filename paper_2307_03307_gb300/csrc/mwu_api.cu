@@ -1101,7 +1101,17 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
 
 int mwu_get_timing(mwu_ctx *c, mwu_timing *out, int32_t reset) {
     if (!c) return MWU_ERR_INVALID;
-    if (out) *out = c->tim;
+    mwu_timing t = c->tim;
+    for (mwu_ctx *b : c->batch) {   // a batch context: the sum over its instances
+        t.dir_ms += b->tim.dir_ms;
+        t.spmv_ms += b->tim.spmv_ms;
+        t.cand_ms += b->tim.cand_ms;
+        t.update_ms += b->tim.update_ms;
+        t.iters += b->tim.iters;
+        t.cand_passes += b->tim.cand_passes;
+        if (reset) b->tim = mwu_timing{};
+    }
+    if (out) *out = t;
     if (reset) c->tim = mwu_timing{};
     return MWU_OK;
 }
