@@ -101,6 +101,9 @@ def parse():
                          "(not bit-reproducible)")
     ap.add_argument("--no-split", action="store_true",
                     help="vertex cover: gather z over every vertex's incident edge ids instead of the split view")
+    ap.add_argument("--warm-start", type=int, default=-1,
+                    help="K-candidate search: 1 starts the exponential phase at the previous step size (the "
+                         "start Table 2 of the paper uses), 0 at alpha = 1 (Alg. 3 as printed); -1: per workload")
     ap.add_argument("--no-tiles", action="store_true",
                     help="row-binned gather SpMV everywhere (no staged tiles for banded CSR sides)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
@@ -360,7 +363,9 @@ def run_ours(args):
     wl = make_workload(name, "cuda")
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
+    warm = args.warm_start if args.warm_start >= 0 else int(step_name == "kary")
     opts = dict(step=step, precision=precision, drop_covered=int(args.drop), timing=0 if args.eager else 1,
+                warm_start=warm,
                 use_graph=0 if args.eager else 1, spmv_tiles=-1 if args.no_tiles else 0,
                 h_scatter=int(args.h_scatter), dv_scatter=int(args.dv_scatter), col_split=-1 if args.no_split else 0)
     if batch:
@@ -422,7 +427,7 @@ def run_ours(args):
         ab = {c: sum(a[c] * i for a, i in zip(abk, it_k)) / tot_it for c in ("dir", "spmv", "cand", "update")}
     else:
         ab = algorithmic_bytes(lp, N, E, wl.graph.n_left or 0, split=split, fused_pairs=lp == "densest")
-    cfg.update({"step": step_name, "K": 8 if step_name == "kary" and prec == "f32" else 1,
+    cfg.update({"step": step_name, "K": 8 if step_name == "kary" and prec == "f32" else 1, "warm_start": bool(warm),
                 "covering_rows": "dropped when satisfied" if args.drop else "kept",
                 "precision": "f64 (plain form)" if prec == "fp64" else "f32 vectors, f64 reductions",
                 "h": ("row scatter (atomic adds)" if args.h_scatter else

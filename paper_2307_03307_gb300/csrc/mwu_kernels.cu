@@ -1189,6 +1189,57 @@ __device__ __forceinline__ void cand_push_m(CandAcc<T> &c, const T *ca, const T 
     }
 }
 
+// Covering rows of a search pass (FP32, exponential phase MODE 0 or
+// refinement MODE 1, K candidates): every exponent x_k = -eta (z + alpha_k dz
+// - s_c) is <= 0 (s_c = min z), so R_k needs no running maximum against
+// overflow: it is accumulated with the constant shift COV_SHIFT,
+//   R_k += e^{a + COV_SHIFT} e^{-b_k},   a = -eta (z - s_c), b_k = alpha_k eta dz,
+// with e^{-b_k} from an exact recurrence along the schedule (squaring when
+// alpha doubles, a product with e^{-delta eta dz} when it grows by delta), so a
+// row costs two exponentials whatever K, and no warp vote or rescale branch.
+// Terms below e^{-87} flush to zero; a row with a < -COV_SHIFT - 87 has no
+// representable term and updates only the minima.  The finish clamps
+// ln R_k (unshifted) at COV_FLOOR: below it the sum is no longer exact and Phi
+// takes its lower bound -(COV_FLOOR - ln S_c)/eta, which can only reject a
+// candidate (f >= 1 is then decided on a value at most Phi).
+constexpr float COV_SHIFT = 60.0f;
+constexpr double COV_FLOOR = -110.0;
+
+template <int MODE>
+__device__ __forceinline__ void cand_push_cov(CandAcc<float> &c, const float *ca, const float *al, float cd, float v,
+                                              float dv, float eta, float s, float hi) {
+    if (!(v < hi)) return;   // a dropped covering row
+    const float a = -eta * (v - s);
+    if (a < -COV_SHIFT - 87.0f) {   // e^{a + COV_SHIFT} flushes to zero: only the minima move
+        if (MODE == 0) {
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) c.zm[k] = fminf(c.zm[k], fmaf(al[k], dv, v));
+        }
+        return;
+    }
+    const float Ash = __expf(a + COV_SHIFT);
+    const float A = __expf(a);
+    float b = ca[0] * dv;
+    float u = one_minus_exp_neg(b);
+    float r = __expf(-b);
+    float ud = 0.0f, rd = 1.0f;
+    if (MODE == 1) {
+        const float bd = cd * dv;
+        ud = one_minus_exp_neg(bd);
+        rd = __expf(-bd);
+    }
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k > 0) {
+            if (MODE == 0) { u = u * (2.0f - u); r = r * r; }
+            else { u = fmaf(ud, 1.0f - u, u); r = r * rd; }
+        }
+        c.R[k] = fmaf(Ash, r, c.R[k]);
+        c.Tt[k] = fmaf(A, u, c.Tt[k]);
+        if (MODE == 0) c.zm[k] = fminf(c.zm[k], fmaf(al[k], dv, v));
+    }
+}
+
 // merge b into a (sgn as above), in precision U with rescale factors in T
 template <class T, class U>
 __device__ __forceinline__ void cand_merge1(U &mx, U &R, U &Tt, U &zm, U bmx, U bR, U bT, U bzm, int sgn) {
@@ -1383,7 +1434,7 @@ __device__ void loop_turn_end(DevState *st, cudaGraphConditionalHandle cond) {
 // are scarce), the sums and the final combination in FP64.
 template <class T>
 __device__ double side_value(const Side<T> &q, int sg, const DevState *st, int ss, double a, double mx, double R,
-                             double Tt) {
+                             double Tt, bool floor_cov) {
     // ln S, 1/S and 1/eta come precomputed with S and eta: this runs on the
     // critical path of every pass, where FP64 divisions are slow on GB300
     const double inv_eta = st->inv_eta, lS0 = st->lnS[ss];
@@ -1395,7 +1446,10 @@ __device__ double side_value(const Side<T> &q, int sg, const DevState *st, int s
     }
     // Phi = -(1/eta) ln(R_true / S_c) = -(1/eta) ln(1 - T_true / S_c)
     const double qv = Tt * st->invS[ss];
-    return (qv <= 0.5) ? -(double)t_log1p((T)(-qv)) * inv_eta : -(mx + (double)t_log((T)R) - lS0) * inv_eta;
+    if (qv <= 0.5) return -(double)t_log1p((T)(-qv)) * inv_eta;
+    double lr = mx + (double)t_log((T)R);
+    if (floor_cov && !(lr > COV_FLOOR)) lr = COV_FLOOR;   // constant-shift sums: Phi's lower bound
+    return -(lr - lS0) * inv_eta;
 }
 
 // Last block of a candidate pass: merges the (side, k) quantities, k < K,
@@ -1404,7 +1458,7 @@ __device__ double side_value(const Side<T> &q, int sg, const DevState *st, int s
 // writes Psi_k / Phi_k, the derivative of candidate 0 and min(z + alpha_k dz)
 // to fin.
 template <class T>
-__device__ void cand_finish_merge(const Problem<T> &p, int gP, int K, double (*fin)[KMAX][4]) {
+__device__ void cand_finish_merge(const Problem<T> &p, int gP, int K, double (*fin)[KMAX][4], bool floor_cov = false) {
     const DevState *st = p.st;
     block_merge_shifted<T, 3, true>(
         2 * K, T(1),
@@ -1423,7 +1477,7 @@ __device__ void cand_finish_merge(const Problem<T> &p, int gP, int K, double (*f
             const int ss = q < K ? 0 : 1, k = q % K;
             const Side<T> &sd = p.side[ss];
             const double a = st->alpha[k];
-            fin[ss][k][0] = side_value(sd, sd.sign, st, ss, a, (double)M, tot[0], tot[1]);
+            fin[ss][k][0] = side_value(sd, sd.sign, st, ss, a, (double)M, tot[0], tot[1], floor_cov);
             // Newton: Psi' = D/R (packing side), Phi' = D/R (covering side); both
             // sums carry the same shift, so the ratio needs no rescale
             fin[ss][k][1] = (sd.rv.kind == RK_DENSE1) ? st->dense_dv[ss] : (tot[0] > 0.0 ? tot[2] / tot[0] : 0.0);
@@ -1442,6 +1496,33 @@ __device__ __forceinline__ void cand_stream(CandAcc<T> &acc, const CandSched<T> 
     const int K = sc.K;
     const T camax = sched_camax(ca, K);
     int64_t start = 4 * tid;
+    if constexpr (sizeof(T) == 4 && SGN < 0 && KC == KMAX && (MODE == 0 || MODE == 1)) {
+        // covering rows of a search pass: constant shift, recurrences (cand_push_cov)
+        CandAcc<float> &c = reinterpret_cast<CandAcc<float> &>(acc);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) c.mx[k] = -COV_SHIFT;
+        const float *cap = reinterpret_cast<const float *>(ca), *alp = reinterpret_cast<const float *>(al);
+        for (int64_t j0 = start; j0 < m; j0 += 4 * nthr) {
+            const int nr = (int)min((int64_t)4, m - j0);
+            float vv[4], dd[4];
+            if (nr == 4) {
+                const float4 a4 = __ldcs(reinterpret_cast<const float4 *>(sd.v + j0));
+                const float4 b4 = __ldcs(reinterpret_cast<const float4 *>(sd.dv + j0));
+                vv[0] = a4.x; vv[1] = a4.y; vv[2] = a4.z; vv[3] = a4.w;
+                dd[0] = b4.x; dd[1] = b4.y; dd[2] = b4.z; dd[3] = b4.w;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    vv[r] = r < nr ? (float)sd.v[j0 + r] : 0.0f;
+                    dd[r] = r < nr ? (float)sd.dv[j0 + r] : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < nr) cand_push_cov<MODE>(c, cap, alp, (float)cd, vv[r], dd[r], (float)eta, (float)sh, (float)hi);
+        }
+        return;
+    }
     if (KC == 1 && sizeof(T) == 4) {
         // one candidate per row leaves the pass short of loads in flight: take
         // eight rows per thread and iteration (four float4 loads issued together)
@@ -1804,7 +1885,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 3 : 1) k_cand(Problem<
     if (!last_block_done(&st->counter[2])) return;
     {
         __shared__ double fin[2][KMAX][4];
-        cand_finish_merge(p, gP, K, fin);
+        // covering sums of a search pass with K = KMAX carry the constant shift (cand_push_cov)
+        const bool floor_cov = sizeof(T) == 4 && K == KMAX && (s_sc.mode == 0 || s_sc.mode == 1);
+        cand_finish_merge(p, gP, K, fin, floor_cov);
         __syncthreads();
         if (threadIdx.x == 0) {
             int ok[KMAX];

@@ -60,7 +60,7 @@ def _ref_worker(rank, world, port, outdir):
     import io
     import contextlib
     import bench
-    args = argparse.Namespace(scale=6, seed=2, steps=1, warmup=0, step="newton", gpus=world)
+    args = argparse.Namespace(workload="bmatch-2k", steps=1, warmup=0, step=None, gpus=world, cpu_procs=2)
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         bench.run_reference(args)
