@@ -136,8 +136,10 @@ typedef struct {
     int32_t max_newton;        /* Newton evaluations per step search; default 8              */
     double newton_tol;         /* Newton has converged once |alpha' - alpha| <= newton_tol
                                   alpha; <= 0 selects eps/20                                 */
-    int32_t batch_workers;     /* mwu_solve_batch: instances solved at once (host threads,
-                                  one stream each); 0 = tuned online over 4, 8, 16            */
+    int32_t batch_workers;     /* mwu_solve_batch: threads per block of the persistent batch
+                                  solve, 256, 512 or 1024; 0 (default) = autotuned: the
+                                  first solve times the whole batch with each and keeps
+                                  the fastest (mwu_batch_tuning reports the timings)      */
     int32_t drop_covered;      /* 1: keep only the unsatisfied covering rows, the last step
                                   of the loop of Alg. 1 and Alg. 2 (C <- {c_j : c_j^T x < 1}):
                                   a row with (Cx)_j >= 1 leaves smin, h, Phi and Phi'.  x
@@ -338,8 +340,7 @@ int mwu_get_vector(mwu_ctx *ctx, int32_t which, void *dst, int64_t n, int32_t as
 int mwu_get_scalars(mwu_ctx *ctx, mwu_scalars *out);
 
 /* Accumulated per-kernel-class times (see mwu_timing); reset != 0 clears them.
- * For a batch context, the sums over its instances (which run concurrently,
- * so the sum exceeds the wall time of the batch). */
+ * A batch context has no per-class times (its solve is one kernel). */
 int mwu_get_timing(mwu_ctx *ctx, mwu_timing *out, int32_t reset);
 
 /* Tiles of the staged forward SpMV of each side (opt.spmv_tiles): *tiles_p and
@@ -406,24 +407,42 @@ int mwu_candidates_static(const float *v, const float *dv, int64_t m, int32_t si
                           double *val, double *vmin, void *stream);
 
 /* ------------------------------------------------------------- batched */
-/* Many independent instances in one context (one launch per phase over all
- * instances, captured in a CUDA graph).  Supported: PACKING over INCIDENCE
- * matrices with optional row_bound (b-matching, Appendix A.1 with lb = 0).
- * P[k] is instance k's matrix; objective rows are ones. */
+/* Many independent b-matching LPs (Appendix A.1 with lb = 0: max 1^T x,
+ * diag(1/b) M x <= 1, M the vertex-edge incidence) in one context.  P[k] is
+ * instance k's MWU_MAT_INCIDENCE edge list (host or device) with optional
+ * row_bound b (capacities > 0); the objective rows are ones.  The instances
+ * are packed into one set of device arrays (the vertex -> incident-edge lists
+ * built with a stable radix sort).  Options: eps, eta_factor, max_iter,
+ * outer_tol, max_probes, max_passes, K, grad_tol, warm_start, step
+ * (MWU_STEP_KARY or MWU_STEP_NEWTON), max_newton and newton_tol as for one
+ * instance (FP32 vectors with FP64 reductions); batch_workers selects the
+ * block size.  MWU_ERR_INVALID for other matrix
+ * kinds, an empty instance or a bad endpoint or bound. */
 int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
                      mwu_ctx **out);
 
-/* Solve every instance of a batch context: per-instance bisection on M, the
- * instances solved concurrently (opt.batch_workers of them at a time, each on
- * its own stream with its own captured iterations, largest first).  Results do
- * not depend on the concurrency.  objective/iters may be NULL; otherwise host
- * arrays of `count` entries.  The batch context is not safe for concurrent use
- * from several host threads.  Each instance runs on three streams; with the
- * driver's default of 8 hardware work queues they share queues, so set
- * CUDA_DEVICE_MAX_CONNECTIONS=32 in the environment before the process
- * initialises CUDA (the Python package does so at import when CUDA is not yet
- * initialised; 256 instances: 1.72 s against 2.09 s). */
+/* Solve every instance of a batch context in one persistent launch (captured
+ * in a CUDA graph with the reset of its work queue): each block takes the
+ * next instance, largest first, and runs its whole solve -- the automatic
+ * bracket and the geometric bisection on M of Sec. 2.2, and per probe the
+ * iterations of Alg. 2 with the configured step search -- with no host round
+ * trip.  An instance is solved by one block with a fixed order of every sum,
+ * so its certified objective does not depend on the batch or the schedule
+ * (only on the block size).  objective / iters: host arrays of `count`
+ * entries or NULL; total: the sums (objective, probes, iters, evals, passes)
+ * and the wall time.  The first call of a context with batch_workers = 0
+ * runs the autotuner first (three extra whole-batch solves).  Not safe for
+ * concurrent use of one context. */
 int mwu_solve_batch(mwu_ctx *ctx, double *objective, int64_t *iters, mwu_result *total);
+
+/* The autotuner's choice (threads per block, 0 before the first solve) and
+ * its timings: ms[0..2] = milliseconds of the whole batch with 256, 512 and
+ * 1024 threads per block (0 where not timed).  Either output may be NULL. */
+int mwu_batch_tuning(mwu_ctx *ctx, int32_t *threads, double *ms);
+
+/* Per-instance candidate passes and probes of the last mwu_solve_batch (host
+ * arrays of `count` entries, either NULL).  MWU_ERR_STATE before a solve. */
+int mwu_batch_stats(mwu_ctx *ctx, int64_t *passes, int32_t *probes);
 
 /* ------------------------------------------------------------ diagnostics */
 /* u[i] = 1 - e^{-b[i]} for b[i] >= 0, by the same device function the

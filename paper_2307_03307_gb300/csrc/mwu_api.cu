@@ -57,9 +57,19 @@ struct mwu_ctx {
     double target = 1.0;
     bool have_direction = false;
     bool trace = false;          // MWU_TRACE=1: one line per probe on stderr
-    // batch front end
-    std::vector<mwu_ctx *> batch;
-    int batch_workers_used = 0;
+    // batch front end: the persistent solve of packed b-matching instances
+    bool is_batch = false;
+    BatchDesc bd{};
+    int32_t batch_count = 0;
+    int64_t batch_edges = 0;
+    std::vector<int64_t> batch_e;            // edges per instance
+    int batch_nt = 0;                        // threads per block in use (0 = not tuned yet)
+    int batch_blocks = 0;
+    double tune_ms[3] = {0.0, 0.0, 0.0};     // autotuner: whole-batch time with 256, 512, 1024 threads
+    cudaGraphExec_t batch_graph = nullptr;   // queue reset + the persistent launch
+    int batch_graph_nt = 0;
+    std::vector<int64_t> batch_last_passes;  // per instance, of the last solve
+    std::vector<int32_t> batch_last_probes;
 };
 
 // ------------------------------------------------------------ helpers
@@ -629,7 +639,6 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
 
 void mwu_destroy(mwu_ctx *c) {
     if (!c) return;
-    for (mwu_ctx *b : c->batch) mwu_destroy(b);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->gexec_chunk) cudaGraphExecDestroy(c->gexec_chunk);
     if (c->gexec_one) cudaGraphExecDestroy(c->gexec_one);
@@ -640,6 +649,7 @@ void mwu_destroy(mwu_ctx *c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
     if (c->kc_stream) cudaStreamDestroy(c->kc_stream);
+    if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
     delete c;
 }
 
@@ -1102,15 +1112,6 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
 int mwu_get_timing(mwu_ctx *c, mwu_timing *out, int32_t reset) {
     if (!c) return MWU_ERR_INVALID;
     mwu_timing t = c->tim;
-    for (mwu_ctx *b : c->batch) {   // a batch context: the sum over its instances
-        t.dir_ms += b->tim.dir_ms;
-        t.spmv_ms += b->tim.spmv_ms;
-        t.cand_ms += b->tim.cand_ms;
-        t.update_ms += b->tim.update_ms;
-        t.iters += b->tim.iters;
-        t.cand_passes += b->tim.cand_passes;
-        if (reset) b->tim = mwu_timing{};
-    }
     if (out) *out = t;
     if (reset) c->tim = mwu_timing{};
     return MWU_OK;
@@ -1531,102 +1532,251 @@ static int potential_all_rows(mwu_ctx *c, const float *x, double *pot, float *gr
 }
 
 // ------------------------------------------------------------ batch
+// The instances are packed into one set of arrays (edges, capacities and the
+// vertex -> incident-edge lists of each, built with the setup's stable radix
+// sort) and solved by one persistent launch (k_batch_solve): a block per
+// instance at a time, taken from a work queue in decreasing size.
 int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt, mwu_ctx **out) {
     if (!out || !P || count <= 0) return fail(nullptr, MWU_ERR_INVALID, "bad batch arguments");
     *out = nullptr;
+    mwu_options o;
+    if (opt) o = *opt;
+    else mwu_default_options(&o);
+    if (!(o.eps > 0.0 && o.eps < 1.0)) return fail(nullptr, MWU_ERR_INVALID, "eps must lie in (0,1)");
+    if (o.batch_workers != 0 && o.batch_workers != 256 && o.batch_workers != 512 && o.batch_workers != 1024)
+        return fail(nullptr, MWU_ERR_INVALID, "batch_workers must be 0 (autotuned), 256, 512 or 1024");
+    int64_t Et = 0, Nt = 0;
+    for (int k = 0; k < count; ++k) {
+        if (P[k].kind != MWU_MAT_INCIDENCE || !P[k].edges || P[k].n_edges <= 0 || P[k].n_vertices <= 0)
+            return fail(nullptr, MWU_ERR_INVALID, "batch instance " + std::to_string(k) +
+                                                  ": PACKING over a non-empty MWU_MAT_INCIDENCE edge list required");
+        if (2 * P[k].n_edges >= (int64_t)INT32_MAX) return fail(nullptr, MWU_ERR_INVALID, "instance too large");
+        Et += P[k].n_edges;
+        Nt += P[k].n_vertices;
+    }
     mwu_ctx *c = new mwu_ctx();
     c->kind = -1;
-    if (opt) c->opt = *opt;
-    else mwu_default_options(&c->opt);
-    for (int k = 0; k < count; ++k) {
-        if (P[k].kind != MWU_MAT_INCIDENCE && P[k].kind != MWU_MAT_CSR) {
-            mwu_destroy(c);
-            return fail(nullptr, MWU_ERR_INVALID, "batch instances must be PACKING over INCIDENCE or CSR");
-        }
-        mwu_ctx *sub = nullptr;
-        mwu_options so = c->opt;
-        so.stream = nullptr;   // every instance on its own stream, so that instances overlap
-        int rc = mwu_create(MWU_PACKING, &P[k], nullptr, nullptr, &so, &sub);
-        if (rc != MWU_OK) {
-            std::string m = g_create_error;
-            mwu_destroy(c);
-            return fail(nullptr, rc, "batch instance " + std::to_string(k) + ": " + m);
-        }
-        c->batch.push_back(sub);
+    c->is_batch = true;
+    if (o.step != MWU_STEP_KARY && o.step != MWU_STEP_NEWTON)
+        return fail(nullptr, MWU_ERR_INVALID, "batch: step must be MWU_STEP_KARY or MWU_STEP_NEWTON");
+    if (o.max_passes <= 0) o.max_passes = o.step == MWU_STEP_NEWTON ? 16 : 6;
+    if (o.max_newton <= 0) o.max_newton = 8;
+    if (!(o.newton_tol > 0.0)) o.newton_tol = o.eps / 20.0;
+    if (o.outer_tol <= 0.0) o.outer_tol = o.eps;
+    if (o.max_probes <= 0) o.max_probes = 64;
+    if (o.grad_tol < 0.0) o.grad_tol = std::ldexp(1.0, -16);
+    if (o.K < 1 || o.K > KMAX) o.K = KMAX;
+    c->opt = o;
+    auto bail = [&](int rc) {
+        g_create_error = c->err;
+        mwu_destroy(c);
+        return rc;
+    };
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "cannot create a CUDA stream (no device?)";
+        return bail(MWU_ERR_CUDA);
     }
+    c->own_stream = true;
+    c->ar.set_stream(c->stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "no CUDA device";
+        return bail(MWU_ERR_CUDA);
+    }
+    cudaStream_t s = c->stream;
+    std::vector<int64_t> eoff(count + 1, 0), voff(count + 1, 0);
+    for (int k = 0; k < count; ++k) {
+        eoff[k + 1] = eoff[k] + P[k].n_edges;
+        voff[k + 1] = voff[k] + P[k].n_vertices;
+        c->batch_e.push_back(P[k].n_edges);
+    }
+    c->batch_count = count;
+    c->batch_edges = Et;
+    int32_t *edges = c->ar.alloc<int32_t>(2 * Et), *vptr = c->ar.alloc<int32_t>(Nt + count), *eids = c->ar.alloc<int32_t>(2 * Et);
+    float *bound = c->ar.alloc<float>(Nt);
+    int64_t *d_eoff = c->ar.alloc<int64_t>(count + 1), *d_voff = c->ar.alloc<int64_t>(count + 1);
+    int32_t *d_order = c->ar.alloc<int32_t>(count);
+    int *d_err = c->ar.alloc<int>(4);
+    if (!edges || !vptr || !eids || !bound || !d_eoff || !d_voff || !d_order || !d_err) {
+        c->err = "allocating the packed batch";
+        return bail(MWU_ERR_OOM);
+    }
+    if (cudaMemsetAsync(d_err, 0, 4 * sizeof(int), s) != cudaSuccess) { c->err = "clearing flags"; return bail(MWU_ERR_CUDA); }
+    std::vector<float> ones;
+    for (int k = 0; k < count; ++k) {
+        const int64_t E = P[k].n_edges, n = P[k].n_vertices;
+        int32_t *ek = edges + 2 * eoff[k];
+        if (cudaMemcpyAsync(ek, P[k].edges, 8 * (size_t)E, cudaMemcpyDefault, s) != cudaSuccess ||
+            validate_edges(ek, E, (int32_t)n, d_err, s) != cudaSuccess) {
+            cudaGetLastError();
+            c->err = "copying instance " + std::to_string(k);
+            return bail(MWU_ERR_CUDA);
+        }
+        int32_t *vp = nullptr, *sl = nullptr, *el = nullptr;
+        cudaError_t e = build_vertex_slots(c->ar, ek, E, (int32_t)n, &vp, &sl, s);
+        if (e == cudaSuccess) e = slots_to_edges(c->ar, sl, 2 * E, &el, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vptr + voff[k] + k, vp, 4 * (size_t)(n + 1), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(eids + 2 * eoff[k], el, 8 * (size_t)E, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) {
+            if (P[k].row_bound) {
+                e = cudaMemcpyAsync(bound + voff[k], P[k].row_bound, 4 * (size_t)n, cudaMemcpyDefault, s);
+            } else {
+                ones.assign((size_t)n, 1.0f);
+                e = cudaMemcpyAsync(bound + voff[k], ones.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
+        }
+        if (e != cudaSuccess) { fail_cuda(c, e, "packing a batch instance"); return bail(MWU_ERR_CUDA); }
+        c->ar.release_tmp();
+    }
+    if (validate_positive(bound, Nt, 7, d_err, s) != cudaSuccess) { c->err = "validating bounds"; return bail(MWU_ERR_CUDA); }
+    int rc = check_err_flag(c, d_err);
+    if (rc != MWU_OK) return bail(rc);
+    std::vector<int32_t> order(count);
+    for (int k = 0; k < count; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return P[a].n_edges > P[b].n_edges; });
+    TRY_CUDA(c, cudaMemcpyAsync(d_eoff, eoff.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s));
+    TRY_CUDA(c, cudaMemcpyAsync(d_voff, voff.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s));
+    TRY_CUDA(c, cudaMemcpyAsync(d_order, order.data(), 4 * (size_t)count, cudaMemcpyHostToDevice, s));
+    BatchDesc &B = c->bd;
+    B.count = count;
+    B.order = d_order;
+    B.eoff = d_eoff;
+    B.voff = d_voff;
+    B.edges = edges;
+    B.bound = bound;
+    B.vptr = vptr;
+    B.eids = eids;
+    B.x = c->ar.alloc<float>(Et);
+    B.d = c->ar.alloc<float>(Et);
+    B.y = c->ar.alloc<float>(Nt);
+    B.dy = c->ar.alloc<float>(Nt);
+    const int max_blocks = c->n_sms * 8;
+    B.st = c->ar.alloc<DevState>(max_blocks);
+    B.obj = c->ar.alloc<double>(count);
+    B.iters = c->ar.alloc<int64_t>(count);
+    B.evals = c->ar.alloc<int64_t>(count);
+    B.passes = c->ar.alloc<int64_t>(count);
+    B.probes = c->ar.alloc<int32_t>(count);
+    B.queue = c->ar.alloc<unsigned int>(1);
+    if (!B.x || !B.d || !B.y || !B.dy || !B.st || !B.obj || !B.iters || !B.evals || !B.passes || !B.probes || !B.queue) {
+        c->err = "allocating the batch work vectors";
+        return bail(MWU_ERR_OOM);
+    }
+    TRY_CUDA(c, cudaMemsetAsync(B.st, 0, sizeof(DevState) * (size_t)max_blocks, s));
+    B.eps = o.eps;
+    B.eta_factor = o.eta_factor;
+    B.outer_tol = o.outer_tol;
+    B.grad_tol = o.grad_tol;
+    B.max_iter = o.max_iter;
+    B.max_probes = o.max_probes;
+    B.max_passes = o.max_passes;
+    B.K = o.K;
+    B.warm_start = o.warm_start;
+    B.step_mode = o.step == MWU_STEP_NEWTON ? 3 : 0;
+    B.max_newton = o.max_newton;
+    B.newton_tol = o.newton_tol;
+    c->batch_nt = o.batch_workers;   // 0: tuned on the first solve
+    TRY_CUDA(c, cudaStreamSynchronize(s));
     *out = c;
     return MWU_OK;
 }
 
-// Instances are solved concurrently: W host workers take the next unsolved
-// instance (largest first) and run its whole solve on the instance's own
-// stream and captured iterations, so the GPU overlaps the small kernels and the
-// host round trips of many instances.  With opt.batch_workers = 0, W is tuned
-// online on the first instances, which count as solved work: W = 4, 8, 16
-// (clipped to the batch) each take a chunk of 2W instances, and the W with the
-// highest edges x iterations per second solves the rest.
+static int batch_blocks_for(mwu_ctx *c, int nt) {
+    return std::max(1, std::min(c->batch_count, c->n_sms * std::min(8, batch_blocks_per_sm(nt))));
+}
+
+// Autotuner: the whole batch solved once with 256, 512 and 1024 threads per
+// block (CUDA events), the fastest kept for the context (and its timings for
+// mwu_batch_tuning).
+static int batch_autotune(mwu_ctx *c) {
+    const int nts[3] = {256, 512, 1024};
+    cudaEvent_t a, b;
+    TRY_CUDA(c, cudaEventCreate(&a));
+    TRY_CUDA(c, cudaEventCreate(&b));
+    int best = 0;
+    for (int i = 0; i < 3; ++i) {
+        cudaError_t e = cudaEventRecord(a, c->stream);
+        if (e == cudaSuccess) e = launch_batch_solve(c->bd, nts[i], batch_blocks_for(c, nts[i]), c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return fail_cuda(c, e, "batch autotune"); }
+        c->tune_ms[i] = ms;
+        if (ms < c->tune_ms[best]) best = i;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c->batch_nt = nts[best];
+    return MWU_OK;
+}
+
 int mwu_solve_batch(mwu_ctx *c, double *objective, int64_t *iters, mwu_result *total) {
-    if (!c || c->batch.empty()) return MWU_ERR_INVALID;
+    if (!c || !c->is_batch) return MWU_ERR_INVALID;
     auto t0 = std::chrono::steady_clock::now();
-    const size_t n = c->batch.size();
-    std::vector<size_t> order(n);
-    for (size_t k = 0; k < n; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return c->batch[a]->n > c->batch[b]->n; });
-    std::vector<mwu_result> res(n);
-    std::vector<int> rcs(n, MWU_OK);
-    auto run_chunk = [&](size_t begin, size_t end, int W) -> double {
-        auto s0 = std::chrono::steady_clock::now();
-        std::atomic<size_t> next{begin};
-        auto worker = [&]() {
-            for (;;) {
-                const size_t i = next.fetch_add(1);
-                if (i >= end) break;
-                const size_t k = order[i];
-                rcs[k] = mwu_solve(c->batch[k], 0.0, 0.0, &res[k]);
-            }
-        };
-        std::vector<std::thread> th;
-        for (int w = 1; w < W; ++w) th.emplace_back(worker);
-        worker();
-        for (auto &t : th) t.join();
-        return std::chrono::duration<double>(std::chrono::steady_clock::now() - s0).count();
-    };
-    auto units = [&](size_t begin, size_t end) {
-        double u = 0.0;
-        for (size_t i = begin; i < end; ++i) u += (double)c->batch[order[i]]->n * (double)res[order[i]].iters;
-        return u;
-    };
-    size_t pos = 0;
-    int best_w = c->opt.batch_workers;
-    if (best_w <= 0) {
-        double best_rate = -1.0;
-        for (int W : {4, 8, 16}) {
-            W = (int)std::min<size_t>((size_t)W, n);
-            const size_t chunk = std::min<size_t>(n - pos, 2 * (size_t)W);
-            if (chunk == 0) break;
-            const double sec = run_chunk(pos, pos + chunk, W);
-            const double rate = units(pos, pos + chunk) / std::max(sec, 1e-9);
-            if (rate > best_rate) { best_rate = rate; best_w = W; }
-            pos += chunk;
-        }
+    int rc;
+    if (c->batch_nt == 0 && (rc = batch_autotune(c)) != MWU_OK) return rc;
+    if (c->batch_graph_nt != c->batch_nt) {
+        if (c->batch_graph) { cudaGraphExecDestroy(c->batch_graph); c->batch_graph = nullptr; }
+        c->batch_blocks = batch_blocks_for(c, c->batch_nt);
+        cudaGraph_t g = nullptr;
+        TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_batch_solve(c->bd, c->batch_nt, c->batch_blocks, c->stream);
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail_cuda(c, e, "capture batch solve"); }
+        if (e2 != cudaSuccess) return fail_cuda(c, e2, "end capture");
+        e = cudaGraphInstantiate(&c->batch_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { c->batch_graph = nullptr; return fail_cuda(c, e, "instantiate batch graph"); }
+        c->batch_graph_nt = c->batch_nt;
     }
-    if (pos < n) run_chunk(pos, n, std::max(1, std::min(best_w, (int)n)));
-    c->batch_workers_used = best_w;
+    TRY_CUDA(c, cudaGraphLaunch(c->batch_graph, c->stream));
+    const int n = c->batch_count;
+    std::vector<double> obj(n);
+    std::vector<int64_t> it(n), ev(n), pa(n);
+    std::vector<int32_t> pr(n);
+    TRY_CUDA(c, cudaMemcpyAsync(obj.data(), c->bd.obj, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaMemcpyAsync(it.data(), c->bd.iters, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaMemcpyAsync(ev.data(), c->bd.evals, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaMemcpyAsync(pa.data(), c->bd.passes, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaMemcpyAsync(pr.data(), c->bd.probes, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
     mwu_result tot{};
-    for (size_t k = 0; k < n; ++k) {
-        if (rcs[k] != MWU_OK)
-            return fail(c, rcs[k], std::string("instance ") + std::to_string(k) + ": " + c->batch[k]->err);
-        const mwu_result &r = res[k];
-        if (objective) objective[k] = r.objective;
-        if (iters) iters[k] = r.iters;
-        tot.objective += r.objective;
-        tot.probes += r.probes;
-        tot.iters += r.iters;
-        tot.evals += r.evals;
-        tot.passes += r.passes;
-        tot.launches += r.launches;
+    bool bad = false;
+    for (int k = 0; k < n; ++k) {
+        if (objective) objective[k] = obj[k];
+        if (iters) iters[k] = it[k];
+        if (!std::isfinite(obj[k])) bad = true;
+        tot.objective += obj[k];
+        tot.probes += pr[k];
+        tot.iters += it[k];
+        tot.evals += ev[k];
+        tot.passes += pa[k];
     }
+    c->batch_last_passes = pa;
+    c->batch_last_probes = pr;
+    tot.launches = 1;
     tot.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (total) *total = tot;
+    return bad ? fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a batch instance") : MWU_OK;
+}
+
+int mwu_batch_tuning(mwu_ctx *c, int32_t *threads, double *ms) {
+    if (!c || !c->is_batch) return MWU_ERR_INVALID;
+    if (threads) *threads = c->batch_nt;
+    if (ms) for (int i = 0; i < 3; ++i) ms[i] = c->tune_ms[i];
+    return MWU_OK;
+}
+
+int mwu_batch_stats(mwu_ctx *c, int64_t *passes, int32_t *probes) {
+    if (!c || !c->is_batch) return MWU_ERR_INVALID;
+    if (c->batch_last_passes.empty()) return fail(c, MWU_ERR_STATE, "no batch solve yet");
+    for (int k = 0; k < c->batch_count; ++k) {
+        if (passes) passes[k] = c->batch_last_passes[k];
+        if (probes) probes[k] = c->batch_last_probes[k];
+    }
     return MWU_OK;
 }

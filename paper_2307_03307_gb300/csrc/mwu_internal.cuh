@@ -241,6 +241,31 @@ template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t 
 // dst[i] = (T) src[i] (device arrays)
 template <class T, class U> cudaError_t launch_convert_in(const U *src, T *dst, int64_t n, cudaStream_t s);
 
+// Packed batch of b-matching instances for the persistent solve (k_batch_solve):
+// instance k owns edges [eoff[k], eoff[k+1]) (int2 (u, v), local vertex ids),
+// vertices [voff[k], voff[k+1]), its vertex -> incident-edge lists at
+// vptr[voff[k] + k .. voff[k+1] + k] (local offsets into eids + 2 eoff[k]).
+struct BatchDesc {
+    int32_t count;
+    const int32_t *order;      // instances in decreasing edge count (the work queue's order)
+    const int64_t *eoff, *voff;
+    const int32_t *edges;
+    const float *bound;        // capacity per vertex, or nullptr (all 1)
+    const int32_t *vptr, *eids;
+    float *x, *d, *y, *dy;     // per edge (x, d) and per vertex (y, dy)
+    DevState *st;              // one per block
+    double *obj;
+    int64_t *iters, *evals, *passes;
+    int32_t *probes;
+    unsigned int *queue;       // next instance to take
+    double eps, eta_factor, outer_tol, grad_tol, newton_tol;
+    int32_t max_iter, max_probes, max_passes, K, warm_start;
+    int32_t step_mode;         // 0 K-candidate search, 3 Newton (Sec. 4.2)
+    int32_t max_newton;
+};
+cudaError_t launch_batch_solve(const BatchDesc &B, int nt, int blocks, cudaStream_t s);
+int batch_blocks_per_sm(int nt);
+
 // Message for mwu_last_error(NULL) from entry points without a context.
 void set_global_error(const char *msg);
 

@@ -2540,6 +2540,349 @@ template <class T> int tiled_blocks_per_sm() {
     return a > 0 ? a : 1;
 }
 
+// ============================================================ batched b-matching
+// One persistent launch solves a batch of independent b-matching LPs
+// (Appendix A.1 with lb = 0: max 1^T x, diag(1/b) M x <= 1, a pure packing LP
+// whose covering side is the objective row (1/M) 1^T x >= 1, Sec. 2.2).  Each
+// block takes the next instance from a device work queue (instances ordered by
+// decreasing size) and runs its whole solve: the bracket and the geometric
+// bisection on M, and per probe Alg. 2's iterations with the K-candidate
+// search (the library's own decision rules, dir_finish / search_decide, on a
+// per-block DevState).  An instance is always solved by one block with a fixed
+// order of every sum, so its result does not depend on the batch, the block or
+// the schedule; only the block size (chosen by the autotuner) sets that order.
+template <int NT>
+__device__ __forceinline__ double bt_sum(double v, double *sm) {
+    return block_sum<double>(v, sm);
+}
+
+// Log-sum-exp of y (packing rows, sign +1): s = max y, S = sum e^{eta (y - s)}.
+template <int NT>
+__device__ void bt_lse(const float *y, int64_t n, float eta, double *sm, double &s_out, double &S_out) {
+    Lse<float> acc{0.0f, 0.0f};
+    for (int64_t j = threadIdx.x; j < n; j += NT) lse_push(acc, y[j], eta, 1);
+    for (int off = 16; off > 0; off >>= 1) {
+        const float os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
+        lse_merge<float, float>(acc, os, oS, eta, 1);
+    }
+    __shared__ double ws[NT / 32], wS[NT / 32];
+    if ((threadIdx.x & 31) == 0) { ws[threadIdx.x >> 5] = acc.s; wS[threadIdx.x >> 5] = acc.S; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Lse<double> t{0.0, 0.0};
+        for (int w = 0; w < NT / 32; ++w) lse_merge<float, double>(t, ws[w], wS[w], (double)eta, 1);
+        sm[0] = t.s;
+        sm[1] = t.S;
+    }
+    __syncthreads();
+    s_out = sm[0];
+    S_out = sm[1];
+    __syncthreads();
+}
+
+// y_w = (1/b_w) sum_{e at w} v_e over the vertex -> incident-edge lists; four
+// independent gathers in flight per thread
+template <int NT>
+__device__ void bt_rows(const int32_t *vp, const int32_t *ei, const float *bnd, const float *v, float *out, int64_t n) {
+    for (int64_t w = threadIdx.x; w < n; w += NT) {
+        const int kb = vp[w], ke = vp[w + 1];
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        int k = kb;
+        for (; k + 3 < ke; k += 4) {
+            const int i0 = ei[k], i1 = ei[k + 1], i2 = ei[k + 2], i3 = ei[k + 3];
+            a0 += v[i0]; a1 += v[i1]; a2 += v[i2]; a3 += v[i3];
+        }
+        for (; k < ke; ++k) a0 += v[ei[k]];
+        const float a = (a0 + a1) + (a2 + a3);
+        out[w] = bnd ? a / bnd[w] : a;
+    }
+}
+
+template <int NT>
+__device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
+    __shared__ double sm[32];
+    __shared__ float s_al[KMAX], s_ca[KMAX];
+    __shared__ float wrec[NT / 32][KMAX][4];
+    __shared__ float wD[NT / 32];
+    __shared__ int s_go;
+    const int64_t e0 = B.eoff[inst], E = B.eoff[inst + 1] - e0;
+    const int64_t v0 = B.voff[inst], n = B.voff[inst + 1] - v0;
+    const int2 *ed = reinterpret_cast<const int2 *>(B.edges) + e0;
+    const float *bnd = B.bound ? B.bound + v0 : nullptr;
+    const int32_t *vp = B.vptr + v0 + inst;
+    const int32_t *ei = B.eids + 2 * e0;
+    float *x = B.x + e0, *d = B.d + e0, *y = B.y + v0, *dy = B.dy + v0;
+    const double eps = B.eps;
+    // bracket (packing, c = 1, a_we = 1/b_w): hi = sum_e max(b_u, b_v), lo = sum_e min(b_u, b_v) / E
+    double hs = 0.0, ls = 0.0;
+    for (int64_t e = threadIdx.x; e < E; e += NT) {
+        const int2 uv = ed[e];
+        const double bu = bnd ? bnd[uv.x] : 1.0, bv = bnd ? bnd[uv.y] : 1.0;
+        hs += fmax(bu, bv);
+        ls += fmin(bu, bv);
+    }
+    double hi = bt_sum<NT>(hs, sm), lo = bt_sum<NT>(ls, sm) / (double)E;
+    double best = lo;
+    int probes = 0;
+    int64_t iters = 0, evals = 0, passes = 0;
+    const double eta = B.eta_factor * log((double)(n + 1)) / eps;
+    const float eta_f = (float)eta;
+    const float thr = (float)(1.0 - B.grad_tol);
+    while (hi > (1.0 + B.outer_tol) * lo && probes < B.max_probes) {
+        const double M = sqrt(lo * hi);
+        const double rho = (1.0 + B.outer_tol) * M / hi;   // the certificate closes the bracket (R12)
+        const float cd_f = (float)(1.0 / eta), invM = (float)(1.0 / M);
+        // a0: x_e = eps / (E max(1/b_u, 1/b_v)), y = Px, z = 1^T x / M
+        double xs = 0.0;
+        for (int64_t e = threadIdx.x; e < E; e += NT) {
+            const int2 uv = ed[e];
+            const double a = bnd ? 1.0 / (double)bnd[uv.x] : 1.0, b = bnd ? 1.0 / (double)bnd[uv.y] : 1.0;
+            const float xe = (float)(eps / ((double)E * fmax(a, b)));
+            x[e] = xe;
+            xs += (double)xe;
+        }
+        double z = bt_sum<NT>(xs, sm) / M;
+        __syncthreads();
+        bt_rows<NT>(vp, ei, bnd, x, y, n);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st->eta = eta; st->eps = eps; st->c_d = 1.0 / eta; st->K = B.K; st->max_passes = B.max_passes;
+            st->warm_start = B.warm_start; st->step_mode = B.step_mode; st->max_newton = B.max_newton;
+            st->newton_tol = B.newton_tol; st->alpha_prev = 0.0; st->scale[0] = 1.0;
+            st->scale[1] = 1.0 / M; st->status = ST_RUNNING; st->reason = RS_NONE; st->iter = 0;
+            st->evals = 0; st->total_passes = 0;
+        }
+        __syncthreads();
+        int status = ST_RUNNING;
+        int it = 0;
+        for (;;) {
+            double sp, Sp;
+            bt_lse<NT>(y, n, eta_f, sm, sp, Sp);
+            // stopping tests before each iteration (Alg. 2, R8, R12), zmin = z (one exact row)
+            const double ymax = sp;
+            if (rho > 0.0 && z > 0.0 && ymax <= rho * z) { status = ST_FEASIBLE; break; }
+            if (z >= 1.0 || ymax > 1.0 + eps) { status = ymax <= (1.0 + eps) * z ? ST_FEASIBLE : ST_INFEASIBLE; break; }
+            if (it >= B.max_iter) { status = ST_MAX_ITER; break; }
+            // a4, a5: g_e = (w_u / b_u + w_v / b_v) / S_p, h_e = 1/M; d_e = c_d max(0, 1 - g/h) x_e
+            const float fp = (float)(1.0 / Sp), s_f = (float)sp;
+            double np = 0.0, ds = 0.0;
+            // four edges per thread and round: their endpoint and x loads, then
+            // the gathers of y and b, then the arithmetic
+            for (int64_t e0 = threadIdx.x; e0 < E; e0 += 4 * NT) {
+                int2 uv[4];
+                float xe[4], yu[4], yv[4], bu[4], bv[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int64_t e = e0 + r * NT;
+                    uv[r] = e < E ? ed[e] : make_int2(0, 0);
+                    xe[r] = e < E ? x[e] : 0.0f;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    yu[r] = y[uv[r].x];
+                    yv[r] = y[uv[r].y];
+                    bu[r] = bnd ? bnd[uv[r].x] : 1.0f;
+                    bv[r] = bnd ? bnd[uv[r].y] : 1.0f;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int64_t e = e0 + r * NT;
+                    if (e < E) {
+                        float wu = t_exp(eta_f * (yu[r] - s_f)), wv = t_exp(eta_f * (yv[r] - s_f));
+                        if (bnd) { wu /= bu[r]; wv /= bv[r]; }
+                        const float g = (wu + wv) * fp, h = invM;
+                        const float de = (g < thr * h) ? cd_f * (1.0f - g / h) * xe[r] : 0.0f;
+                        d[e] = de;
+                        np += de > 0.0f;
+                        ds += (double)de;
+                    }
+                }
+            }
+            np = bt_sum<NT>(np, sm);
+            ds = bt_sum<NT>(ds, sm);
+            __syncthreads();
+            bt_rows<NT>(vp, ei, bnd, d, dy, n);   // a6: dy = P d
+            if (threadIdx.x == 0) {
+                st->phase = PH_DONE;
+                dir_finish(st, np, 0.0, ds);   // d = 0 -> INFEASIBLE, else the search starts
+                st->dense_v[1] = z;
+                s_go = st->status == ST_RUNNING ? 1 : 0;
+            }
+            __syncthreads();
+            if (!s_go) { status = ST_INFEASIBLE; break; }
+            const double dz = st->dense_dv[1];
+            // a7: the step search over the packing rows (Phi_k = alpha_k dz, Phi' = dz
+            // exactly): K-candidate passes (exponential phase, refinement), Newton
+            // and backoff passes (one candidate with Psi'), the covering step
+            for (int guard = 0; guard < 128; ++guard) {
+                const int phase = st->phase;
+                if (phase == PH_COVER) {   // the smallest step that covers the objective row
+                    if (threadIdx.x == 0) {
+                        const double ac = z >= 1.0 ? 0.0 : (dz > 0.0 ? (1.0 - z) / dz : (double)INFINITY);
+                        st->passes += 1;
+                        st->total_passes += 1;
+                        search_finish(st, fmax(1.0, fmin(st->alpha[0], ac)));
+                    }
+                    __syncthreads();
+                    break;
+                }
+                const bool nwt = phase == PH_NEWTON || phase == PH_BACKOFF;
+                const int K = nwt ? 1 : st->kpass;
+                if (threadIdx.x < KMAX) {
+                    const double a = threadIdx.x < K ? st->alpha[threadIdx.x] : 0.0;
+                    s_al[threadIdx.x] = (float)a;
+                    s_ca[threadIdx.x] = (float)(a * eta);
+                }
+                __syncthreads();
+                float ca[KMAX], al[KMAX];
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k) { ca[k] = s_ca[k]; al[k] = s_al[k]; }
+                const float camax = sched_camax(ca, K);
+                CandAcc<float> acc;
+                cand_init(acc, 1);
+                if (nwt) {
+                    for (int64_t j = threadIdx.x; j < n; j += NT)
+                        cand_push_m<float, 3, 1, 1>(acc, ca, al, 0.0f, 1, y[j], dy[j], eta_f, s_f, t_inf<float>(), camax);
+                } else {
+                    for (int64_t j = threadIdx.x; j < n; j += NT)
+                        cand_push_m<float, 2, 1, 0>(acc, ca, al, 0.0f, K, y[j], dy[j], eta_f, s_f, t_inf<float>(), camax);
+                }
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k) {
+                    if (k < K) {
+                        float mx = acc.mx[k], R = acc.R[k], Tt = acc.Tt[k], zm = acc.zm[k], D = k == 0 ? acc.D : 0.0f;
+                        for (int off = 16; off > 0; off >>= 1) {
+                            const float omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off),
+                                        oz = shfl_x(zm, off), oD = shfl_x(D, off);
+                            cand_merge1d<float, float>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, 1);
+                        }
+                        if ((threadIdx.x & 31) == 0) {
+                            float *o = wrec[threadIdx.x >> 5][k];
+                            o[0] = mx; o[1] = R; o[2] = Tt; o[3] = zm;
+                            if (k == 0) wD[threadIdx.x >> 5] = D;
+                        }
+                    }
+                }
+                __syncthreads();
+                __shared__ double s_psi[KMAX], s_dpsi;
+                if (threadIdx.x < K) {
+                    const int k = threadIdx.x;
+                    double mx = 0.0, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
+                    for (int w = 0; w < NT / 32; ++w)
+                        cand_merge1d<float, double>(mx, R, Tt, zm, D, wrec[w][k][0], wrec[w][k][1], wrec[w][k][2],
+                                                    wrec[w][k][3], k == 0 ? (double)wD[w] : 0.0, 1);
+                    // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p) (Sec. 4.1);
+                    // the transcendentals in FP32 (as the FP32 form's passes take them), the
+                    // combination in FP64
+                    const double lS = (double)logf((float)Sp);
+                    const double lq = mx + (double)logf((float)Tt) - lS;
+                    s_psi[k] = (lq < 0.0) ? (double)log1pf(expf((float)lq)) / eta : (mx + (double)logf((float)R) - lS) / eta;
+                    if (k == 0) s_dpsi = R > 0.0 ? D / R : 0.0;   // Psi' (Sec. 4.2): both sums share the shift
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int ok[KMAX];
+                    double zmk[KMAX];
+                    for (int k = 0; k < K; ++k) {
+                        const double phi = st->alpha[k] * dz;
+                        st->psi[k] = s_psi[k];
+                        st->phi[k] = phi;
+                        ok[k] = phi >= s_psi[k];
+                        zmk[k] = z + st->alpha[k] * dz;
+                    }
+                    if (phase == PH_NEWTON) {
+                        st->dpsi = s_dpsi;
+                        st->dphi = dz;
+                        newton_decide(st, s_psi[0], st->phi[0], s_dpsi, dz, zmk[0]);
+                    } else if (phase == PH_BACKOFF) {
+                        backoff_decide(st, ok[0]);
+                    } else {
+                        search_decide(st, ok, zmk);
+                    }
+                    s_go = (st->status == ST_RUNNING && st->phase != PH_DONE) ? 1 : 0;
+                }
+                __syncthreads();
+                if (!s_go) break;
+            }
+            if (st->status != ST_RUNNING || !(st->alpha_acc >= 1.0)) { status = ST_INFEASIBLE; break; }
+            // a8: x += alpha d, y += alpha dy, z += alpha dz
+            const double alpha = st->alpha_acc;
+            const float af = (float)alpha;
+            for (int64_t e = threadIdx.x; e < E; e += NT) x[e] = fmaf(af, d[e], x[e]);
+            for (int64_t w = threadIdx.x; w < n; w += NT) y[w] = fmaf(af, dy[w], y[w]);
+            z += alpha * dz;
+            ++it;
+            __syncthreads();
+            if (threadIdx.x == 0) { st->alpha_prev = alpha; st->iter = it; }
+        }
+        __syncthreads();
+        evals += st->evals;
+        passes += st->total_passes;
+        iters += it;
+        ++probes;
+        // certificate of the probe's x: 1^T x / max(Px), with y recomputed from x
+        double sx = 0.0;
+        for (int64_t e = threadIdx.x; e < E; e += NT) sx += (double)x[e];
+        sx = bt_sum<NT>(sx, sm);
+        bt_rows<NT>(vp, ei, bnd, x, y, n);
+        __syncthreads();
+        double ym = 0.0;
+        for (int64_t w = threadIdx.x; w < n; w += NT) ym = fmax(ym, (double)y[w]);
+        ym = block_max<double>(ym, sm);
+        const double cert = ym > 0.0 ? sx / ym : 0.0;
+        best = fmax(best, cert);
+        lo = fmax(lo, cert);
+        if (status == ST_FEASIBLE) lo = fmax(lo, M);
+        else hi = fmin(hi, M);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        B.obj[inst] = best;
+        B.iters[inst] = iters;
+        B.probes[inst] = probes;
+        B.evals[inst] = evals;
+        B.passes[inst] = passes;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batch_solve(BatchDesc B) {
+    __shared__ int s_q;
+    DevState *st = B.st + blockIdx.x;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = (int)atomicAdd(B.queue, 1u);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();
+        if (q >= B.count) return;
+        bt_solve<NT>(B, B.order[q], st);
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_batch_solve(const BatchDesc &B, int nt, int blocks, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(B.queue, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    switch (nt) {
+    case 256: k_batch_solve<256><<<blocks, 256, 0, s>>>(B); break;
+    case 512: k_batch_solve<512><<<blocks, 512, 0, s>>>(B); break;
+    case 1024: k_batch_solve<1024><<<blocks, 1024, 0, s>>>(B); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm(int nt) {
+    int a = 0;
+    switch (nt) {
+    case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<256>, 256, 0); break;
+    case 512: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<512>, 512, 0); break;
+    case 1024: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<1024>, 1024, 0); break;
+    default: break;
+    }
+    return a > 0 ? a : 1;
+}
+
 #define MWU_INSTANTIATE(T)                                                                                     \
     template cudaError_t launch_x_init<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_x_set<T>(const Problem<T> &, const void *, int, cudaStream_t);                 \

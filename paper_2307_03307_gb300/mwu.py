@@ -119,6 +119,8 @@ def load(path: str = LIB_PATH):
         "mwu_create_batch": (C.c_int, [I32, P(mwu_matrix), P(mwu_options), P(V)]),
         "mwu_diag_one_minus_exp_neg": (C.c_int, [V, V, I64, V]),
         "mwu_solve_batch": (C.c_int, [V, P(D), P(I64), P(mwu_result)]),
+        "mwu_batch_tuning": (C.c_int, [V, P(I32), P(D)]),
+        "mwu_batch_stats": (C.c_int, [V, P(I64), P(I32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -134,7 +136,8 @@ def exported_symbols():
             "mwu_set_x", "mwu_set_state", "mwu_set_direction", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_eval_newton", "mwu_search",
             "mwu_solve",
             "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_spmv_tiles", "mwu_potential",
-            "mwu_candidates_static", "mwu_create_batch", "mwu_solve_batch", "mwu_diag_one_minus_exp_neg"]
+            "mwu_candidates_static", "mwu_create_batch", "mwu_solve_batch", "mwu_batch_tuning", "mwu_batch_stats",
+            "mwu_diag_one_minus_exp_neg"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -369,3 +372,19 @@ def mwu_solve_batch(ctx, count):
     r = mwu_result()
     _check(ctx, load().mwu_solve_batch(ctx, obj, it, C.byref(r)))
     return list(obj), list(it), _as_dict(r)
+
+
+def mwu_batch_tuning(ctx):
+    """(threads per block in use, [ms with 256, 512, 1024]) of the batch autotuner."""
+    nt = C.c_int32()
+    ms = (C.c_double * 3)()
+    _check(ctx, load().mwu_batch_tuning(ctx, C.byref(nt), ms))
+    return nt.value, list(ms)
+
+
+def mwu_batch_stats(ctx, count):
+    """Per-instance candidate passes and probes of the last batch solve."""
+    pa = (C.c_int64 * count)()
+    pr = (C.c_int32 * count)()
+    _check(ctx, load().mwu_batch_stats(ctx, pa, pr))
+    return list(pa), list(pr)

@@ -1,7 +1,9 @@
-"""Batched b-matching (many independent packing LPs, Appendix A.1 with lb = 0):
-the concurrent batch solve gives every instance the same certified objective as
-solving it alone, and each is within (1+eps)^2 of the exact b-matching LP
-optimum (max flow) and within 1+eps of the FP64 oracle's solve."""
+"""Batched b-matching (many independent packing LPs, Appendix A.1 with lb = 0)
+in one persistent launch: every instance's certified objective is the same
+whether it is solved in the batch or alone (one block per instance, a fixed
+order of every sum), lies within (1+eps)^2 of the exact b-matching LP optimum
+(max flow), and within 1+eps of the FP64 oracle's solve; the autotuner keeps
+the fastest block size it timed."""
 import numpy as np
 import pytest
 import torch
@@ -24,31 +26,64 @@ def M():
     return mwu
 
 
-@pytest.mark.parametrize("workers", [0, 3])
-def test_batch_equals_single_and_exact(M, workers):
+def _mats(insts, device="cuda"):
     from paper_2307_03307_gb300 import lpspec
+    return [lpspec.from_workload(wl, device=device)[1] for wl in insts]
+
+
+@pytest.mark.parametrize("nt,step", [(256, "kary"), (512, "newton"), (1024, "kary"), (1024, "newton")])
+def test_batch_equals_alone_and_exact(M, nt, step):
     insts = W.bmatching_batch(count=10, seed=4, lo=1e3, hi=1.2e4)
-    mats = []
-    for wl in insts:
-        kind, P, C, obj = lpspec.from_workload(wl, device="cuda")
-        mats.append(P)
-    ctx = M.mwu_create_batch(mats, batch_workers=workers)
+    st = M.STEP_NEWTON if step == "newton" else M.STEP_KARY
+    ctx = M.mwu_create_batch(_mats(insts), batch_workers=nt, step=st)
     try:
-        obj_b, it_b, tot = M.mwu_solve_batch(ctx, len(mats))
+        obj_b, it_b, tot = M.mwu_solve_batch(ctx, len(insts))
+        obj_2, it_2, _ = M.mwu_solve_batch(ctx, len(insts))     # a second solve of the same context
     finally:
         M.mwu_destroy(ctx)
-    assert tot["iters"] == sum(it_b)
+    assert tot["iters"] == sum(it_b) and tot["launches"] == 1
+    assert obj_b == obj_2 and it_b == it_2
     for k, wl in enumerate(insts):
-        kind, P, C, obj = lpspec.from_workload(wl, device="cuda")
-        c1 = M.mwu_create(kind, P, C, obj, eps=wl.eps)
+        c1 = M.mwu_create_batch(_mats([wl]), batch_workers=nt, step=st)
         try:
-            r1 = M.mwu_solve(c1)
+            o1, i1, _ = M.mwu_solve_batch(c1, 1)
         finally:
             M.mwu_destroy(c1)
-        assert obj_b[k] == r1["objective"] and it_b[k] == r1["iters"], k   # concurrency changes nothing
+        assert obj_b[k] == o1[0] and it_b[k] == i1[0], k   # the batch changes nothing
         g = wl.graph
         opt = exact.b_matching_size(g.n_left, g.n, g.u.numpy(), g.v.numpy(), wl.bounds.numpy())
         assert opt / (1 + wl.eps) ** 2 <= obj_b[k] <= opt * (1 + 1e-6), (k, obj_b[k], opt)
         if k < 3:
-            ores = H.oracle_solve(wl)
+            ores = H.oracle_solve(wl, step=step)
             assert 1 / (1 + wl.eps) <= obj_b[k] / ores.objective <= 1 + wl.eps
+
+
+def test_batch_from_host_arrays_and_autotuner(M):
+    insts = W.bmatching_batch(count=12, seed=9, lo=1e3, hi=3e4)
+    ctx = M.mwu_create_batch(_mats(insts, device="cpu"))
+    try:
+        nt0, _ = M.mwu_batch_tuning(ctx)
+        assert nt0 == 0
+        obj, it, tot = M.mwu_solve_batch(ctx, len(insts))
+        nt, ms = M.mwu_batch_tuning(ctx)
+        assert nt in (256, 512, 1024) and all(t > 0 for t in ms)
+        assert ms[(256, 512, 1024).index(nt)] == min(ms)       # the fastest configuration it timed
+        passes, probes = M.mwu_batch_stats(ctx, len(insts))
+        assert sum(passes) == tot["passes"] and sum(probes) == tot["probes"]
+    finally:
+        M.mwu_destroy(ctx)
+    ctx = M.mwu_create_batch(_mats(insts), batch_workers=nt)
+    try:
+        obj2, it2, _ = M.mwu_solve_batch(ctx, len(insts))
+    finally:
+        M.mwu_destroy(ctx)
+    assert obj == obj2 and it == it2                         # host or device inputs, same solve
+
+
+def test_batch_rejects_other_matrices(M):
+    from paper_2307_03307_gb300 import lpspec
+    wl = W.vcover(8, seed=3)
+    kind, P, C, obj = lpspec.from_workload(wl, device="cuda")
+    with pytest.raises(M.MWUError) as e:
+        M.mwu_create_batch([C])
+    assert e.value.code == M.ERR_INVALID
