@@ -21,6 +21,9 @@
  *     the context creates).  A context is not thread safe.
  *   - Indices are int32; sizes int64.  Vectors of the FP32 form are float32,
  *     of the FP64 form float64.
+ *   - MWU_FAULT_ALLOC_AT=k in the environment makes the k-th device allocation
+ *     of each context fail (a host-side fault injection): the call returns
+ *     MWU_ERR_OOM and releases everything it had allocated.
  */
 #ifndef MWU_H_
 #define MWU_H_
@@ -42,7 +45,9 @@ typedef enum {
     MWU_ERR_CUDA = -2,      /* a CUDA call failed                                               */
     MWU_ERR_OOM = -3,       /* device allocation failed                                         */
     MWU_ERR_NUMERIC = -4,   /* NaN/Inf met in a reduction                                       */
-    MWU_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                                    */
+    MWU_ERR_TIMEOUT = -5,   /* a bounded loop gave up: the step search ran more turns than
+                               max_passes + 4 (MWU_SEARCH_GUARD=n in the environment sets
+                               that bound, a test hook); the context stays usable          */
     MWU_ERR_STATE = -6      /* call out of order (e.g. candidates before a direction)           */
 } mwu_status;
 
@@ -265,7 +270,9 @@ const char *mwu_last_error(const mwu_ctx *ctx);
 int mwu_set_target(mwu_ctx *ctx, double target);
 
 /* Replace x (n entries, host or device, float32 or float64 per x_is_fp64) and
- * recompute y = Px, z = Cx and their reductions.  Keeps eta and the target. */
+ * recompute y = Px, z = Cx and their reductions.  Keeps eta and the target.
+ * MWU_ERR_NUMERIC when the reductions are not finite (an x so large that Px
+ * or Cx overflows the form's precision). */
 int mwu_set_x(mwu_ctx *ctx, const void *x, int32_t x_is_fp64);
 
 /* Stage hooks that load the constraint vectors themselves, so that each kernel
@@ -282,7 +289,8 @@ int mwu_set_x(mwu_ctx *ctx, const void *x, int32_t x_is_fp64);
  * followed by Alg. 2's stopping test; mwu_direction then computes g, h, d from
  * these y, z and the current x.  When dy or dz is given, mwu_eval_candidates,
  * mwu_eval_newton and mwu_search use them as the last direction's products
- * (Sec. 4.1 / 4.2).  Returns MWU_ERR_NUMERIC when a reduction is not finite.
+ * (Sec. 4.1 / 4.2).  MWU_ERR_INVALID when a loaded value is negative, NaN or
+ * infinite; MWU_ERR_NUMERIC when a reduction is not finite.
  *
  * mwu_set_direction loads d (n entries, same conventions) and computes
  * dy = Pd, dz = Cd with the forward products of the iteration (a6 of Alg. 2:
@@ -362,6 +370,14 @@ int mwu_spmv_tiles(mwu_ctx *ctx, int32_t *tiles_p, int32_t *tiles_c);
  * left at x with its reductions over the active rows. */
 int mwu_potential(mwu_ctx *ctx, const float *x, double *pot,
                   float *grad_x, float *grad_obj, float *grad_vals);
+
+/* Whether objective (n floats, NULL = not checked) and vals (the stored
+ * values of the explicit CSR sides, packing side first, NULL = not checked)
+ * equal, bit for bit, the copies the context made at mwu_create (a side or
+ * objective given as NULL there counts as all ones).  *same = 1 or 0.  The
+ * autograd wrapper refuses tensors that differ: the gradients refer to the
+ * context's copies. */
+int mwu_check_values(mwu_ctx *ctx, const float *objective, const float *vals, int32_t *same);
 
 /* ------------------------------------------- allocation-free evaluation */
 /* For callers that must not allocate device memory: code that runs inside a

@@ -1,6 +1,6 @@
 """Build libmwu.so in-tree for sm_103a with nvcc (translation units compiled in parallel).
 
-    python -m paper_2307_03307_gb300._build [--force] [--checked]
+    python -m paper_2307_03307_gb300._build [--force]
 
 The library lands in ``paper_2307_03307_gb300/_lib/libmwu.so``.  Object files
 go to ``paper_2307_03307_gb300/_lib/obj``.  A rebuild happens only when a
@@ -55,12 +55,12 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, checked: bool = False, verbose: bool = False) -> str:
-    if not force and not checked and up_to_date():
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and up_to_date():
         return LIB
     nvcc = _nvcc()
     os.makedirs(OBJDIR, exist_ok=True)
-    extra = ["-DMWU_CHECKED=1"] if checked else []
+    extra = []
 
     def compile_one(src):
         obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
@@ -84,4 +84,4 @@ def build(force: bool = False, checked: bool = False, verbose: bool = False) -> 
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, checked="--checked" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True))

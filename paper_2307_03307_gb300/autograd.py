@@ -10,9 +10,12 @@ call returns the value and the three gradients:
   (+w_j x_i on the packing side, -w_j x_i on the covering side)
 
 The context fixes P, C, eta (``mwu_set_target``) and reads the objective and
-the CSR values it was created from; the tensors passed here for them only carry
-autograd's bookkeeping, so they must be the ones the context was created with.
-Every step runs in the library's kernels; there is no CPU path.
+the CSR values it was created from.  The tensors passed here for them must
+hold the same values: ``potential`` checks them against the context's copies
+on the device (``mwu_check_values``) and raises ValueError when they differ
+(for instance after an in-place update), since the gradients refer to the
+context's copies.  Every step runs in the library's kernels; there is no CPU
+path.
 """
 from __future__ import annotations
 
@@ -51,4 +54,7 @@ def potential(handle, x, objective=None, values=None):
     ``objective`` (the c the context was created with) and ``values`` (the explicit
     CSR values it was created with, packing side first)."""
     n_values = int(values.numel()) if values is not None else 0
+    if (objective is not None or values is not None) and not M.mwu_check_values(handle, objective, values):
+        raise ValueError("objective / values differ from the arrays the context was created with; create a new "
+                         "context for new values")
     return _Potential.apply(x, objective, values, handle, n_values)

@@ -57,6 +57,8 @@ struct mwu_ctx {
     double target = 1.0;
     bool have_direction = false;
     bool trace = false;          // MWU_TRACE=1: one line per probe on stderr
+    int guard_limit = 0;         // MWU_SEARCH_GUARD=n: turns of the device-side search loop before it
+                                 // gives up with MWU_ERR_TIMEOUT (default max_passes + 4; a test hook)
     // batch front end: the persistent solve of packed b-matching instances
     bool is_batch = false;
     BatchDesc bd{};
@@ -485,6 +487,7 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     c->kind = kind;
     c->fp64 = o.precision == MWU_PREC_FP64;
     if (const char *tr = std::getenv("MWU_TRACE")) c->trace = tr[0] == '1';
+    if (const char *g = std::getenv("MWU_SEARCH_GUARD")) c->guard_limit = std::atoi(g);
     if (c->fp64 || o.step == MWU_STEP_BINARY) o.K = 1;
     if (o.max_passes <= 0) o.max_passes = (c->fp64 || o.K == 1) ? 64 : (o.step == MWU_STEP_NEWTON ? 16 : 6);
     if (o.max_newton == 0) o.max_newton = 8;
@@ -498,7 +501,7 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     c->opt = o;
     auto bail = [&](int rc) {
         g_create_error = c->err;
-        delete c;   // destructor frees the arena
+        mwu_destroy(c);   // frees the arena, the stream and the pinned state
         return rc;
     };
     if (o.stream) {
@@ -687,6 +690,7 @@ static int probe_status(const DevState &h) {
     case ST_INFEASIBLE: return MWU_INFEASIBLE;
     case ST_MAX_ITER: return MWU_MAX_ITER;
     case ST_RUNNING: return MWU_RUNNING;
+    case ST_TIMEOUT: return MWU_ERR_TIMEOUT;
     default: return MWU_ERR_NUMERIC;
     }
 }
@@ -710,6 +714,7 @@ int mwu_set_target(mwu_ctx *c, double target) {
     h.max_iter = o.max_iter;
     h.K = o.K;
     h.max_passes = o.max_passes;
+    h.guard_limit = c->guard_limit > 0 ? c->guard_limit : o.max_passes + 4;
     h.warm_start = o.warm_start;
     h.step_mode = o.step == MWU_STEP_STANDARD ? 2 : (o.step == MWU_STEP_BINARY ? 1 : (o.step == MWU_STEP_NEWTON ? 3 : 0));
     h.max_newton = o.max_newton;
@@ -752,7 +757,8 @@ int mwu_set_x(mwu_ctx *c, const void *x, int32_t x_is_fp64) {
     if (e != cudaSuccess) return fail_cuda(c, e, "launch_x_set");
     c->have_direction = false;
     if ((rc = pull_state(c)) != MWU_OK) return rc;
-    return MWU_OK;
+    return probe_status(*c->st_host) == MWU_ERR_NUMERIC ? fail(c, MWU_ERR_NUMERIC, "NaN/Inf in the reductions of Px, Cx")
+                                                         : MWU_OK;
 }
 
 // a6: dv = A d for both sides.  The covering side's dz is already written by
@@ -786,8 +792,17 @@ static int load_vec(mwu_ctx *c, T *dst, const void *src, int64_t n, int32_t src_
     }
     cudaError_t e = src_fp64 ? launch_convert_in<T>((const double *)from, dst, n, c->stream)
                              : launch_convert_in<T>((const float *)from, dst, n, c->stream);
-    if (tmp) { cudaStreamSynchronize(c->stream); cudaFree(tmp); }
+    // every constraint value and direction product of the LP is finite and >= 0
+    int *bad = nullptr, h = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_check_nonneg<T>(dst, n, bad, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (bad) cudaFree(bad);
     if (e != cudaSuccess) return fail_cuda(c, e, "convert vector in");
+    if (h) return fail(c, MWU_ERR_INVALID, "loaded vector holds a negative, NaN or infinite value");
     return MWU_OK;
 }
 
@@ -1062,7 +1077,10 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             c->launches += 3;
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             int guard = 0;
-            while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE && guard++ < 256) {
+            const int limit = c->guard_limit > 0 ? c->guard_limit : c->opt.max_passes + 4;
+            while (c->st_host->status == ST_RUNNING && c->st_host->phase != PH_DONE) {
+                if (guard++ >= limit)
+                    return fail(c, MWU_ERR_TIMEOUT, "the step search exceeded its bound on candidate passes");
                 const bool cover = c->st_host->phase == PH_COVER;
                 TRY_CUDA(c, with_prob(c, [&](auto &p) {
                     return cover ? launch_cand_newton(p, c->stream) : launch_cand(p, 0, c->stream);
@@ -1106,6 +1124,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
     fill_stats(c, stats);
     int st = probe_status(*c->st_host);
     if (st == MWU_ERR_NUMERIC) return fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a reduction");
+    if (st == MWU_ERR_TIMEOUT) return fail(c, MWU_ERR_TIMEOUT, "the device-side step search exceeded its bound on turns");
     return st;
 }
 
@@ -1139,6 +1158,7 @@ int mwu_direction(mwu_ctx *c, int64_t *n_positive) {
     c->have_direction = true;
     int st = probe_status(*c->st_host);
     if (st == MWU_ERR_NUMERIC) return fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a reduction");
+    if (st == MWU_ERR_TIMEOUT) return fail(c, MWU_ERR_TIMEOUT, "the device-side step search exceeded its bound on turns");
     return st == MWU_RUNNING ? MWU_OK : st;
 }
 
@@ -1528,6 +1548,57 @@ static int potential_all_rows(mwu_ctx *c, const float *x, double *pot, float *gr
     TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_potential_grads(p, x, grad_x, grad_obj, gp, gc, c->stream); }));
     TRY_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_direction = false;
+    return MWU_OK;
+}
+
+// ------------------------------------------------------------ value check
+int mwu_check_values(mwu_ctx *c, const float *objective, const float *vals, int32_t *same) {
+    if (!c || !same || c->is_batch) return MWU_ERR_INVALID;
+    *same = 1;
+    int *flag = nullptr;
+    TRY_CUDA(c, cudaMalloc(&flag, sizeof(int)));
+    std::vector<void *> staged;
+    auto release = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void *p : staged) cudaFree(p);
+        cudaFree(flag);
+    };
+    auto device_view = [&](const float *src, int64_t n, const float **out) -> cudaError_t {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeDevice) {
+            *out = src;
+            return cudaSuccess;
+        }
+        cudaGetLastError();
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, 4 * (size_t)std::max<int64_t>(n, 1));
+        if (e != cudaSuccess) return e;
+        staged.push_back(p);
+        *out = (const float *)p;
+        return cudaMemcpyAsync(p, src, 4 * (size_t)n, cudaMemcpyDefault, c->stream);
+    };
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess && objective && (c->kind == MWU_PACKING || c->kind == MWU_COVERING)) {
+        const float *d = nullptr;
+        e = device_view(objective, c->n, &d);
+        if (e == cudaSuccess) e = launch_same_f32(c->objective, d, c->n, flag, c->stream);
+    }
+    if (e == cudaSuccess && vals) {
+        int64_t off = 0;
+        for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+            const RowView &rv = c->fp64 ? c->pd.side[s].rv : c->pf.side[s].rv;
+            if (rv.kind != RK_CSR) continue;
+            const float *d = nullptr;
+            e = device_view(vals + off, rv.nnz, &d);
+            if (e == cudaSuccess) e = launch_same_f32(rv.val, d, rv.nnz, flag, c->stream);
+            off += rv.nnz;
+        }
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    release();
+    if (e != cudaSuccess) return fail_cuda(c, e, "mwu_check_values");
+    *same = h ? 0 : 1;
     return MWU_OK;
 }
 

@@ -123,7 +123,8 @@ struct Side {
 };
 
 // Probe status values stored on the device.
-enum : int32_t { ST_FEASIBLE = 0, ST_INFEASIBLE = 1, ST_MAX_ITER = 2, ST_RUNNING = 3, ST_NUMERIC = -4 };
+enum : int32_t { ST_FEASIBLE = 0, ST_INFEASIBLE = 1, ST_MAX_ITER = 2, ST_RUNNING = 3, ST_NUMERIC = -4,
+                 ST_TIMEOUT = -5 };   // a bounded device-side loop gave up
 enum : int32_t { RS_NONE = 0, RS_COVERED = 1, RS_PACKING = 2, RS_DZERO = 3, RS_ALPHA = 4, RS_MAXITER = 5,
                  RS_RATIO = 6 };
 
@@ -159,6 +160,7 @@ struct DevState {
     double bo_cur;              // backoff: last value alpha (1 - eps)^p handed out
     double dpsi, dphi;          // Psi'(alpha_0), Phi'(alpha_0) of the last Newton pass
     int32_t loop_guard;         // passes run by the device-side search loop of this iteration
+    int32_t guard_limit;        // turns after which that loop gives up (ST_TIMEOUT); max_passes + 4
     long long loop_launches;    // kernels run inside the device-side search loops (all iterations)
     double lb, ub;
     double alpha[KMAX];
@@ -238,6 +240,10 @@ template <class T> cudaError_t launch_search_begin(const Problem<T> &p, cudaStre
 template <class T> cudaError_t launch_potential_grads(const Problem<T> &p, const float *x, float *gx, float *gobj,
                                                       float *gvals_p, float *gvals_c, cudaStream_t s);
 template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t n, int fp64, cudaStream_t s);
+// *bad |= 1 if some v[i] is negative, NaN or infinite
+template <class T> cudaError_t launch_check_nonneg(const T *v, int64_t n, int *bad, cudaStream_t s);
+// *differ |= 1 if a (nullptr = ones) and b (device arrays of n floats) differ bitwise
+cudaError_t launch_same_f32(const float *a, const float *b, int64_t n, int *differ, cudaStream_t s);
 // dst[i] = (T) src[i] (device arrays)
 template <class T, class U> cudaError_t launch_convert_in(const U *src, T *dst, int64_t n, cudaStream_t s);
 

@@ -1420,9 +1420,8 @@ __device__ void search_decide(DevState *st, const int *ok, const double *zmin_k)
 // ever fail.
 __device__ void loop_turn_end(DevState *st, cudaGraphConditionalHandle cond) {
     unsigned v = search_continues(st);
-    if (v && ++st->loop_guard > st->max_passes + 4) {
-        st->status = ST_NUMERIC;
-        st->numeric_bad = 3;
+    if (v && ++st->loop_guard > st->guard_limit) {
+        st->status = ST_TIMEOUT;   // the decide rules end every search sooner: a bounded give-up
         v = 0u;
     }
     cudaGraphSetConditional(cond, v);
@@ -2495,6 +2494,35 @@ template <class T> cudaError_t launch_copy_vec(const T *src, void *dst, int64_t 
     int g = grid_for(n, 4096);
     if (fp64) k_convert<T, double><<<g, BLOCK, 0, s>>>(src, (double *)dst, n);
     else k_convert<T, float><<<g, BLOCK, 0, s>>>(src, (float *)dst, n);
+    return cudaGetLastError();
+}
+
+template <class T>
+__global__ void k_nonneg_finite(const T *v, int64_t n, int *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T a = v[i];
+        if (!(a >= T(0)) || !isfinite(a)) atomicOr(bad, 1);
+    }
+}
+
+template <class T> cudaError_t launch_check_nonneg(const T *v, int64_t n, int *bad, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_nonneg_finite<T><<<grid_for(n, 4096), BLOCK, 0, s>>>(v, n, bad);
+    return cudaGetLastError();
+}
+template cudaError_t launch_check_nonneg<float>(const float *, int64_t, int *, cudaStream_t);
+template cudaError_t launch_check_nonneg<double>(const double *, int64_t, int *, cudaStream_t);
+
+__global__ void k_same_f32(const float *a, const float *b, int64_t n, int *differ) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float va = a ? a[i] : 1.0f;
+        if (__float_as_uint(va) != __float_as_uint(b[i])) atomicOr(differ, 1);
+    }
+}
+
+cudaError_t launch_same_f32(const float *a, const float *b, int64_t n, int *differ, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_same_f32<<<grid_for(n, 4096), BLOCK, 0, s>>>(a, b, n, differ);
     return cudaGetLastError();
 }
 

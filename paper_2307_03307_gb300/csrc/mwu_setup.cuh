@@ -4,6 +4,7 @@
 
 #include "mwu_internal.cuh"
 
+#include <cstdlib>
 #include <vector>
 
 namespace mwu {
@@ -12,7 +13,11 @@ namespace mwu {
 // context is destroyed; alloc_tmp()/scratch() buffers until release_tmp().
 class Arena {
 public:
-    explicit Arena(cudaStream_t s = nullptr) : stream_(s) {}
+    // MWU_FAULT_ALLOC_AT=k in the environment makes the k-th allocation of each
+    // arena fail (a host-side fault injection for the out-of-memory paths)
+    explicit Arena(cudaStream_t s = nullptr) : stream_(s) {
+        if (const char *f = std::getenv("MWU_FAULT_ALLOC_AT")) fail_at_ = std::atol(f);
+    }
     ~Arena() { free_all(); }
     Arena(const Arena &) = delete;
     Arena &operator=(const Arena &) = delete;
@@ -24,7 +29,7 @@ public:
     void *raw(size_t nbytes) {
         void *p = nullptr;
         if (nbytes == 0) nbytes = 16;
-        if (cudaMalloc(&p, nbytes) != cudaSuccess) { failed_ = true; cudaGetLastError(); return nullptr; }
+        if (injected_failure() || cudaMalloc(&p, nbytes) != cudaSuccess) { failed_ = true; cudaGetLastError(); return nullptr; }
         keep_.push_back(p);
         bytes_ += nbytes;
         return p;
@@ -34,7 +39,7 @@ public:
     void *raw_tmp(size_t nbytes) {
         void *p = nullptr;
         if (nbytes == 0) nbytes = 16;
-        if (cudaMalloc(&p, nbytes) != cudaSuccess) { failed_ = true; cudaGetLastError(); return nullptr; }
+        if (injected_failure() || cudaMalloc(&p, nbytes) != cudaSuccess) { failed_ = true; cudaGetLastError(); return nullptr; }
         tmp_.push_back(p);
         return p;
     }
@@ -56,6 +61,8 @@ public:
     }
 
 private:
+    bool injected_failure() { return fail_at_ > 0 && ++count_ == fail_at_; }
+    long fail_at_ = 0, count_ = 0;
     cudaStream_t stream_;
     std::vector<void *> keep_, tmp_;
     size_t bytes_ = 0;

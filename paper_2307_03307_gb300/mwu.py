@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         "mwu_get_timing": (C.c_int, [V, P(mwu_timing), I32]),
         "mwu_spmv_tiles": (C.c_int, [V, P(I32), P(I32)]),
         "mwu_potential": (C.c_int, [V, V, P(D), V, V, V]),
+        "mwu_check_values": (C.c_int, [V, V, V, P(I32)]),
         "mwu_candidates_static": (C.c_int, [V, V, I64, I32, D, D, D, P(D), I32, P(D), P(D), V]),
         "mwu_create_batch": (C.c_int, [I32, P(mwu_matrix), P(mwu_options), P(V)]),
         "mwu_diag_one_minus_exp_neg": (C.c_int, [V, V, I64, V]),
@@ -135,7 +136,7 @@ def exported_symbols():
     return ["mwu_default_options", "mwu_create", "mwu_destroy", "mwu_last_error", "mwu_set_target",
             "mwu_set_x", "mwu_set_state", "mwu_set_direction", "mwu_iterate", "mwu_direction", "mwu_eval_candidates", "mwu_eval_newton", "mwu_search",
             "mwu_solve",
-            "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_spmv_tiles", "mwu_potential",
+            "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_spmv_tiles", "mwu_potential", "mwu_check_values",
             "mwu_candidates_static", "mwu_create_batch", "mwu_solve_batch", "mwu_batch_tuning", "mwu_batch_stats",
             "mwu_diag_one_minus_exp_neg"]
 
@@ -340,6 +341,21 @@ def mwu_potential(ctx, x, grad_x=None, grad_obj=None, grad_vals=None):
     pot = C.c_double()
     _check(ctx, load().mwu_potential(ctx, _ptr(x), C.byref(pot), _ptr(grad_x), _ptr(grad_obj), _ptr(grad_vals)))
     return pot.value
+
+
+def mwu_check_values(ctx, objective=None, values=None):
+    """True when objective / values equal the copies the context was created from."""
+    def f32(a):
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            return np.ascontiguousarray(a, dtype=np.float32)
+        return a.detach().float().contiguous()
+
+    same = C.c_int32()
+    ob, va = f32(objective), f32(values)
+    _check(ctx, load().mwu_check_values(ctx, _ptr(ob), _ptr(va), C.byref(same)))
+    return bool(same.value)
 
 
 def mwu_candidates_static(v, dv, sign, eta, shift, S, alphas, stream=None):
