@@ -461,6 +461,8 @@ def run_ours(args):
         "roofline": (batch_roofline(M, ctx, wl, timed[-1], statistics.mean(step_ms)) if batch else
                      roofline(ab, tim, name) if not args.eager else None),
     }
+    if batch:   # the e2e leg reuses the tuned block size (a fresh context would tune again)
+        opts["batch_workers"] = M.mwu_batch_tuning(ctx)[0]
     M.mwu_destroy(ctx)
 
     if rank == 0 and not batch and not args.no_alt:

@@ -884,9 +884,18 @@ int mwu_set_direction(mwu_ctx *c, const void *d, int32_t is_fp64) {
 // events are recorded as external event nodes when the sequence is captured.
 // kernels an eager iteration launches: direction, SpMV, update and max_passes
 // turns of the search (two kernels per turn with Newton's method)
+// kernels an iteration launches besides direction, SpMV and update: the h
+// scatter, the x step before a rebuilding update, the split view's segment
+// pre-pass and the long-row segment fix-up after the SpMV
+static int extra_kernels(const mwu_ctx *c) {
+    auto count = [](const auto &p) {
+        return (p.hacc != nullptr) + p.x_eager + (p.side[1].cv.n_cseg > 0) +
+               (p.side[0].rv.n_long + p.side[1].rv.n_long > 0);
+    };
+    return c->fp64 ? count(c->pd) : count(c->pf);
+}
 static int kernels_per_iteration(const mwu_ctx *c) {
-    const int extra = (c->fp64 ? c->pd.x_eager : c->pf.x_eager) + (c->fp64 ? c->pd.hacc != nullptr : c->pf.hacc != nullptr);
-    return 3 + extra + (c->opt.step == MWU_STEP_NEWTON ? 2 : 1) * c->opt.max_passes;
+    return 3 + extra_kernels(c) + (c->opt.step == MWU_STEP_NEWTON ? 2 : 1) * c->opt.max_passes;
 }
 constexpr int EV_PER_IT = 5;
 
@@ -1091,7 +1100,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[3], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_update(p, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[4], c->stream));
-            c->launches += 1 + c->pd.x_eager;
+            c->launches += 1 + extra_kernels(c);
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             if (c->opt.timing && (rc = accumulate_timing(c, ev, c->st_host->iter - iter0)) != MWU_OK) return rc;
             done += 1;
@@ -1102,9 +1111,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             // direction, SpMV and update per captured iteration, plus the kernels
             // the search loops ran (counted on the device)
-            c->launches += (int64_t)n * (3 + (c->fp64 ? c->pd.hacc != nullptr : c->pf.hacc != nullptr) +
-                                         (c->fp64 ? c->pd.x_eager : c->pf.x_eager)) +
-                           (c->st_host->loop_launches - loop0);
+            c->launches += (int64_t)n * (3 + extra_kernels(c)) + (c->st_host->loop_launches - loop0);
             if (c->opt.timing &&
                 (rc = accumulate_timing(c, chunk ? c->ev : c->ev_one, c->st_host->iter - iter0)) != MWU_OK)
                 return rc;

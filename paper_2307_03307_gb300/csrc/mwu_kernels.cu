@@ -1652,30 +1652,36 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 5) k_spmv(Problem<
     const SweepConsts<T> K0 = sweep_consts<T>(st);
     if (!(skip & 1)) spmv_side(p, 0, in, to_v, K0.scale0);
     if (!(skip & 2)) spmv_side(p, 1, in, to_v, K0.scale1);
-    const int nseg0 = (skip & 1) ? 0 : p.side[0].rv.n_seg, nseg1 = (skip & 2) ? 0 : p.side[1].rv.n_seg;
-    if (nseg0 == 0 && nseg1 == 0) return;
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->counter[5], 1u) == (unsigned)(gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+}
+
+// Long CSR rows after k_spmv: a warp per row adds the row's segment partial
+// sums (lanes strided over the segments, then the fixed shuffle tree), so the
+// result does not depend on scheduling; the rows' count sets the grid.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_seg_fixup(Problem<T> p, int to_v, int skip) {
+    const DevState *st = p.st;
+    if (!to_v && st->status != ST_RUNNING) return;
+    const SweepConsts<T> K0 = sweep_consts<T>(st);
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t base = 0;
 #pragma unroll 1
     for (int s = 0; s < 2; ++s) {
         const Side<T> &sd = p.side[s];
         const RowView &rv = sd.rv;
-        if (rv.kind != RK_CSR || ((skip >> s) & 1)) continue;
+        if (rv.kind != RK_CSR || ((skip >> s) & 1) || rv.n_long == 0) continue;
         T *out = to_v ? sd.v : sd.dv;
-        const T scale = (T)st->scale[s];
-        for (int i = threadIdx.x; i < rv.n_long; i += blockDim.x) {
-            const int j = rv.long_rows[i];
+        const T scale = s == 0 ? K0.scale0 : K0.scale1;
+        for (int64_t q = w - base; q < rv.n_long; q += nw) {
+            if (q < 0) continue;
+            const int j = rv.long_rows[q];
             T sum = T(0);
-            for (int q = rv.long_seg[i]; q < rv.long_seg[i + 1]; ++q) sum += sd.seg_part[q];
-            out[j] = sum * row_coef(sd, j, scale);
+            for (int k = rv.long_seg[q] + lane; k < rv.long_seg[q + 1]; k += 32) sum += sd.seg_part[k];
+            sum = group_sum(sum, 32);
+            if (lane == 0) out[j] = sum * row_coef(sd, j, scale);
         }
+        base += rv.n_long;
     }
-    if (threadIdx.x == 0) st->counter[5] = 0;
 }
 
 // Sum over [beg, end) with stride `step` of val[k] * win[idx[k] - lo], the
@@ -2334,7 +2340,14 @@ template <class T> static cudaError_t spmv_sides(const Problem<T> &p, const T *i
     const int gs = spmv_grid(p, skip);
     if (gs == 0) return cudaSuccess;
     k_spmv<T><<<gs, BLOCK, 0, s>>>(p, in, to_v, skip);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nl = ((skip & 1) ? 0 : (int64_t)p.side[0].rv.n_long) + ((skip & 2) ? 0 : (int64_t)p.side[1].rv.n_long);
+    if (nl > 0) {
+        k_seg_fixup<T><<<grid_for(32 * nl, p.grid_spmv), BLOCK, 0, s>>>(p, to_v, skip);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 template <class T> static cudaError_t rows_at_x(const Problem<T> &p, int nb_var, cudaStream_t s) {
