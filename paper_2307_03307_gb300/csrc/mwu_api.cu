@@ -581,6 +581,7 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     // each), heavy beyond (a block each)
     int G_var = 1;
     int32_t *hv = nullptr, nhv = 0, *mv = nullptr, nmv = 0;
+    int32_t *tv = nullptr, ntv = 0, *lv = nullptr, nlv = -1;
     auto col_lengths = [&](const SideBuild &b) -> const int32_t * {
         return (b.cv.kind == CK_CSR || b.cv.kind == CK_SPLIT2) ? b.cv.ptr : nullptr;
     };
@@ -603,6 +604,12 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         if (e != cudaSuccess) { fail_cuda(c, e, "variable length classes"); return bail(MWU_ERR_CUDA); }
         if (sb[1].cv.kind == CK_SPLIT2 && nhv > 0 && (rc = split_segments(c, sb[1].cv, hv, nhv)) != MWU_OK)
             return bail(rc);
+        if (sb[1].cv.kind == CK_SPLIT2 && !cp0) {   // split view: tiny and light variable lists
+            const int lt = std::min(light, SPLIT_HEAVY);
+            e = range_list2(c->ar, nullptr, cp1, c->n, -1, SPLIT_TINY, &tv, &ntv, c->stream);
+            if (e == cudaSuccess) e = range_list2(c->ar, nullptr, cp1, c->n, SPLIT_TINY, lt, &lv, &nlv, c->stream);
+            if (e != cudaSuccess) { fail_cuda(c, e, "variable length classes"); return bail(MWU_ERR_CUDA); }
+        }
     }
     // device state
     c->st_dev = c->ar.alloc<DevState>(1);
@@ -621,9 +628,11 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     if (c->fp64) {
         sweep_blocks_per_sm<double>(&vb, &rb, &ub);
         rc = alloc_problem(c, c->pd, sb, hv, nhv, mv, nmv, G_var, vb, rb, ub);
+        c->pd.n_tiny_var = ntv; c->pd.tiny_var = tv; c->pd.n_light_var = nlv; c->pd.light_var = lv;
     } else {
         sweep_blocks_per_sm<float>(&vb, &rb, &ub);
         rc = alloc_problem(c, c->pf, sb, hv, nhv, mv, nmv, G_var, vb, rb, ub);
+        c->pf.n_tiny_var = ntv; c->pf.tiny_var = tv; c->pf.n_light_var = nlv; c->pf.light_var = lv;
     }
     if (rc != MWU_OK) return bail(rc);
     c->x_best = c->ar.raw((size_t)c->n * (c->fp64 ? sizeof(double) : sizeof(float)));

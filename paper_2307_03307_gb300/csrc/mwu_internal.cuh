@@ -80,6 +80,7 @@ template <class T> constexpr int tile_wmax() { return TILE_SMEM / (int)sizeof(T)
 // the segment pre-pass in SPLIT_SEG-entry pieces (one warp each)
 constexpr int SPLIT_HEAVY = 256;
 constexpr int SPLIT_SEG = 256;
+constexpr int SPLIT_TINY = 8;
 constexpr int SHORT_LEN = 16;
 constexpr int MED_LEN = 256;
 constexpr int MED_LANES = 16;
@@ -210,6 +211,14 @@ struct Problem {
     const int32_t *heavy_var;
     int32_t n_med_var;
     const int32_t *med_var;
+    // split view only (n_light_var >= 0): the variables with at most
+    // SPLIT_TINY combined column entries take one thread each (tiny_var), the
+    // other light ones G_var lanes each (light_var); -1: every variable is
+    // visited by the G_var-lane loop
+    int32_t n_tiny_var;
+    const int32_t *tiny_var;
+    int32_t n_light_var;
+    const int32_t *light_var;
 };
 
 // ---------------------------------------------------------------- launchers

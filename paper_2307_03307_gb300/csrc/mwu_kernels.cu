@@ -803,13 +803,25 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 6 : 4) k_dir(Problem<T
             }
         }
     }
+    if (p.n_light_var >= 0) {   // split view: tiny columns one thread each
+        const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p.n_tiny_var; q += nt) {
+            const int64_t i = p.tiny_var[q];
+            const T sg = col_gather<T, true>(P.cv, i, 0, 1, wp, T(1));
+            const T sh = col_gather<T, true>(C.cv, i, 0, 1, wc, T(1));
+            finish(i, sg, sh);
+        }
+    }
     int G = p.G_var, lane = threadIdx.x & (G - 1);
     int64_t per_block = blockDim.x / G;
     int64_t stride = (int64_t)gridDim.x * per_block;
     int64_t warp_base = (int64_t)blockIdx.x * per_block + (threadIdx.x & ~31) / G;
-    for (int64_t base = warp_base; base < p.n; base += stride) {
-        int64_t i = base + (threadIdx.x & 31) / G;
-        bool live = i < p.n;
+    const bool listed = p.n_light_var >= 0;
+    const int64_t n_loop = listed ? p.n_light_var : p.n;
+    for (int64_t base = warp_base; base < n_loop; base += stride) {
+        const int64_t q = base + (threadIdx.x & 31) / G;
+        bool live = q < n_loop;
+        const int64_t i = (listed && live) ? (int64_t)p.light_var[q] : q;
         T sg = T(0), sh = T(0);
         bool heavy = false;
         if (live) {
