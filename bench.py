@@ -249,13 +249,14 @@ def batch_roofline(M, ctx, insts, last, step_ms):
         ab = algorithmic_bytes("bmatching", w.graph.n, w.graph.m)
         total += it * (ab["dir"] + ab["spmv"] + ab["update"]) + pa * ab["cand"]
     peak, src = measured_peaks()
-    nt, ms = M.mwu_batch_tuning(ctx)
+    nt, cl, ms = M.mwu_batch_tuning(ctx)
     achieved = total / (step_ms / 1e3) / 1e9
     return {"bound": "hbm", "kernel": "k_batch_solve (one persistent launch)", "class": "batch",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
             "algorithmic_bytes_per_launch": total, "avg_launch_ms": step_ms,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if src == "measured" else "fallback 6800 GB/s",
-            "threads_per_block": nt, "autotune_ms": {"256": ms[0], "512": ms[1], "1024": ms[2]},
+            "threads_per_block": nt, "blocks_per_cluster": cl,
+            "autotune_ms": {f"{t}x{c}": m for (t, c), m in zip(M.BATCH_TUNE_CONFIGS, ms)},
             "note": "the instances' vectors (about 150 MB) stay largely in the 129 MB L2"}
 
 
@@ -461,8 +462,8 @@ def run_ours(args):
         "roofline": (batch_roofline(M, ctx, wl, timed[-1], statistics.mean(step_ms)) if batch else
                      roofline(ab, tim, name) if not args.eager else None),
     }
-    if batch:   # the e2e leg reuses the tuned block size (a fresh context would tune again)
-        opts["batch_workers"] = M.mwu_batch_tuning(ctx)[0]
+    if batch:   # the e2e leg reuses the tuned block and cluster size (a fresh context would tune again)
+        opts["batch_workers"], opts["batch_cluster"] = M.mwu_batch_tuning(ctx)[:2]
     M.mwu_destroy(ctx)
 
     if rank == 0 and not batch and not args.no_alt:

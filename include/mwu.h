@@ -142,9 +142,10 @@ typedef struct {
     double newton_tol;         /* Newton has converged once |alpha' - alpha| <= newton_tol
                                   alpha; <= 0 selects eps/20                                 */
     int32_t batch_workers;     /* mwu_solve_batch: threads per block of the persistent batch
-                                  solve, 256, 512 or 1024; 0 (default) = autotuned: the
-                                  first solve times the whole batch with each and keeps
-                                  the fastest (mwu_batch_tuning reports the timings)      */
+                                  solve, 256, 512 or 1024; 0 (default) = autotuned together
+                                  with batch_cluster: the first solve times the whole batch
+                                  in each configuration of mwu_batch_tuning and keeps the
+                                  fastest                                                  */
     int32_t drop_covered;      /* 1: keep only the unsatisfied covering rows, the last step
                                   of the loop of Alg. 1 and Alg. 2 (C <- {c_j : c_j^T x < 1}):
                                   a row with (Cx)_j >= 1 leaves smin, h, Phi and Phi'.  x
@@ -185,6 +186,13 @@ typedef struct {
                                   entries are summed in 256-entry segments.  -1 keeps z
                                   incremental (z += alpha dz, Alg. 2) and gathers z over
                                   every vertex's incident edge ids                      */
+    int32_t batch_cluster;     /* mwu_solve_batch with batch_workers 256 or 512: blocks per
+                                  thread-block cluster, 1 (or 0, the default) or 4 or 8.
+                                  With 4 or 8, every instance of at least
+                                  8 x batch_workers x batch_cluster edges is solved by a
+                                  whole cluster (its sums combined across the cluster's
+                                  blocks in a fixed order), the others by one block.
+                                  Ignored when batch_workers = 0 (autotuned)              */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
@@ -431,30 +439,38 @@ int mwu_candidates_static(const float *v, const float *dv, int64_t m, int32_t si
  * built with a stable radix sort).  Options: eps, eta_factor, max_iter,
  * outer_tol, max_probes, max_passes, K, grad_tol, warm_start, step
  * (MWU_STEP_KARY or MWU_STEP_NEWTON), max_newton and newton_tol as for one
- * instance (FP32 vectors with FP64 reductions); batch_workers selects the
- * block size.  MWU_ERR_INVALID for other matrix
- * kinds, an empty instance or a bad endpoint or bound. */
+ * instance (FP32 vectors with FP64 reductions); batch_workers and
+ * batch_cluster select the block and cluster size.  MWU_ERR_INVALID for other
+ * matrix kinds, an empty instance, a bad endpoint or bound, or a bad block or
+ * cluster size. */
 int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
                      mwu_ctx **out);
 
 /* Solve every instance of a batch context in one persistent launch (captured
- * in a CUDA graph with the reset of its work queue): each block takes the
- * next instance, largest first, and runs its whole solve -- the automatic
- * bracket and the geometric bisection on M of Sec. 2.2, and per probe the
+ * in a CUDA graph with the reset of its work queue).  With clusters, each
+ * cluster first takes the next large instance, largest first, and its blocks
+ * solve it together; then each block takes the next remaining instance and
+ * solves it alone.  A solve is the whole of Sec. 2.2's outer search -- the
+ * automatic bracket and the geometric bisection on M, and per probe the
  * iterations of Alg. 2 with the configured step search -- with no host round
- * trip.  An instance is solved by one block with a fixed order of every sum,
- * so its certified objective does not depend on the batch or the schedule
- * (only on the block size).  objective / iters: host arrays of `count`
- * entries or NULL; total: the sums (objective, probes, iters, evals, passes)
- * and the wall time.  The first call of a context with batch_workers = 0
- * runs the autotuner first (three extra whole-batch solves).  Not safe for
- * concurrent use of one context. */
+ * trip.  Every sum of an instance runs in a fixed order, so its certified
+ * objective does not depend on the batch or the schedule (only on the block
+ * size and on the cluster size when a cluster solves it).  objective / iters:
+ * host arrays of `count` entries or NULL; total: the sums (objective, probes,
+ * iters, evals, passes) and the wall time.  The first call of a context with
+ * batch_workers = 0 runs the autotuner first (one extra whole-batch solve per
+ * configuration).  Not safe for concurrent use of one context. */
 int mwu_solve_batch(mwu_ctx *ctx, double *objective, int64_t *iters, mwu_result *total);
 
-/* The autotuner's choice (threads per block, 0 before the first solve) and
- * its timings: ms[0..2] = milliseconds of the whole batch with 256, 512 and
- * 1024 threads per block (0 where not timed).  Either output may be NULL. */
-int mwu_batch_tuning(mwu_ctx *ctx, int32_t *threads, double *ms);
+/* The autotuner's choice (threads per block and blocks per cluster, both 0
+ * before the first solve of an autotuned context) and its timings:
+ * ms[0 .. MWU_BATCH_TUNE_CONFIGS) = milliseconds of the whole batch in the
+ * configurations (threads, cluster) = (256, 1), (512, 1), (1024, 1),
+ * (256, 4), (512, 4), (256, 8), (512, 8), in this order (0 where not timed:
+ * a context with fixed batch_workers, or a cluster size the device cannot
+ * hold).  Any output may be NULL. */
+#define MWU_BATCH_TUNE_CONFIGS 7
+int mwu_batch_tuning(mwu_ctx *ctx, int32_t *threads, int32_t *cluster, double *ms);
 
 /* Per-instance candidate passes and probes of the last mwu_solve_batch (host
  * arrays of `count` entries, either NULL).  MWU_ERR_STATE before a solve. */

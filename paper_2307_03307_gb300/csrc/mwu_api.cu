@@ -66,10 +66,12 @@ struct mwu_ctx {
     int64_t batch_edges = 0;
     std::vector<int64_t> batch_e;            // edges per instance
     int batch_nt = 0;                        // threads per block in use (0 = not tuned yet)
+    int batch_cl = 1;                        // blocks per cluster in use
     int batch_blocks = 0;
-    double tune_ms[3] = {0.0, 0.0, 0.0};     // autotuner: whole-batch time with 256, 512, 1024 threads
+    double tune_ms[MWU_BATCH_TUNE_CONFIGS] = {};   // autotuner: whole-batch time per configuration
     cudaGraphExec_t batch_graph = nullptr;   // queue reset + the persistent launch
-    int batch_graph_nt = 0;
+    int batch_graph_nt = 0, batch_graph_cl = 0;
+    std::vector<int32_t> batch_order;        // instances in decreasing edge count
     std::vector<int64_t> batch_last_passes;  // per instance, of the last solve
     std::vector<int32_t> batch_last_probes;
 };
@@ -135,6 +137,7 @@ int mwu_default_options(mwu_options *o) {
     o->max_newton = 8;
     o->newton_tol = 0.0;   // 0 -> eps / 20
     o->batch_workers = 0;  // 0 -> tuned online
+    o->batch_cluster = 0;
     o->drop_covered = 0;
     o->spmv_tiles = 0;     // automatic
     o->h_scatter = 0;
@@ -1632,6 +1635,11 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
     if (!(o.eps > 0.0 && o.eps < 1.0)) return fail(nullptr, MWU_ERR_INVALID, "eps must lie in (0,1)");
     if (o.batch_workers != 0 && o.batch_workers != 256 && o.batch_workers != 512 && o.batch_workers != 1024)
         return fail(nullptr, MWU_ERR_INVALID, "batch_workers must be 0 (autotuned), 256, 512 or 1024");
+    if (o.batch_cluster == 0) o.batch_cluster = 1;
+    if (o.batch_cluster != 1 && o.batch_cluster != 4 && o.batch_cluster != 8)
+        return fail(nullptr, MWU_ERR_INVALID, "batch_cluster must be 0, 1, 4 or 8");
+    if (o.batch_cluster > 1 && o.batch_workers == 1024)
+        return fail(nullptr, MWU_ERR_INVALID, "batch_cluster > 1 needs batch_workers 0, 256 or 512");
     int64_t Et = 0, Nt = 0;
     for (int k = 0; k < count; ++k) {
         if (P[k].kind != MWU_MAT_INCIDENCE || !P[k].edges || P[k].n_edges <= 0 || P[k].n_vertices <= 0)
@@ -1724,6 +1732,7 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
     std::vector<int32_t> order(count);
     for (int k = 0; k < count; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return P[a].n_edges > P[b].n_edges; });
+    c->batch_order = order;
     TRY_CUDA(c, cudaMemcpyAsync(d_eoff, eoff.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s));
     TRY_CUDA(c, cudaMemcpyAsync(d_voff, voff.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s));
     TRY_CUDA(c, cudaMemcpyAsync(d_order, order.data(), 4 * (size_t)count, cudaMemcpyHostToDevice, s));
@@ -1747,7 +1756,7 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
     B.evals = c->ar.alloc<int64_t>(count);
     B.passes = c->ar.alloc<int64_t>(count);
     B.probes = c->ar.alloc<int32_t>(count);
-    B.queue = c->ar.alloc<unsigned int>(1);
+    B.queue = c->ar.alloc<unsigned int>(2);
     if (!B.x || !B.d || !B.y || !B.dy || !B.st || !B.obj || !B.iters || !B.evals || !B.passes || !B.probes || !B.queue) {
         c->err = "allocating the batch work vectors";
         return bail(MWU_ERR_OOM);
@@ -1766,38 +1775,68 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
     B.max_newton = o.max_newton;
     B.newton_tol = o.newton_tol;
     c->batch_nt = o.batch_workers;   // 0: tuned on the first solve
+    c->batch_cl = o.batch_cluster;
     TRY_CUDA(c, cudaStreamSynchronize(s));
     *out = c;
     return MWU_OK;
 }
 
-static int batch_blocks_for(mwu_ctx *c, int nt) {
-    return std::max(1, std::min(c->batch_count, c->n_sms * std::min(8, batch_blocks_per_sm(nt))));
+// The autotuner's configurations (threads per block, blocks per cluster), in
+// the order of mwu_batch_tuning's timings.
+static const int kTuneNT[MWU_BATCH_TUNE_CONFIGS] = {256, 512, 1024, 256, 512, 256, 512};
+static const int kTuneCL[MWU_BATCH_TUNE_CONFIGS] = {1, 1, 1, 4, 4, 8, 8};
+
+// Instances solved by whole clusters: the prefix of the order with at least
+// batch_cluster_edges(nt, cl) edges.
+static int batch_n_cluster(const mwu_ctx *c, int nt, int cl) {
+    const int64_t thr = batch_cluster_edges(nt, cl);
+    int k = 0;
+    while (k < c->batch_count && c->batch_e[c->batch_order[k]] >= thr) ++k;
+    return k;
 }
 
-// Autotuner: the whole batch solved once with 256, 512 and 1024 threads per
-// block (CUDA events), the fastest kept for the context (and its timings for
-// mwu_batch_tuning).
+// The persistent grid: every block resident, no more than the work needs.
+static int batch_blocks_for(mwu_ctx *c, int nt, int cl) {
+    const int res = batch_blocks(nt, cl, c->n_sms);
+    if (res <= 0) return 0;
+    const int nc = batch_n_cluster(c, nt, cl);
+    const int64_t need = (int64_t)nc * cl + (c->batch_count - nc);
+    const int64_t b = std::min<int64_t>(res, (need + cl - 1) / cl * cl);
+    return (int)std::max<int64_t>(cl, b);
+}
+
+static cudaError_t batch_launch(mwu_ctx *c, int nt, int cl) {
+    const int blocks = batch_blocks_for(c, nt, cl);
+    if (blocks <= 0) return cudaErrorInvalidConfiguration;
+    return launch_batch_solve(c->bd, nt, cl, batch_n_cluster(c, nt, cl), blocks, c->stream);
+}
+
+// Autotuner: the whole batch solved once in each configuration (CUDA events),
+// the fastest kept for the context (and its timings for mwu_batch_tuning).  A
+// configuration the device cannot run (no resident cluster) is skipped.
 static int batch_autotune(mwu_ctx *c) {
-    const int nts[3] = {256, 512, 1024};
     cudaEvent_t a, b;
     TRY_CUDA(c, cudaEventCreate(&a));
     TRY_CUDA(c, cudaEventCreate(&b));
-    int best = 0;
-    for (int i = 0; i < 3; ++i) {
+    int best = -1;
+    for (int i = 0; i < MWU_BATCH_TUNE_CONFIGS; ++i) {
+        c->tune_ms[i] = 0.0;
+        if (batch_blocks_for(c, kTuneNT[i], kTuneCL[i]) <= 0) continue;
         cudaError_t e = cudaEventRecord(a, c->stream);
-        if (e == cudaSuccess) e = launch_batch_solve(c->bd, nts[i], batch_blocks_for(c, nts[i]), c->stream);
+        if (e == cudaSuccess) e = batch_launch(c, kTuneNT[i], kTuneCL[i]);
         if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
         if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return fail_cuda(c, e, "batch autotune"); }
         c->tune_ms[i] = ms;
-        if (ms < c->tune_ms[best]) best = i;
+        if (best < 0 || ms < c->tune_ms[best]) best = i;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    c->batch_nt = nts[best];
+    if (best < 0) return fail(c, MWU_ERR_CUDA, "batch autotune: no configuration can run");
+    c->batch_nt = kTuneNT[best];
+    c->batch_cl = kTuneCL[best];
     return MWU_OK;
 }
 
@@ -1806,12 +1845,13 @@ int mwu_solve_batch(mwu_ctx *c, double *objective, int64_t *iters, mwu_result *t
     auto t0 = std::chrono::steady_clock::now();
     int rc;
     if (c->batch_nt == 0 && (rc = batch_autotune(c)) != MWU_OK) return rc;
-    if (c->batch_graph_nt != c->batch_nt) {
+    if (c->batch_graph_nt != c->batch_nt || c->batch_graph_cl != c->batch_cl) {
         if (c->batch_graph) { cudaGraphExecDestroy(c->batch_graph); c->batch_graph = nullptr; }
-        c->batch_blocks = batch_blocks_for(c, c->batch_nt);
+        c->batch_blocks = batch_blocks_for(c, c->batch_nt, c->batch_cl);
+        if (c->batch_blocks <= 0) return fail(c, MWU_ERR_INVALID, "batch: no cluster of this size fits the device");
         cudaGraph_t g = nullptr;
         TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = launch_batch_solve(c->bd, c->batch_nt, c->batch_blocks, c->stream);
+        cudaError_t e = batch_launch(c, c->batch_nt, c->batch_cl);
         cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail_cuda(c, e, "capture batch solve"); }
         if (e2 != cudaSuccess) return fail_cuda(c, e2, "end capture");
@@ -1819,6 +1859,7 @@ int mwu_solve_batch(mwu_ctx *c, double *objective, int64_t *iters, mwu_result *t
         cudaGraphDestroy(g);
         if (e != cudaSuccess) { c->batch_graph = nullptr; return fail_cuda(c, e, "instantiate batch graph"); }
         c->batch_graph_nt = c->batch_nt;
+        c->batch_graph_cl = c->batch_cl;
     }
     TRY_CUDA(c, cudaGraphLaunch(c->batch_graph, c->stream));
     const int n = c->batch_count;
@@ -1851,10 +1892,11 @@ int mwu_solve_batch(mwu_ctx *c, double *objective, int64_t *iters, mwu_result *t
     return bad ? fail(c, MWU_ERR_NUMERIC, "NaN/Inf in a batch instance") : MWU_OK;
 }
 
-int mwu_batch_tuning(mwu_ctx *c, int32_t *threads, double *ms) {
+int mwu_batch_tuning(mwu_ctx *c, int32_t *threads, int32_t *cluster, double *ms) {
     if (!c || !c->is_batch) return MWU_ERR_INVALID;
     if (threads) *threads = c->batch_nt;
-    if (ms) for (int i = 0; i < 3; ++i) ms[i] = c->tune_ms[i];
+    if (cluster) *cluster = c->batch_nt ? c->batch_cl : 0;
+    if (ms) for (int i = 0; i < MWU_BATCH_TUNE_CONFIGS; ++i) ms[i] = c->tune_ms[i];
     return MWU_OK;
 }
 

@@ -2596,24 +2596,145 @@ template <class T> int tiled_blocks_per_sm() {
 // ============================================================ batched b-matching
 // One persistent launch solves a batch of independent b-matching LPs
 // (Appendix A.1 with lb = 0: max 1^T x, diag(1/b) M x <= 1, a pure packing LP
-// whose covering side is the objective row (1/M) 1^T x >= 1, Sec. 2.2).  Each
-// block takes the next instance from a device work queue (instances ordered by
-// decreasing size) and runs its whole solve: the bracket and the geometric
-// bisection on M, and per probe Alg. 2's iterations with the K-candidate
-// search (the library's own decision rules, dir_finish / search_decide, on a
-// per-block DevState).  An instance is always solved by one block with a fixed
-// order of every sum, so its result does not depend on the batch, the block or
-// the schedule; only the block size (chosen by the autotuner) sets that order.
-template <int NT>
-__device__ __forceinline__ double bt_sum(double v, double *sm) {
-    return block_sum<double>(v, sm);
+// whose covering side is the objective row (1/M) 1^T x >= 1, Sec. 2.2).  A
+// crew -- one block, or a thread-block cluster of C blocks -- takes the next
+// instance from a device work queue (instances ordered by decreasing size) and
+// runs its whole solve: the bracket and the geometric bisection on M, and per
+// probe Alg. 2's iterations with the K-candidate or Newton search (the
+// library's own decision rules, dir_finish / search_decide / newton_decide, on
+// a DevState that every block of the crew keeps and updates identically).
+//
+// Cluster launches (C > 1) first drain a queue of the large instances (at
+// least batch_cluster_edges(NT, C) edges), each solved by the whole cluster:
+// every loop is strided over the C * NT threads, and every sum is reduced in
+// the block, published in a shared-memory slot, and combined by each block
+// from the C slots in rank order through distributed shared memory after one
+// cluster barrier (release / acquire), so that all blocks hold bit-identical
+// totals and take identical decisions.  The barriers also order the global
+// writes of one block before another block's gathers (of y in the direction,
+// of d and x in P v); those gathers bypass L1 (ld.global.cg).  Then every block
+// takes the remaining small instances alone from a second queue.  An
+// instance's result depends only on the block size and on whether a cluster
+// (and of which size) solved it, never on the batch or the schedule.
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// A double in block `rank`'s shared memory at the address of p in this block's.
+__device__ __forceinline__ double ld_peer(const double *p, unsigned rank) {
+    uint32_t a = (uint32_t)__cvta_generic_to_shared(p), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(r));
+    return v;
+}
+
+constexpr int XS = 5 * KMAX;   // doubles per exchange slot (K candidate records)
+
+template <int NT, int C> struct Crew {
+    static constexpr int S = NT * C;   // loop stride over an instance's edges and vertices
+    unsigned rank;                     // block rank in the cluster (0 when C == 1)
+    int par;                           // exchange-slot parity (alternates per exchange)
+    double *slot;                      // this block's exchange slots, [2][XS] in shared memory
+    __device__ int64_t tid() const { return (int64_t)rank * NT + threadIdx.x; }
+    // the slot of the next exchange; the alternation makes one barrier per
+    // exchange enough (a slot is rewritten only after the next exchange's
+    // barrier, which every block reaches after its reads of this one)
+    __device__ double *next() {
+        double *p = slot + par * XS;
+        par ^= 1;
+        return p;
+    }
+};
+
+// Gathered load of data that another block of the crew wrote
+template <int C> __device__ __forceinline__ float gload(const float *p) {
+    if constexpr (C == 1) return *p;
+    else return __ldcg(p);
+}
+
+template <int NT, int C> __device__ double crew_sum(Crew<NT, C> &cw, double v, double *sm) {
+    v = block_sum<double>(v, sm);
+    if constexpr (C == 1) {
+        return v;
+    } else {
+        double *sl = cw.next();
+        if (threadIdx.x == 0) sl[0] = v;
+        cluster_barrier();
+        if (threadIdx.x == 0) {
+            double r[C];
+#pragma unroll
+            for (int q = 0; q < C; ++q) r[q] = ld_peer(sl, q);
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < C; ++q) t += r[q];
+            sm[0] = t;
+        }
+        __syncthreads();
+        const double t = sm[0];
+        __syncthreads();
+        return t;
+    }
+}
+
+// Two sums with one exchange
+template <int NT, int C> __device__ void crew_sum2(Crew<NT, C> &cw, double &a, double &b, double *sm) {
+    a = block_sum<double>(a, sm);
+    b = block_sum<double>(b, sm);
+    if constexpr (C > 1) {
+        double *sl = cw.next();
+        if (threadIdx.x == 0) { sl[0] = a; sl[1] = b; }
+        cluster_barrier();
+        if (threadIdx.x < 2) {
+            double r[C];
+#pragma unroll
+            for (int q = 0; q < C; ++q) r[q] = ld_peer(sl + threadIdx.x, q);
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < C; ++q) t += r[q];
+            sm[threadIdx.x] = t;
+        }
+        __syncthreads();
+        a = sm[0];
+        b = sm[1];
+        __syncthreads();
+    }
+}
+
+template <int NT, int C> __device__ double crew_max(Crew<NT, C> &cw, double v, double *sm) {
+    v = block_max<double>(v, sm);
+    if constexpr (C == 1) {
+        return v;
+    } else {
+        double *sl = cw.next();
+        if (threadIdx.x == 0) sl[0] = v;
+        cluster_barrier();
+        if (threadIdx.x == 0) {
+            double r[C];
+#pragma unroll
+            for (int q = 0; q < C; ++q) r[q] = ld_peer(sl, q);
+            double t = r[0];
+#pragma unroll
+            for (int q = 1; q < C; ++q) t = fmax(t, r[q]);
+            sm[0] = t;
+        }
+        __syncthreads();
+        const double t = sm[0];
+        __syncthreads();
+        return t;
+    }
 }
 
 // Log-sum-exp of y (packing rows, sign +1): s = max y, S = sum e^{eta (y - s)}.
-template <int NT>
-__device__ void bt_lse(const float *y, int64_t n, float eta, double *sm, double &s_out, double &S_out) {
+template <int NT, int C>
+__device__ void bt_lse(Crew<NT, C> &cw, const float *y, int64_t n, float eta, double *sm, double &s_out,
+                       double &S_out) {
     Lse<float> acc{0.0f, 0.0f};
-    for (int64_t j = threadIdx.x; j < n; j += NT) lse_push(acc, y[j], eta, 1);
+    for (int64_t j = cw.tid(); j < n; j += Crew<NT, C>::S) lse_push(acc, y[j], eta, 1);
     for (int off = 16; off > 0; off >>= 1) {
         const float os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
         lse_merge<float, float>(acc, os, oS, eta, 1);
@@ -2628,6 +2749,22 @@ __device__ void bt_lse(const float *y, int64_t n, float eta, double *sm, double 
         sm[1] = t.S;
     }
     __syncthreads();
+    if constexpr (C > 1) {
+        double *sl = cw.next();
+        if (threadIdx.x == 0) { sl[0] = sm[0]; sl[1] = sm[1]; }
+        cluster_barrier();
+        if (threadIdx.x == 0) {
+            double rs[C], rS[C];
+#pragma unroll
+            for (int q = 0; q < C; ++q) { rs[q] = ld_peer(sl, q); rS[q] = ld_peer(sl + 1, q); }
+            Lse<double> t{0.0, 0.0};
+#pragma unroll
+            for (int q = 0; q < C; ++q) lse_merge<float, double>(t, rs[q], rS[q], (double)eta, 1);
+            sm[0] = t.s;
+            sm[1] = t.S;
+        }
+        __syncthreads();
+    }
     s_out = sm[0];
     S_out = sm[1];
     __syncthreads();
@@ -2635,29 +2772,33 @@ __device__ void bt_lse(const float *y, int64_t n, float eta, double *sm, double 
 
 // y_w = (1/b_w) sum_{e at w} v_e over the vertex -> incident-edge lists; four
 // independent gathers in flight per thread
-template <int NT>
-__device__ void bt_rows(const int32_t *vp, const int32_t *ei, const float *bnd, const float *v, float *out, int64_t n) {
-    for (int64_t w = threadIdx.x; w < n; w += NT) {
+template <int NT, int C>
+__device__ void bt_rows(const Crew<NT, C> &cw, const int32_t *vp, const int32_t *ei, const float *bnd, const float *v,
+                        float *out, int64_t n) {
+    for (int64_t w = cw.tid(); w < n; w += Crew<NT, C>::S) {
         const int kb = vp[w], ke = vp[w + 1];
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
         int k = kb;
         for (; k + 3 < ke; k += 4) {
             const int i0 = ei[k], i1 = ei[k + 1], i2 = ei[k + 2], i3 = ei[k + 3];
-            a0 += v[i0]; a1 += v[i1]; a2 += v[i2]; a3 += v[i3];
+            a0 += gload<C>(v + i0); a1 += gload<C>(v + i1); a2 += gload<C>(v + i2); a3 += gload<C>(v + i3);
         }
-        for (; k < ke; ++k) a0 += v[ei[k]];
+        for (; k < ke; ++k) a0 += gload<C>(v + ei[k]);
         const float a = (a0 + a1) + (a2 + a3);
         out[w] = bnd ? a / bnd[w] : a;
     }
 }
 
-template <int NT>
-__device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
+template <int NT, int C>
+__device__ void bt_solve(const BatchDesc &B, int inst, DevState *st, Crew<NT, C> &cw) {
+    constexpr int S = Crew<NT, C>::S;
     __shared__ double sm[32];
     __shared__ float s_al[KMAX], s_ca[KMAX];
     __shared__ float wrec[NT / 32][KMAX][4];
     __shared__ float wD[NT / 32];
+    __shared__ double brec[KMAX][5];
     __shared__ int s_go;
+    const int64_t tid = cw.tid();
     const int64_t e0 = B.eoff[inst], E = B.eoff[inst + 1] - e0;
     const int64_t v0 = B.voff[inst], n = B.voff[inst + 1] - v0;
     const int2 *ed = reinterpret_cast<const int2 *>(B.edges) + e0;
@@ -2668,13 +2809,14 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
     const double eps = B.eps;
     // bracket (packing, c = 1, a_we = 1/b_w): hi = sum_e max(b_u, b_v), lo = sum_e min(b_u, b_v) / E
     double hs = 0.0, ls = 0.0;
-    for (int64_t e = threadIdx.x; e < E; e += NT) {
+    for (int64_t e = tid; e < E; e += S) {
         const int2 uv = ed[e];
         const double bu = bnd ? bnd[uv.x] : 1.0, bv = bnd ? bnd[uv.y] : 1.0;
         hs += fmax(bu, bv);
         ls += fmin(bu, bv);
     }
-    double hi = bt_sum<NT>(hs, sm), lo = bt_sum<NT>(ls, sm) / (double)E;
+    crew_sum2(cw, hs, ls, sm);
+    double hi = hs, lo = ls / (double)E;
     double best = lo;
     int probes = 0;
     int64_t iters = 0, evals = 0, passes = 0;
@@ -2687,16 +2829,17 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
         const float cd_f = (float)(1.0 / eta), invM = (float)(1.0 / M);
         // a0: x_e = eps / (E max(1/b_u, 1/b_v)), y = Px, z = 1^T x / M
         double xs = 0.0;
-        for (int64_t e = threadIdx.x; e < E; e += NT) {
+        for (int64_t e = tid; e < E; e += S) {
             const int2 uv = ed[e];
             const double a = bnd ? 1.0 / (double)bnd[uv.x] : 1.0, b = bnd ? 1.0 / (double)bnd[uv.y] : 1.0;
             const float xe = (float)(eps / ((double)E * fmax(a, b)));
             x[e] = xe;
             xs += (double)xe;
         }
-        double z = bt_sum<NT>(xs, sm) / M;
-        __syncthreads();
-        bt_rows<NT>(vp, ei, bnd, x, y, n);
+        double z = crew_sum(cw, xs, sm) / M;   // (the exchange orders the x writes before the gathers)
+        bt_rows(cw, vp, ei, bnd, x, y, n);
+        // the probe's search state starts from zero in every block of the crew
+        for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 8); i += NT) reinterpret_cast<long long *>(st)[i] = 0;
         __syncthreads();
         if (threadIdx.x == 0) {
             st->eta = eta; st->eps = eps; st->c_d = 1.0 / eta; st->K = B.K; st->max_passes = B.max_passes;
@@ -2710,7 +2853,7 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
         int it = 0;
         for (;;) {
             double sp, Sp;
-            bt_lse<NT>(y, n, eta_f, sm, sp, Sp);
+            bt_lse(cw, y, n, eta_f, sm, sp, Sp);   // (its exchange orders the y writes before the gathers)
             // stopping tests before each iteration (Alg. 2, R8, R12), zmin = z (one exact row)
             const double ymax = sp;
             if (rho > 0.0 && z > 0.0 && ymax <= rho * z) { status = ST_FEASIBLE; break; }
@@ -2721,25 +2864,25 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
             double np = 0.0, ds = 0.0;
             // four edges per thread and round: their endpoint and x loads, then
             // the gathers of y and b, then the arithmetic
-            for (int64_t e0 = threadIdx.x; e0 < E; e0 += 4 * NT) {
+            for (int64_t e0 = tid; e0 < E; e0 += 4 * S) {
                 int2 uv[4];
                 float xe[4], yu[4], yv[4], bu[4], bv[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const int64_t e = e0 + r * NT;
+                    const int64_t e = e0 + r * S;
                     uv[r] = e < E ? ed[e] : make_int2(0, 0);
                     xe[r] = e < E ? x[e] : 0.0f;
                 }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    yu[r] = y[uv[r].x];
-                    yv[r] = y[uv[r].y];
+                    yu[r] = gload<C>(y + uv[r].x);
+                    yv[r] = gload<C>(y + uv[r].y);
                     bu[r] = bnd ? bnd[uv[r].x] : 1.0f;
                     bv[r] = bnd ? bnd[uv[r].y] : 1.0f;
                 }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const int64_t e = e0 + r * NT;
+                    const int64_t e = e0 + r * S;
                     if (e < E) {
                         float wu = t_exp(eta_f * (yu[r] - s_f)), wv = t_exp(eta_f * (yv[r] - s_f));
                         if (bnd) { wu /= bu[r]; wv /= bv[r]; }
@@ -2751,10 +2894,8 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
                     }
                 }
             }
-            np = bt_sum<NT>(np, sm);
-            ds = bt_sum<NT>(ds, sm);
-            __syncthreads();
-            bt_rows<NT>(vp, ei, bnd, d, dy, n);   // a6: dy = P d
+            crew_sum2(cw, np, ds, sm);   // (orders the d writes before the gathers of P d)
+            bt_rows(cw, vp, ei, bnd, d, dy, n);   // a6: dy = P d
             if (threadIdx.x == 0) {
                 st->phase = PH_DONE;
                 dir_finish(st, np, 0.0, ds);   // d = 0 -> INFEASIBLE, else the search starts
@@ -2794,10 +2935,10 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
                 CandAcc<float> acc;
                 cand_init(acc, 1);
                 if (nwt) {
-                    for (int64_t j = threadIdx.x; j < n; j += NT)
+                    for (int64_t j = tid; j < n; j += S)
                         cand_push_m<float, 3, 1, 1>(acc, ca, al, 0.0f, 1, y[j], dy[j], eta_f, s_f, t_inf<float>(), camax);
                 } else {
-                    for (int64_t j = threadIdx.x; j < n; j += NT)
+                    for (int64_t j = tid; j < n; j += S)
                         cand_push_m<float, 2, 1, 0>(acc, ca, al, 0.0f, K, y[j], dy[j], eta_f, s_f, t_inf<float>(), camax);
                 }
 #pragma unroll
@@ -2818,12 +2959,40 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
                 }
                 __syncthreads();
                 __shared__ double s_psi[KMAX], s_dpsi;
+                double *sl = nullptr;
+                if constexpr (C > 1) sl = cw.next();
                 if (threadIdx.x < K) {
                     const int k = threadIdx.x;
                     double mx = 0.0, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
                     for (int w = 0; w < NT / 32; ++w)
                         cand_merge1d<float, double>(mx, R, Tt, zm, D, wrec[w][k][0], wrec[w][k][1], wrec[w][k][2],
                                                     wrec[w][k][3], k == 0 ? (double)wD[w] : 0.0, 1);
+                    brec[k][0] = mx; brec[k][1] = R; brec[k][2] = Tt; brec[k][3] = zm; brec[k][4] = D;
+                    if constexpr (C > 1) {
+                        double *o = sl + 5 * k;
+                        o[0] = mx; o[1] = R; o[2] = Tt; o[3] = zm; o[4] = D;
+                    }
+                }
+                if constexpr (C > 1) {
+                    cluster_barrier();
+                    if (threadIdx.x < K) {   // the C blocks' records of candidate k, in rank order
+                        const int k = threadIdx.x;
+                        const double *o = sl + 5 * k;
+                        double r[C][5];
+#pragma unroll
+                        for (int q = 0; q < C; ++q)
+#pragma unroll
+                            for (int f = 0; f < 5; ++f) r[q][f] = ld_peer(o + f, q);
+                        double mx = 0.0, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
+#pragma unroll
+                        for (int q = 0; q < C; ++q)
+                            cand_merge1d<float, double>(mx, R, Tt, zm, D, r[q][0], r[q][1], r[q][2], r[q][3], r[q][4], 1);
+                        brec[k][0] = mx; brec[k][1] = R; brec[k][2] = Tt; brec[k][3] = zm; brec[k][4] = D;
+                    }
+                }
+                if (threadIdx.x < K) {
+                    const int k = threadIdx.x;
+                    const double mx = brec[k][0], R = brec[k][1], Tt = brec[k][2], D = brec[k][4];
                     // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p) (Sec. 4.1);
                     // the transcendentals in FP32 (as the FP32 form's passes take them), the
                     // combination in FP64
@@ -2861,8 +3030,8 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
             // a8: x += alpha d, y += alpha dy, z += alpha dz
             const double alpha = st->alpha_acc;
             const float af = (float)alpha;
-            for (int64_t e = threadIdx.x; e < E; e += NT) x[e] = fmaf(af, d[e], x[e]);
-            for (int64_t w = threadIdx.x; w < n; w += NT) y[w] = fmaf(af, dy[w], y[w]);
+            for (int64_t e = tid; e < E; e += S) x[e] = fmaf(af, d[e], x[e]);
+            for (int64_t w = tid; w < n; w += S) y[w] = fmaf(af, dy[w], y[w]);
             z += alpha * dz;
             ++it;
             __syncthreads();
@@ -2875,13 +3044,13 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
         ++probes;
         // certificate of the probe's x: 1^T x / max(Px), with y recomputed from x
         double sx = 0.0;
-        for (int64_t e = threadIdx.x; e < E; e += NT) sx += (double)x[e];
-        sx = bt_sum<NT>(sx, sm);
-        bt_rows<NT>(vp, ei, bnd, x, y, n);
+        for (int64_t e = tid; e < E; e += S) sx += (double)x[e];
+        sx = crew_sum(cw, sx, sm);   // (orders the last x writes before the gathers)
+        bt_rows(cw, vp, ei, bnd, x, y, n);
         __syncthreads();
         double ym = 0.0;
-        for (int64_t w = threadIdx.x; w < n; w += NT) ym = fmax(ym, (double)y[w]);
-        ym = block_max<double>(ym, sm);
+        for (int64_t w = tid; w < n; w += S) ym = fmax(ym, (double)y[w]);
+        ym = crew_max(cw, ym, sm);
         const double cert = ym > 0.0 ? sx / ym : 0.0;
         best = fmax(best, cert);
         lo = fmax(lo, cert);
@@ -2889,7 +3058,7 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
         else hi = fmin(hi, M);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (cw.rank == 0 && threadIdx.x == 0) {
         B.obj[inst] = best;
         B.iters[inst] = iters;
         B.probes[inst] = probes;
@@ -2898,42 +3067,114 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st) {
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_batch_solve(BatchDesc B) {
+// Block-alone solves of the instances order[n_cluster ..] from queue[1]
+template <int NT> __device__ void bt_alone(const BatchDesc &B, DevState *st, double *slot) {
     __shared__ int s_q;
-    DevState *st = B.st + blockIdx.x;
+    Crew<NT, 1> cw{0u, 0, slot};
     for (;;) {
-        if (threadIdx.x == 0) s_q = (int)atomicAdd(B.queue, 1u);
+        if (threadIdx.x == 0) s_q = (int)atomicAdd(B.queue + 1, 1u);
         __syncthreads();
-        const int q = s_q;
+        const int q = B.n_cluster + s_q;
         __syncthreads();
         if (q >= B.count) return;
-        bt_solve<NT>(B, B.order[q], st);
+        bt_solve<NT, 1>(B, B.order[q], st, cw);
         __syncthreads();
     }
 }
 
-cudaError_t launch_batch_solve(const BatchDesc &B, int nt, int blocks, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(B.queue, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    switch (nt) {
-    case 256: k_batch_solve<256><<<blocks, 256, 0, s>>>(B); break;
-    case 512: k_batch_solve<512><<<blocks, 512, 0, s>>>(B); break;
-    case 1024: k_batch_solve<1024><<<blocks, 1024, 0, s>>>(B); break;
-    default: return cudaErrorInvalidValue;
+template <int NT, int C>
+__global__ void __launch_bounds__(NT) k_batch_solve(BatchDesc B) {
+    __shared__ double slot[2 * XS];
+    DevState *st = B.st + blockIdx.x;
+    if constexpr (C > 1) {
+        // the cluster's instances: rank 0 takes the next from queue[0] and
+        // publishes it; all C blocks solve it together
+        __shared__ int s_q;
+        Crew<NT, C> cw{cluster_rank(), 0, slot};
+        for (;;) {
+            double *sl = cw.next();
+            if (cw.rank == 0 && threadIdx.x == 0) sl[0] = (double)atomicAdd(B.queue, 1u);
+            cluster_barrier();
+            if (threadIdx.x == 0) s_q = (int)ld_peer(sl, 0);
+            __syncthreads();
+            const int q = s_q;
+            __syncthreads();
+            if (q >= B.n_cluster) break;
+            bt_solve<NT, C>(B, B.order[q], st, cw);
+        }
+        cluster_barrier();   // no block reads a peer's shared memory past this point
     }
-    return cudaGetLastError();
+    bt_alone<NT>(B, st, slot);
 }
 
-int batch_blocks_per_sm(int nt) {
-    int a = 0;
-    switch (nt) {
-    case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<256>, 256, 0); break;
-    case 512: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<512>, 512, 0); break;
-    case 1024: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<1024>, 1024, 0); break;
-    default: break;
+int batch_cluster_edges(int nt, int cl) { return cl > 1 ? 8 * nt * cl : 0x7fffffff; }
+
+template <int NT, int C> static cudaError_t batch_launch_cfg(const BatchDesc &B, int blocks, cudaStream_t s) {
+    if constexpr (C == 1) {
+        k_batch_solve<NT, 1><<<blocks, NT, 0, s>>>(B);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_batch_solve<NT, C>, B);
     }
-    return a > 0 ? a : 1;
+}
+
+template <int NT, int C> static int batch_blocks_cfg(int n_sms) {
+    if constexpr (C == 1) {
+        int a = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<NT, 1>, NT, 0);
+        return n_sms * std::min(8, a > 0 ? a : 1);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(C * n_sms));
+        cfg.blockDim = dim3(NT);
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, k_batch_solve<NT, C>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return std::min(ncl * C, (n_sms * 8 / C) * C);
+    }
+}
+
+#define MWU_BATCH_CFGS(X) X(256, 1) X(512, 1) X(1024, 1) X(256, 4) X(512, 4) X(256, 8) X(512, 8)
+
+cudaError_t launch_batch_solve(const BatchDesc &Bin, int nt, int cl, int n_cluster, int blocks, cudaStream_t s) {
+    BatchDesc B = Bin;
+    B.n_cluster = cl > 1 ? n_cluster : 0;
+    cudaError_t e = cudaMemsetAsync(B.queue, 0, 2 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+#define MWU_BATCH_LAUNCH(a, b) \
+    if (nt == a && cl == b) return batch_launch_cfg<a, b>(B, blocks, s);
+    MWU_BATCH_CFGS(MWU_BATCH_LAUNCH)
+#undef MWU_BATCH_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+int batch_blocks(int nt, int cl, int n_sms) {
+#define MWU_BATCH_BLOCKS(a, b) \
+    if (nt == a && cl == b) return batch_blocks_cfg<a, b>(n_sms);
+    MWU_BATCH_CFGS(MWU_BATCH_BLOCKS)
+#undef MWU_BATCH_BLOCKS
+    return 0;
 }
 
 #define MWU_INSTANTIATE(T)                                                                                     \

@@ -44,7 +44,7 @@ class mwu_options(C.Structure):
                 ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p),
                 ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("batch_workers", C.c_int32),
                 ("drop_covered", C.c_int32), ("spmv_tiles", C.c_int32), ("h_scatter", C.c_int32),
-                ("dv_scatter", C.c_int32), ("col_split", C.c_int32)]
+                ("dv_scatter", C.c_int32), ("col_split", C.c_int32), ("batch_cluster", C.c_int32)]
 
 
 class mwu_iter_stats(C.Structure):
@@ -120,7 +120,7 @@ def load(path: str = LIB_PATH):
         "mwu_create_batch": (C.c_int, [I32, P(mwu_matrix), P(mwu_options), P(V)]),
         "mwu_diag_one_minus_exp_neg": (C.c_int, [V, V, I64, V]),
         "mwu_solve_batch": (C.c_int, [V, P(D), P(I64), P(mwu_result)]),
-        "mwu_batch_tuning": (C.c_int, [V, P(I32), P(D)]),
+        "mwu_batch_tuning": (C.c_int, [V, P(I32), P(I32), P(D)]),
         "mwu_batch_stats": (C.c_int, [V, P(I64), P(I32)]),
     }
     for name, (res, args) in sig.items():
@@ -390,12 +390,17 @@ def mwu_solve_batch(ctx, count):
     return list(obj), list(it), _as_dict(r)
 
 
+# the autotuner's (threads per block, blocks per cluster), in mwu_batch_tuning's order
+BATCH_TUNE_CONFIGS = ((256, 1), (512, 1), (1024, 1), (256, 4), (512, 4), (256, 8), (512, 8))
+
+
 def mwu_batch_tuning(ctx):
-    """(threads per block in use, [ms with 256, 512, 1024]) of the batch autotuner."""
-    nt = C.c_int32()
-    ms = (C.c_double * 3)()
-    _check(ctx, load().mwu_batch_tuning(ctx, C.byref(nt), ms))
-    return nt.value, list(ms)
+    """(threads per block, blocks per cluster, [ms per BATCH_TUNE_CONFIGS entry])
+    of the batch autotuner."""
+    nt, cl = C.c_int32(), C.c_int32()
+    ms = (C.c_double * len(BATCH_TUNE_CONFIGS))()
+    _check(ctx, load().mwu_batch_tuning(ctx, C.byref(nt), C.byref(cl), ms))
+    return nt.value, cl.value, list(ms)
 
 
 def mwu_batch_stats(ctx, count):

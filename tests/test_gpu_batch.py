@@ -1,7 +1,7 @@
 """Batched b-matching (many independent packing LPs, Appendix A.1 with lb = 0)
 in one persistent launch: every instance's certified objective is the same
-whether it is solved in the batch or alone (one block per instance, a fixed
-order of every sum), lies within (1+eps)^2 of the exact b-matching LP optimum
+whether it is solved in the batch or alone (one block or one cluster per
+instance, a fixed order of every sum), lies within (1+eps)^2 of the exact b-matching LP optimum
 (max flow), and within 1+eps of the FP64 oracle's solve; the autotuner keeps
 the fastest block size it timed."""
 import numpy as np
@@ -62,22 +62,64 @@ def test_batch_from_host_arrays_and_autotuner(M):
     insts = W.bmatching_batch(count=12, seed=9, lo=1e3, hi=3e4)
     ctx = M.mwu_create_batch(_mats(insts, device="cpu"))
     try:
-        nt0, _ = M.mwu_batch_tuning(ctx)
-        assert nt0 == 0
+        nt0, cl0, _ = M.mwu_batch_tuning(ctx)
+        assert nt0 == 0 and cl0 == 0
         obj, it, tot = M.mwu_solve_batch(ctx, len(insts))
-        nt, ms = M.mwu_batch_tuning(ctx)
-        assert nt in (256, 512, 1024) and all(t > 0 for t in ms)
-        assert ms[(256, 512, 1024).index(nt)] == min(ms)       # the fastest configuration it timed
+        nt, cl, ms = M.mwu_batch_tuning(ctx)
+        assert (nt, cl) in M.BATCH_TUNE_CONFIGS and ms[:3] and all(t > 0 for t in ms[:3])
+        timed = [t for t in ms if t > 0]
+        assert ms[M.BATCH_TUNE_CONFIGS.index((nt, cl))] == min(timed)   # the fastest configuration it timed
         passes, probes = M.mwu_batch_stats(ctx, len(insts))
         assert sum(passes) == tot["passes"] and sum(probes) == tot["probes"]
     finally:
         M.mwu_destroy(ctx)
-    ctx = M.mwu_create_batch(_mats(insts), batch_workers=nt)
+    ctx = M.mwu_create_batch(_mats(insts), batch_workers=nt, batch_cluster=cl)
     try:
         obj2, it2, _ = M.mwu_solve_batch(ctx, len(insts))
     finally:
         M.mwu_destroy(ctx)
     assert obj == obj2 and it == it2                         # host or device inputs, same solve
+
+
+@pytest.mark.parametrize("nt,cl,step", [(256, 4, "kary"), (512, 8, "newton"), (256, 8, "kary")])
+def test_cluster_batch_equals_alone_and_exact(M, nt, cl, step):
+    """Instances of at least 8 * nt * cl edges are solved by a whole cluster
+    (sums combined across its blocks in rank order), the rest by one block;
+    either way the batch changes nothing and the objective is certified."""
+    insts = W.bmatching_batch(count=8, seed=11, lo=2e3, hi=8e4)
+    thr = 8 * nt * cl
+    assert any(w.graph.m >= thr for w in insts) and any(w.graph.m < thr for w in insts)
+    st = M.STEP_NEWTON if step == "newton" else M.STEP_KARY
+    ctx = M.mwu_create_batch(_mats(insts), batch_workers=nt, batch_cluster=cl, step=st)
+    try:
+        obj_b, it_b, tot = M.mwu_solve_batch(ctx, len(insts))
+        obj_2, it_2, _ = M.mwu_solve_batch(ctx, len(insts))
+        assert M.mwu_batch_tuning(ctx)[:2] == (nt, cl)
+    finally:
+        M.mwu_destroy(ctx)
+    assert obj_b == obj_2 and it_b == it_2 and tot["launches"] == 1
+    for k, wl in enumerate(insts):
+        c1 = M.mwu_create_batch(_mats([wl]), batch_workers=nt, batch_cluster=cl, step=st)
+        try:
+            o1, i1, _ = M.mwu_solve_batch(c1, 1)
+        finally:
+            M.mwu_destroy(c1)
+        assert obj_b[k] == o1[0] and it_b[k] == i1[0], k
+        g = wl.graph
+        opt = exact.b_matching_size(g.n_left, g.n, g.u.numpy(), g.v.numpy(), wl.bounds.numpy())
+        assert opt / (1 + wl.eps) ** 2 <= obj_b[k] <= opt * (1 + 1e-6), (k, obj_b[k], opt)
+    # a clustered instance against the FP64 oracle's solve
+    big = max(range(len(insts)), key=lambda k: insts[k].graph.m)
+    ores = H.oracle_solve(insts[big], step=step)
+    assert 1 / (1 + insts[big].eps) <= obj_b[big] / ores.objective <= 1 + insts[big].eps
+
+
+def test_batch_rejects_bad_cluster(M):
+    insts = W.bmatching_batch(count=2, seed=4, lo=1e3, hi=2e3)
+    for kw in ({"batch_workers": 256, "batch_cluster": 3}, {"batch_workers": 1024, "batch_cluster": 4}):
+        with pytest.raises(M.MWUError) as e:
+            M.mwu_create_batch(_mats(insts), **kw)
+        assert e.value.code == M.ERR_INVALID
 
 
 def test_batch_rejects_other_matrices(M):
