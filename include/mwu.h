@@ -187,12 +187,15 @@ typedef struct {
                                   incremental (z += alpha dz, Alg. 2) and gathers z over
                                   every vertex's incident edge ids                      */
     int32_t batch_cluster;     /* mwu_solve_batch with batch_workers 256 or 512: blocks per
-                                  thread-block cluster, 1 (or 0, the default) or 4 or 8.
-                                  With 4 or 8, every instance of at least
-                                  8 x batch_workers x batch_cluster edges is solved by a
-                                  whole cluster (its sums combined across the cluster's
-                                  blocks in a fixed order), the others by one block.
-                                  Ignored when batch_workers = 0 (autotuned)              */
+                                  thread-block cluster, 1 (or 0, the default), 4, 8 or 16
+                                  (16 where the device allows clusters beyond the portable
+                                  8).  With more than 1, every instance of at least
+                                  batch_cluster_edges edges is solved by a whole cluster
+                                  (its sums combined across the cluster's blocks in a fixed
+                                  order), the others by one block.  Ignored when
+                                  batch_workers = 0 (autotuned)                            */
+    int32_t batch_cluster_edges; /* smallest instance (edges) a cluster solves; 0 (default)
+                                  = 2 x threads per block x blocks per cluster             */
 } mwu_options;
 
 /* Fill *opt with the defaults above.  Returns MWU_OK or MWU_ERR_INVALID (opt == NULL). */
@@ -466,15 +469,21 @@ int mwu_solve_batch(mwu_ctx *ctx, double *objective, int64_t *iters, mwu_result 
  * before the first solve of an autotuned context) and its timings:
  * ms[0 .. MWU_BATCH_TUNE_CONFIGS) = milliseconds of the whole batch in the
  * configurations (threads, cluster) = (256, 1), (512, 1), (1024, 1),
- * (256, 4), (512, 4), (256, 8), (512, 8), in this order (0 where not timed:
- * a context with fixed batch_workers, or a cluster size the device cannot
- * hold).  Any output may be NULL. */
-#define MWU_BATCH_TUNE_CONFIGS 7
+ * (256, 4), (512, 4), (256, 8), (512, 8), (256, 16), (512, 16), in this order
+ * (0 where not timed: a context with fixed batch_workers, or a cluster size
+ * the device cannot hold).  Any output may be NULL. */
+#define MWU_BATCH_TUNE_CONFIGS 9
 int mwu_batch_tuning(mwu_ctx *ctx, int32_t *threads, int32_t *cluster, double *ms);
 
 /* Per-instance candidate passes and probes of the last mwu_solve_batch (host
  * arrays of `count` entries, either NULL).  MWU_ERR_STATE before a solve. */
 int mwu_batch_stats(mwu_ctx *ctx, int64_t *passes, int32_t *probes);
+
+/* Per-instance start and end of its solve in the last mwu_solve_batch, in
+ * milliseconds after the earliest start (the device's global timer): shows
+ * which instance ends last and sets the batch time.  Host arrays of `count`
+ * entries, either NULL.  MWU_ERR_STATE before a solve. */
+int mwu_batch_timeline(mwu_ctx *ctx, double *start_ms, double *end_ms);
 
 /* ------------------------------------------------------------ diagnostics */
 /* u[i] = 1 - e^{-b[i]} for b[i] >= 0, by the same device function the

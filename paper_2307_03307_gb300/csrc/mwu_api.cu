@@ -74,6 +74,7 @@ struct mwu_ctx {
     std::vector<int32_t> batch_order;        // instances in decreasing edge count
     std::vector<int64_t> batch_last_passes;  // per instance, of the last solve
     std::vector<int32_t> batch_last_probes;
+    std::vector<int64_t> batch_t_beg, batch_t_end;   // per instance, %globaltimer ns of the last solve
 };
 
 // ------------------------------------------------------------ helpers
@@ -138,6 +139,7 @@ int mwu_default_options(mwu_options *o) {
     o->newton_tol = 0.0;   // 0 -> eps / 20
     o->batch_workers = 0;  // 0 -> tuned online
     o->batch_cluster = 0;
+    o->batch_cluster_edges = 0;
     o->drop_covered = 0;
     o->spmv_tiles = 0;     // automatic
     o->h_scatter = 0;
@@ -1636,8 +1638,9 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
     if (o.batch_workers != 0 && o.batch_workers != 256 && o.batch_workers != 512 && o.batch_workers != 1024)
         return fail(nullptr, MWU_ERR_INVALID, "batch_workers must be 0 (autotuned), 256, 512 or 1024");
     if (o.batch_cluster == 0) o.batch_cluster = 1;
-    if (o.batch_cluster != 1 && o.batch_cluster != 4 && o.batch_cluster != 8)
-        return fail(nullptr, MWU_ERR_INVALID, "batch_cluster must be 0, 1, 4 or 8");
+    if (o.batch_cluster != 1 && o.batch_cluster != 4 && o.batch_cluster != 8 && o.batch_cluster != 16)
+        return fail(nullptr, MWU_ERR_INVALID, "batch_cluster must be 0, 1, 4, 8 or 16");
+    if (o.batch_cluster_edges < 0) return fail(nullptr, MWU_ERR_INVALID, "batch_cluster_edges must be >= 0");
     if (o.batch_cluster > 1 && o.batch_workers == 1024)
         return fail(nullptr, MWU_ERR_INVALID, "batch_cluster > 1 needs batch_workers 0, 256 or 512");
     int64_t Et = 0, Nt = 0;
@@ -1749,19 +1752,19 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
     B.d = c->ar.alloc<float>(Et);
     B.y = c->ar.alloc<float>(Nt);
     B.dy = c->ar.alloc<float>(Nt);
-    const int max_blocks = c->n_sms * 8;
-    B.st = c->ar.alloc<DevState>(max_blocks);
     B.obj = c->ar.alloc<double>(count);
     B.iters = c->ar.alloc<int64_t>(count);
     B.evals = c->ar.alloc<int64_t>(count);
     B.passes = c->ar.alloc<int64_t>(count);
     B.probes = c->ar.alloc<int32_t>(count);
     B.queue = c->ar.alloc<unsigned int>(2);
-    if (!B.x || !B.d || !B.y || !B.dy || !B.st || !B.obj || !B.iters || !B.evals || !B.passes || !B.probes || !B.queue) {
+    B.t_beg = c->ar.alloc<int64_t>(count);
+    B.t_end = c->ar.alloc<int64_t>(count);
+    if (!B.x || !B.d || !B.y || !B.dy || !B.obj || !B.iters || !B.evals || !B.passes || !B.probes || !B.queue ||
+        !B.t_beg || !B.t_end) {
         c->err = "allocating the batch work vectors";
         return bail(MWU_ERR_OOM);
     }
-    TRY_CUDA(c, cudaMemsetAsync(B.st, 0, sizeof(DevState) * (size_t)max_blocks, s));
     B.eps = o.eps;
     B.eta_factor = o.eta_factor;
     B.outer_tol = o.outer_tol;
@@ -1783,13 +1786,14 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
 
 // The autotuner's configurations (threads per block, blocks per cluster), in
 // the order of mwu_batch_tuning's timings.
-static const int kTuneNT[MWU_BATCH_TUNE_CONFIGS] = {256, 512, 1024, 256, 512, 256, 512};
-static const int kTuneCL[MWU_BATCH_TUNE_CONFIGS] = {1, 1, 1, 4, 4, 8, 8};
+static const int kTuneNT[MWU_BATCH_TUNE_CONFIGS] = {256, 512, 1024, 256, 512, 256, 512, 256, 512};
+static const int kTuneCL[MWU_BATCH_TUNE_CONFIGS] = {1, 1, 1, 4, 4, 8, 8, 16, 16};
 
 // Instances solved by whole clusters: the prefix of the order with at least
-// batch_cluster_edges(nt, cl) edges.
+// batch_cluster_edges edges (0: 2 x threads x cluster).
 static int batch_n_cluster(const mwu_ctx *c, int nt, int cl) {
-    const int64_t thr = batch_cluster_edges(nt, cl);
+    if (cl <= 1) return 0;
+    const int64_t thr = c->opt.batch_cluster_edges > 0 ? (int64_t)c->opt.batch_cluster_edges : 2LL * nt * cl;
     int k = 0;
     while (k < c->batch_count && c->batch_e[c->batch_order[k]] >= thr) ++k;
     return k;
@@ -1866,6 +1870,10 @@ int mwu_solve_batch(mwu_ctx *c, double *objective, int64_t *iters, mwu_result *t
     std::vector<double> obj(n);
     std::vector<int64_t> it(n), ev(n), pa(n);
     std::vector<int32_t> pr(n);
+    c->batch_t_beg.resize(n);
+    c->batch_t_end.resize(n);
+    TRY_CUDA(c, cudaMemcpyAsync(c->batch_t_beg.data(), c->bd.t_beg, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaMemcpyAsync(c->batch_t_end.data(), c->bd.t_end, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     TRY_CUDA(c, cudaMemcpyAsync(obj.data(), c->bd.obj, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     TRY_CUDA(c, cudaMemcpyAsync(it.data(), c->bd.iters, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     TRY_CUDA(c, cudaMemcpyAsync(ev.data(), c->bd.evals, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
@@ -1897,6 +1905,17 @@ int mwu_batch_tuning(mwu_ctx *c, int32_t *threads, int32_t *cluster, double *ms)
     if (threads) *threads = c->batch_nt;
     if (cluster) *cluster = c->batch_nt ? c->batch_cl : 0;
     if (ms) for (int i = 0; i < MWU_BATCH_TUNE_CONFIGS; ++i) ms[i] = c->tune_ms[i];
+    return MWU_OK;
+}
+
+int mwu_batch_timeline(mwu_ctx *c, double *start_ms, double *end_ms) {
+    if (!c || !c->is_batch) return MWU_ERR_INVALID;
+    if (c->batch_t_beg.empty()) return fail(c, MWU_ERR_STATE, "no batch solve yet");
+    const int64_t t0 = *std::min_element(c->batch_t_beg.begin(), c->batch_t_beg.end());
+    for (int k = 0; k < c->batch_count; ++k) {
+        if (start_ms) start_ms[k] = 1e-6 * (double)(c->batch_t_beg[k] - t0);
+        if (end_ms) end_ms[k] = 1e-6 * (double)(c->batch_t_end[k] - t0);
+    }
     return MWU_OK;
 }
 

@@ -268,24 +268,23 @@ struct BatchDesc {
     const float *bound;        // capacity per vertex, or nullptr (all 1)
     const int32_t *vptr, *eids;
     float *x, *d, *y, *dy;     // per edge (x, d) and per vertex (y, dy)
-    DevState *st;              // one per block (each block of a cluster keeps an identical copy)
     double *obj;
     int64_t *iters, *evals, *passes;
     int32_t *probes;
     unsigned int *queue;       // next instance to take: [0] cluster-solved, [1] block-solved
     int32_t n_cluster;         // order[0 .. n_cluster) are solved by whole clusters (set per launch)
+    int64_t *t_beg, *t_end;    // per instance: %globaltimer (ns) at the start and end of its solve
     double eps, eta_factor, outer_tol, grad_tol, newton_tol;
     int32_t max_iter, max_probes, max_passes, K, warm_start;
     int32_t step_mode;         // 0 K-candidate search, 3 Newton (Sec. 4.2)
     int32_t max_newton;
 };
-// nt threads per block, cl blocks per cluster (1, 4 or 8 with nt 256 or 512; 1
-// with 1024); the first n_cluster instances of the order are solved by whole
+// nt threads per block, cl blocks per cluster (1, 4, 8 or 16 with nt 256 or
+// 512; 1 with 1024); the first n_cluster instances of the order are solved by whole
 // clusters.  batch_blocks: the persistent grid (all blocks resident), 0 if the
 // configuration cannot run.
 cudaError_t launch_batch_solve(const BatchDesc &B, int nt, int cl, int n_cluster, int blocks, cudaStream_t s);
 int batch_blocks(int nt, int cl, int n_sms);
-int batch_cluster_edges(int nt, int cl);   // smallest instance (edges) a cluster solves
 
 // Message for mwu_last_error(NULL) from entry points without a context.
 void set_global_error(const char *msg);

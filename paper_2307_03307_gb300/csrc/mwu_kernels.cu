@@ -2616,6 +2616,11 @@ template <class T> int tiled_blocks_per_sm() {
 // takes the remaining small instances alone from a second queue.  An
 // instance's result depends only on the block size and on whether a cluster
 // (and of which size) solved it, never on the batch or the schedule.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -2657,147 +2662,251 @@ template <int C> __device__ __forceinline__ float gload(const float *p) {
     else return __ldcg(p);
 }
 
-template <int NT, int C> __device__ double crew_sum(Crew<NT, C> &cw, double v, double *sm) {
-    v = block_sum<double>(v, sm);
-    if constexpr (C == 1) {
-        return v;
-    } else {
-        double *sl = cw.next();
-        if (threadIdx.x == 0) sl[0] = v;
-        cluster_barrier();
-        if (threadIdx.x == 0) {
-            double r[C];
-#pragma unroll
-            for (int q = 0; q < C; ++q) r[q] = ld_peer(sl, q);
-            double t = 0.0;
-#pragma unroll
-            for (int q = 0; q < C; ++q) t += r[q];
-            sm[0] = t;
-        }
-        __syncthreads();
-        const double t = sm[0];
-        __syncthreads();
-        return t;
-    }
-}
+// ---- crew reductions.  GB300 runs FP64 at a small fraction of its FP32 rate,
+// so the per-thread and per-warp work is FP32 and FP64 is kept to short trees
+// over the warps' and blocks' totals.  Every result is valid at thread 0 of
+// each block of the crew (identical in all blocks: the same values combined by
+// the same tree); the callers broadcast what the other threads need.
 
-// Two sums with one exchange
-template <int NT, int C> __device__ void crew_sum2(Crew<NT, C> &cw, double &a, double &b, double *sm) {
-    a = block_sum<double>(a, sm);
-    b = block_sum<double>(b, sm);
+// Sums over the crew of per-thread partials P (FP32, or FP64 where a solve's
+// certificate depends on them): P within each warp, FP64 over the warps (a
+// tree in warp 0) and over the cluster's blocks (a tree over lanes 0 .. C-1
+// after one exchange).
+template <int NT, int C, int NV, class P>
+__device__ void crew_sums(Crew<NT, C> &cw, P (&v)[NV], double (&out)[NV], double *sm) {
+    constexpr int W = NT / 32;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        for (int off = 16; off > 0; off >>= 1) v[i] += shfl_x(v[i], off);
+        if (l == 0) sm[i * W + w] = (double)v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = 0.0;
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double t = l < W ? sm[i * W + l] : 0.0;
+            for (int off = W / 2; off > 0; off >>= 1) t += shfl_x(t, off);
+            out[i] = t;
+        }
+    }
     if constexpr (C > 1) {
         double *sl = cw.next();
-        if (threadIdx.x == 0) { sl[0] = a; sl[1] = b; }
-        cluster_barrier();
-        if (threadIdx.x < 2) {
-            double r[C];
-#pragma unroll
-            for (int q = 0; q < C; ++q) r[q] = ld_peer(sl + threadIdx.x, q);
-            double t = 0.0;
-#pragma unroll
-            for (int q = 0; q < C; ++q) t += r[q];
-            sm[threadIdx.x] = t;
-        }
-        __syncthreads();
-        a = sm[0];
-        b = sm[1];
-        __syncthreads();
-    }
-}
-
-template <int NT, int C> __device__ double crew_max(Crew<NT, C> &cw, double v, double *sm) {
-    v = block_max<double>(v, sm);
-    if constexpr (C == 1) {
-        return v;
-    } else {
-        double *sl = cw.next();
-        if (threadIdx.x == 0) sl[0] = v;
-        cluster_barrier();
         if (threadIdx.x == 0) {
-            double r[C];
 #pragma unroll
-            for (int q = 0; q < C; ++q) r[q] = ld_peer(sl, q);
-            double t = r[0];
-#pragma unroll
-            for (int q = 1; q < C; ++q) t = fmax(t, r[q]);
-            sm[0] = t;
+            for (int i = 0; i < NV; ++i) sl[i] = out[i];
         }
-        __syncthreads();
-        const double t = sm[0];
-        __syncthreads();
-        return t;
+        cluster_barrier();
+        if (w == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                double t = l < C ? ld_peer(sl + i, l) : 0.0;
+                for (int off = C / 2; off > 0; off >>= 1) t += shfl_x(t, off);
+                out[i] = t;
+            }
+        }
     }
+    __syncthreads();
 }
 
-// Log-sum-exp of y (packing rows, sign +1): s = max y, S = sum e^{eta (y - s)}.
+// Maximum over the crew of per-thread values (all >= 0), FP32.
+template <int NT, int C> __device__ float crew_max(Crew<NT, C> &cw, float v, float *smf) {
+    constexpr int W = NT / 32;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, shfl_x(v, off));
+    if (l == 0) smf[w] = v;
+    __syncthreads();
+    float t = 0.0f;
+    if (w == 0) {
+        t = l < W ? smf[l] : 0.0f;
+        for (int off = W / 2; off > 0; off >>= 1) t = fmaxf(t, shfl_x(t, off));
+    }
+    if constexpr (C > 1) {
+        double *sl = cw.next();
+        if (threadIdx.x == 0) sl[0] = (double)t;
+        cluster_barrier();
+        if (w == 0) {
+            t = l < C ? (float)ld_peer(sl, l) : 0.0f;
+            for (int off = C / 2; off > 0; off >>= 1) t = fmaxf(t, shfl_x(t, off));
+        }
+    }
+    __syncthreads();
+    return t;
+}
+
+// Log-sum-exp of y (packing rows, sign +1): s = max y, S = sum e^{eta (y - s)},
+// FP32 throughout (per thread, a tree over the lanes, the warps and the
+// cluster's blocks); valid at thread 0.
 template <int NT, int C>
-__device__ void bt_lse(Crew<NT, C> &cw, const float *y, int64_t n, float eta, double *sm, double &s_out,
-                       double &S_out) {
+__device__ void bt_lse(Crew<NT, C> &cw, const float *y, int64_t n, float eta, float *smf, float &s_out,
+                       float &S_out) {
+    constexpr int W = NT / 32;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     Lse<float> acc{0.0f, 0.0f};
     for (int64_t j = cw.tid(); j < n; j += Crew<NT, C>::S) lse_push(acc, y[j], eta, 1);
     for (int off = 16; off > 0; off >>= 1) {
         const float os = shfl_x(acc.s, off), oS = shfl_x(acc.S, off);
         lse_merge<float, float>(acc, os, oS, eta, 1);
     }
-    __shared__ double ws[NT / 32], wS[NT / 32];
-    if ((threadIdx.x & 31) == 0) { ws[threadIdx.x >> 5] = acc.s; wS[threadIdx.x >> 5] = acc.S; }
+    if (l == 0) { smf[w] = acc.s; smf[W + w] = acc.S; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        Lse<double> t{0.0, 0.0};
-        for (int w = 0; w < NT / 32; ++w) lse_merge<float, double>(t, ws[w], wS[w], (double)eta, 1);
-        sm[0] = t.s;
-        sm[1] = t.S;
+    Lse<float> t{0.0f, 0.0f};
+    if (w == 0) {
+        if (l < W) t = Lse<float>{smf[l], smf[W + l]};
+        for (int off = W / 2; off > 0; off >>= 1) {
+            const float os = shfl_x(t.s, off), oS = shfl_x(t.S, off);
+            lse_merge<float, float>(t, os, oS, eta, 1);
+        }
     }
-    __syncthreads();
     if constexpr (C > 1) {
         double *sl = cw.next();
-        if (threadIdx.x == 0) { sl[0] = sm[0]; sl[1] = sm[1]; }
+        if (threadIdx.x == 0) { sl[0] = (double)t.s; sl[1] = (double)t.S; }
         cluster_barrier();
-        if (threadIdx.x == 0) {
-            double rs[C], rS[C];
-#pragma unroll
-            for (int q = 0; q < C; ++q) { rs[q] = ld_peer(sl, q); rS[q] = ld_peer(sl + 1, q); }
-            Lse<double> t{0.0, 0.0};
-#pragma unroll
-            for (int q = 0; q < C; ++q) lse_merge<float, double>(t, rs[q], rS[q], (double)eta, 1);
-            sm[0] = t.s;
-            sm[1] = t.S;
+        if (w == 0) {
+            t = Lse<float>{0.0f, 0.0f};
+            if (l < C) t = Lse<float>{(float)ld_peer(sl, l), (float)ld_peer(sl + 1, l)};
+            for (int off = C / 2; off > 0; off >>= 1) {
+                const float os = shfl_x(t.s, off), oS = shfl_x(t.S, off);
+                lse_merge<float, float>(t, os, oS, eta, 1);
+            }
         }
-        __syncthreads();
     }
-    s_out = sm[0];
-    S_out = sm[1];
     __syncthreads();
+    s_out = t.s;
+    S_out = t.S;
 }
 
-// y_w = (1/b_w) sum_{e at w} v_e over the vertex -> incident-edge lists; four
-// independent gathers in flight per thread
+// y_w = (1/b_w) sum_{e at w} v_e over the vertex -> incident-edge lists: four
+// vertices per thread and round, their list bounds loaded together, then four
+// edge ids of each and their four gathers in flight at a time.  Vertex w is
+// handled by the thread that owns index w in every other strided loop.
 template <int NT, int C>
 __device__ void bt_rows(const Crew<NT, C> &cw, const int32_t *vp, const int32_t *ei, const float *bnd, const float *v,
                         float *out, int64_t n) {
-    for (int64_t w = cw.tid(); w < n; w += Crew<NT, C>::S) {
-        const int kb = vp[w], ke = vp[w + 1];
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-        int k = kb;
-        for (; k + 3 < ke; k += 4) {
-            const int i0 = ei[k], i1 = ei[k + 1], i2 = ei[k + 2], i3 = ei[k + 3];
-            a0 += gload<C>(v + i0); a1 += gload<C>(v + i1); a2 += gload<C>(v + i2); a3 += gload<C>(v + i3);
+    constexpr int S = Crew<NT, C>::S;
+    for (int64_t w0 = cw.tid(); w0 < n; w0 += 4 * S) {
+        int kb[4], ke[4];
+        float acc[4];
+        int len = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t w = w0 + r * S;
+            kb[r] = w < n ? vp[w] : 0;
+            ke[r] = w < n ? vp[w + 1] : 0;
+            acc[r] = 0.0f;
         }
-        for (; k < ke; ++k) a0 += gload<C>(v + ei[k]);
-        const float a = (a0 + a1) + (a2 + a3);
-        out[w] = bnd ? a / bnd[w] : a;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) len = max(len, ke[r] - kb[r]);
+        for (int t = 0; t < len; t += 4) {
+            int id[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = kb[r] + t + q;
+                    id[r][q] = k < ke[r] ? ei[k] : -1;
+                }
+            float g[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) g[r][q] = id[r][q] >= 0 ? gload<C>(v + id[r][q]) : 0.0f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r] += (g[r][0] + g[r][1]) + (g[r][2] + g[r][3]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t w = w0 + r * S;
+            if (w < n) out[w] = bnd ? acc[r] / bnd[w] : acc[r];
+        }
+    }
+}
+
+// Candidate records of one pass: the warps' records (wrec, wD) merged by warp
+// 0, four lanes per candidate (each merges every fourth warp, then two
+// butterfly steps), then the cluster's blocks likewise after one exchange.
+// Candidate k's record lands in lane 4k of warp 0.
+template <int NT, int C>
+__device__ void bt_cand_reduce(Crew<NT, C> &cw, const float (*wrec)[KMAX][4], const float *wD, int K, float &mx,
+                               float &R, float &Tt, float &zm, float &D) {
+    constexpr int W = NT / 32;
+    const int l = threadIdx.x & 31, k = l >> 2, j = l & 3;
+    mx = 0.0f; R = 0.0f; Tt = 0.0f; zm = t_inf<float>(); D = 0.0f;
+    const bool wz = (threadIdx.x >> 5) == 0;
+    if (wz) {
+        if (k < K)
+            for (int q = j; q < W; q += 4)
+                cand_merge1d<float, float>(mx, R, Tt, zm, D, wrec[q][k][0], wrec[q][k][1], wrec[q][k][2], wrec[q][k][3],
+                                           k == 0 ? wD[q] : 0.0f, 1);
+        for (int off = 1; off < 4; off <<= 1) {
+            const float omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off),
+                        oD = shfl_x(D, off);
+            cand_merge1d<float, float>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, 1);
+        }
+    }
+    if constexpr (C > 1) {
+        double *sl = cw.next();
+        if (wz && j == 0 && k < K) {
+            double *o = sl + 5 * k;
+            o[0] = mx; o[1] = R; o[2] = Tt; o[3] = zm; o[4] = D;
+        }
+        cluster_barrier();
+        if (wz) {
+            mx = 0.0f; R = 0.0f; Tt = 0.0f; zm = t_inf<float>(); D = 0.0f;
+            if (k < K) {
+                const double *o = sl + 5 * k;
+                for (int q = j; q < C; q += 4)
+                    cand_merge1d<float, float>(mx, R, Tt, zm, D, (float)ld_peer(o, q), (float)ld_peer(o + 1, q),
+                                               (float)ld_peer(o + 2, q), (float)ld_peer(o + 3, q),
+                                               (float)ld_peer(o + 4, q), 1);
+            }
+            for (int off = 1; off < 4; off <<= 1) {
+                const float omx = shfl_x(mx, off), oR = shfl_x(R, off), oT = shfl_x(Tt, off), oz = shfl_x(zm, off),
+                            oD = shfl_x(D, off);
+                cand_merge1d<float, float>(mx, R, Tt, zm, D, omx, oR, oT, oz, oD, 1);
+            }
+        }
+    }
+}
+
+// Scalars of one solve, owned by thread 0 (the doubles) and broadcast to the
+// block through shared memory (the floats and the flag).
+// Each broadcast field is written by thread 0 before a barrier and read by the
+// others after it, and thread 0 rewrites it only after a later barrier (go is
+// shared by decisions that have at least one barrier between them; phase and
+// kpass copy the search state for the pass loop; acc / af end a step search).
+struct BtCtl {
+    double eta, hi, lo, best, M, rho, z, dz, lnS;
+    long long iters, evals, passes;
+    int probes, it, status, go, acc, phase, kpass;
+    float eta_f, thr, x0, cdf, invM, fp, sf, af;
+};
+
+// Thread 0, at the end of a step search: accept alpha (>= 1) or end the probe.
+__device__ __forceinline__ void bt_step_end(BtCtl &cs, DevState *st) {
+    const double alpha = st->alpha_acc;
+    cs.acc = st->status == ST_RUNNING && alpha >= 1.0;
+    if (cs.acc) {
+        cs.af = (float)alpha;
+        cs.z += alpha * cs.dz;
+        cs.it += 1;
+        st->alpha_prev = alpha;
+        st->iter = cs.it;
     }
 }
 
 template <int NT, int C>
 __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st, Crew<NT, C> &cw) {
-    constexpr int S = Crew<NT, C>::S;
-    __shared__ double sm[32];
+    constexpr int S = Crew<NT, C>::S, W = NT / 32;
+    __shared__ double sm[2 * W];
+    __shared__ float smf[2 * W];
     __shared__ float s_al[KMAX], s_ca[KMAX];
-    __shared__ float wrec[NT / 32][KMAX][4];
-    __shared__ float wD[NT / 32];
-    __shared__ double brec[KMAX][5];
-    __shared__ int s_go;
+    __shared__ float wrec[W][KMAX][4];
+    __shared__ float wD[W];
+    __shared__ double s_psi[KMAX], s_dpsi;
+    __shared__ BtCtl cs;
     const int64_t tid = cw.tid();
     const int64_t e0 = B.eoff[inst], E = B.eoff[inst + 1] - e0;
     const int64_t v0 = B.voff[inst], n = B.voff[inst + 1] - v0;
@@ -2807,36 +2916,59 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st, Crew<NT, C>
     const int32_t *ei = B.eids + 2 * e0;
     float *x = B.x + e0, *d = B.d + e0, *y = B.y + v0, *dy = B.dy + v0;
     const double eps = B.eps;
+    if (cw.rank == 0 && threadIdx.x == 0) B.t_beg[inst] = (int64_t)globaltimer_ns();
     // bracket (packing, c = 1, a_we = 1/b_w): hi = sum_e max(b_u, b_v), lo = sum_e min(b_u, b_v) / E
-    double hs = 0.0, ls = 0.0;
-    for (int64_t e = tid; e < E; e += S) {
-        const int2 uv = ed[e];
-        const double bu = bnd ? bnd[uv.x] : 1.0, bv = bnd ? bnd[uv.y] : 1.0;
-        hs += fmax(bu, bv);
-        ls += fmin(bu, bv);
-    }
-    crew_sum2(cw, hs, ls, sm);
-    double hi = hs, lo = ls / (double)E;
-    double best = lo;
-    int probes = 0;
-    int64_t iters = 0, evals = 0, passes = 0;
-    const double eta = B.eta_factor * log((double)(n + 1)) / eps;
-    const float eta_f = (float)eta;
-    const float thr = (float)(1.0 - B.grad_tol);
-    while (hi > (1.0 + B.outer_tol) * lo && probes < B.max_probes) {
-        const double M = sqrt(lo * hi);
-        const double rho = (1.0 + B.outer_tol) * M / hi;   // the certificate closes the bracket (R12)
-        const float cd_f = (float)(1.0 / eta), invM = (float)(1.0 / M);
-        // a0: x_e = eps / (E max(1/b_u, 1/b_v)), y = Px, z = 1^T x / M
-        double xs = 0.0;
+    {
+        float v[2] = {0.0f, 0.0f};
         for (int64_t e = tid; e < E; e += S) {
             const int2 uv = ed[e];
-            const double a = bnd ? 1.0 / (double)bnd[uv.x] : 1.0, b = bnd ? 1.0 / (double)bnd[uv.y] : 1.0;
-            const float xe = (float)(eps / ((double)E * fmax(a, b)));
-            x[e] = xe;
-            xs += (double)xe;
+            const float bu = bnd ? bnd[uv.x] : 1.0f, bv = bnd ? bnd[uv.y] : 1.0f;
+            v[0] += fmaxf(bu, bv);
+            v[1] += fminf(bu, bv);
         }
-        double z = crew_sum(cw, xs, sm) / M;   // (the exchange orders the x writes before the gathers)
+        double o[2];
+        crew_sums(cw, v, o, sm);
+        if (threadIdx.x == 0) {
+            const double eta = B.eta_factor * log((double)(n + 1)) / eps;
+            cs.eta = eta; cs.eta_f = (float)eta; cs.cdf = (float)(1.0 / eta);
+            cs.thr = (float)(1.0 - B.grad_tol);
+            cs.x0 = (float)(eps / (double)E);
+            cs.hi = o[0]; cs.lo = o[1] / (double)E; cs.best = cs.lo;
+            cs.probes = 0; cs.iters = 0; cs.evals = 0; cs.passes = 0;
+        }
+        __syncthreads();
+    }
+    const double eta = cs.eta;
+    const float eta_f = cs.eta_f, thr = cs.thr, cd_f = cs.cdf, x0 = cs.x0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            cs.go = cs.hi > (1.0 + B.outer_tol) * cs.lo && cs.probes < B.max_probes;
+            if (cs.go) {
+                cs.M = sqrt(cs.lo * cs.hi);
+                cs.rho = (1.0 + B.outer_tol) * cs.M / cs.hi;   // the certificate closes the bracket (R12)
+                cs.invM = (float)(1.0 / cs.M);
+            }
+        }
+        __syncthreads();
+        if (!cs.go) break;
+        const float invM = cs.invM;
+        // a0: x_e = eps / (E max(1/b_u, 1/b_v)) = (eps / E) min(b_u, b_v), y = Px, z = 1^T x / M
+        {
+            double v[1] = {0.0};   // FP32 over runs of 8 edges, folded into FP64
+            float run = 0.0f;
+            int cnt = 0;
+            for (int64_t e = tid; e < E; e += S) {
+                const int2 uv = ed[e];
+                const float xe = x0 * (bnd ? fminf(bnd[uv.x], bnd[uv.y]) : 1.0f);
+                x[e] = xe;
+                run += xe;
+                if (++cnt == 8) { v[0] += (double)run; run = 0.0f; cnt = 0; }
+            }
+            v[0] += (double)run;
+            double o[1];
+            crew_sums(cw, v, o, sm);   // (the exchange orders the x writes before the gathers)
+            if (threadIdx.x == 0) cs.z = o[0] / cs.M;
+        }
         bt_rows(cw, vp, ei, bnd, x, y, n);
         // the probe's search state starts from zero in every block of the crew
         for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 8); i += NT) reinterpret_cast<long long *>(st)[i] = 0;
@@ -2845,83 +2977,101 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st, Crew<NT, C>
             st->eta = eta; st->eps = eps; st->c_d = 1.0 / eta; st->K = B.K; st->max_passes = B.max_passes;
             st->warm_start = B.warm_start; st->step_mode = B.step_mode; st->max_newton = B.max_newton;
             st->newton_tol = B.newton_tol; st->alpha_prev = 0.0; st->scale[0] = 1.0;
-            st->scale[1] = 1.0 / M; st->status = ST_RUNNING; st->reason = RS_NONE; st->iter = 0;
-            st->evals = 0; st->total_passes = 0;
+            st->scale[1] = 1.0 / cs.M; st->status = ST_RUNNING; st->reason = RS_NONE; st->iter = 0;
+            cs.it = 0;
+            cs.status = ST_RUNNING;
         }
         __syncthreads();
-        int status = ST_RUNNING;
-        int it = 0;
         for (;;) {
-            double sp, Sp;
-            bt_lse(cw, y, n, eta_f, sm, sp, Sp);   // (its exchange orders the y writes before the gathers)
+            float sp, Sp;
+            bt_lse(cw, y, n, eta_f, smf, sp, Sp);   // (its exchange orders the y writes before the gathers)
             // stopping tests before each iteration (Alg. 2, R8, R12), zmin = z (one exact row)
-            const double ymax = sp;
-            if (rho > 0.0 && z > 0.0 && ymax <= rho * z) { status = ST_FEASIBLE; break; }
-            if (z >= 1.0 || ymax > 1.0 + eps) { status = ymax <= (1.0 + eps) * z ? ST_FEASIBLE : ST_INFEASIBLE; break; }
-            if (it >= B.max_iter) { status = ST_MAX_ITER; break; }
-            // a4, a5: g_e = (w_u / b_u + w_v / b_v) / S_p, h_e = 1/M; d_e = c_d max(0, 1 - g/h) x_e
-            const float fp = (float)(1.0 / Sp), s_f = (float)sp;
-            double np = 0.0, ds = 0.0;
-            // four edges per thread and round: their endpoint and x loads, then
-            // the gathers of y and b, then the arithmetic
-            for (int64_t e0 = tid; e0 < E; e0 += 4 * S) {
-                int2 uv[4];
-                float xe[4], yu[4], yv[4], bu[4], bv[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int64_t e = e0 + r * S;
-                    uv[r] = e < E ? ed[e] : make_int2(0, 0);
-                    xe[r] = e < E ? x[e] : 0.0f;
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    yu[r] = gload<C>(y + uv[r].x);
-                    yv[r] = gload<C>(y + uv[r].y);
-                    bu[r] = bnd ? bnd[uv[r].x] : 1.0f;
-                    bv[r] = bnd ? bnd[uv[r].y] : 1.0f;
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int64_t e = e0 + r * S;
-                    if (e < E) {
-                        float wu = t_exp(eta_f * (yu[r] - s_f)), wv = t_exp(eta_f * (yv[r] - s_f));
-                        if (bnd) { wu /= bu[r]; wv /= bv[r]; }
-                        const float g = (wu + wv) * fp, h = invM;
-                        const float de = (g < thr * h) ? cd_f * (1.0f - g / h) * xe[r] : 0.0f;
-                        d[e] = de;
-                        np += de > 0.0f;
-                        ds += (double)de;
-                    }
-                }
-            }
-            crew_sum2(cw, np, ds, sm);   // (orders the d writes before the gathers of P d)
-            bt_rows(cw, vp, ei, bnd, d, dy, n);   // a6: dy = P d
             if (threadIdx.x == 0) {
-                st->phase = PH_DONE;
-                dir_finish(st, np, 0.0, ds);   // d = 0 -> INFEASIBLE, else the search starts
-                st->dense_v[1] = z;
-                s_go = st->status == ST_RUNNING ? 1 : 0;
+                const double ymax = sp, z = cs.z;
+                int stt = ST_RUNNING;
+                if (cs.rho > 0.0 && z > 0.0 && ymax <= cs.rho * z) stt = ST_FEASIBLE;
+                else if (z >= 1.0 || ymax > 1.0 + eps) stt = ymax <= (1.0 + eps) * z ? ST_FEASIBLE : ST_INFEASIBLE;
+                else if (cs.it >= B.max_iter) stt = ST_MAX_ITER;
+                cs.status = stt;
+                cs.go = stt == ST_RUNNING;
+                cs.fp = (float)(1.0 / (double)Sp);
+                cs.sf = sp;
+                cs.lnS = (double)logf(Sp);
             }
             __syncthreads();
-            if (!s_go) { status = ST_INFEASIBLE; break; }
-            const double dz = st->dense_dv[1];
+            if (!cs.go) break;
+            // a4, a5: g_e = (w_u / b_u + w_v / b_v) / S_p, h_e = 1/M; d_e = c_d max(0, 1 - g/h) x_e
+            const float fp = cs.fp, s_f = cs.sf;
+            {
+                float v[2] = {0.0f, 0.0f};   // count of d_e > 0, sum of d_e
+                // four edges per thread and round: their endpoint and x loads, then
+                // the gathers of y and b, then the arithmetic
+                for (int64_t ea = tid; ea < E; ea += 4 * S) {
+                    int2 uv[4];
+                    float xe[4], yu[4], yv[4], bu[4], bv[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int64_t e = ea + r * S;
+                        uv[r] = e < E ? ed[e] : make_int2(0, 0);
+                        xe[r] = e < E ? x[e] : 0.0f;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        yu[r] = gload<C>(y + uv[r].x);
+                        yv[r] = gload<C>(y + uv[r].y);
+                        bu[r] = bnd ? bnd[uv[r].x] : 1.0f;
+                        bv[r] = bnd ? bnd[uv[r].y] : 1.0f;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int64_t e = ea + r * S;
+                        if (e < E) {
+                            float wu = t_exp(eta_f * (yu[r] - s_f)), wv = t_exp(eta_f * (yv[r] - s_f));
+                            if (bnd) { wu /= bu[r]; wv /= bv[r]; }
+                            const float g = (wu + wv) * fp, h = invM;
+                            const float de = (g < thr * h) ? cd_f * (1.0f - g / h) * xe[r] : 0.0f;
+                            d[e] = de;
+                            v[0] += de > 0.0f ? 1.0f : 0.0f;
+                            v[1] += de;
+                        }
+                    }
+                }
+                double o[2];
+                crew_sums(cw, v, o, sm);   // (orders the d writes before the gathers of P d)
+                bt_rows(cw, vp, ei, bnd, d, dy, n);   // a6: dy = P d
+                if (threadIdx.x == 0) {
+                    st->phase = PH_DONE;
+                    dir_finish(st, o[0], 0.0, o[1]);   // d = 0 -> INFEASIBLE, else the search starts
+                    st->dense_v[1] = cs.z;
+                    cs.dz = st->dense_dv[1];
+                    cs.go = st->status == ST_RUNNING;
+                    cs.status = ST_INFEASIBLE;   // unless a step is accepted (the next stop test rewrites it)
+                    cs.acc = 0;
+                    cs.phase = st->phase;
+                    cs.kpass = st->kpass;
+                }
+                __syncthreads();
+                if (!cs.go) break;
+            }
             // a7: the step search over the packing rows (Phi_k = alpha_k dz, Phi' = dz
             // exactly): K-candidate passes (exponential phase, refinement), Newton
             // and backoff passes (one candidate with Psi'), the covering step
             for (int guard = 0; guard < 128; ++guard) {
-                const int phase = st->phase;
+                const int phase = cs.phase;
                 if (phase == PH_COVER) {   // the smallest step that covers the objective row
                     if (threadIdx.x == 0) {
+                        const double z = cs.z, dz = cs.dz;
                         const double ac = z >= 1.0 ? 0.0 : (dz > 0.0 ? (1.0 - z) / dz : (double)INFINITY);
                         st->passes += 1;
                         st->total_passes += 1;
                         search_finish(st, fmax(1.0, fmin(st->alpha[0], ac)));
+                        bt_step_end(cs, st);
                     }
                     __syncthreads();
                     break;
                 }
                 const bool nwt = phase == PH_NEWTON || phase == PH_BACKOFF;
-                const int K = nwt ? 1 : st->kpass;
+                const int K = nwt ? 1 : cs.kpass;
                 if (threadIdx.x < KMAX) {
                     const double a = threadIdx.x < K ? st->alpha[threadIdx.x] : 0.0;
                     s_al[threadIdx.x] = (float)a;
@@ -2958,51 +3108,23 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st, Crew<NT, C>
                     }
                 }
                 __syncthreads();
-                __shared__ double s_psi[KMAX], s_dpsi;
-                double *sl = nullptr;
-                if constexpr (C > 1) sl = cw.next();
-                if (threadIdx.x < K) {
-                    const int k = threadIdx.x;
-                    double mx = 0.0, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
-                    for (int w = 0; w < NT / 32; ++w)
-                        cand_merge1d<float, double>(mx, R, Tt, zm, D, wrec[w][k][0], wrec[w][k][1], wrec[w][k][2],
-                                                    wrec[w][k][3], k == 0 ? (double)wD[w] : 0.0, 1);
-                    brec[k][0] = mx; brec[k][1] = R; brec[k][2] = Tt; brec[k][3] = zm; brec[k][4] = D;
-                    if constexpr (C > 1) {
-                        double *o = sl + 5 * k;
-                        o[0] = mx; o[1] = R; o[2] = Tt; o[3] = zm; o[4] = D;
+                {
+                    float mx, R, Tt, zm, D;
+                    bt_cand_reduce(cw, wrec, wD, K, mx, R, Tt, zm, D);
+                    const int l = threadIdx.x & 31, k = l >> 2;
+                    if (threadIdx.x < 32 && (l & 3) == 0 && k < K) {
+                        // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p) (Sec. 4.1);
+                        // the transcendentals in FP32, the combination in FP64
+                        const double lS = cs.lnS;
+                        const double lq = (double)mx + (double)logf(Tt) - lS;
+                        s_psi[k] = (lq < 0.0) ? (double)log1pf(expf((float)lq)) / eta
+                                              : ((double)mx + (double)logf(R) - lS) / eta;
+                        if (k == 0) s_dpsi = R > 0.0f ? (double)D / (double)R : 0.0;   // Psi' (Sec. 4.2)
                     }
-                }
-                if constexpr (C > 1) {
-                    cluster_barrier();
-                    if (threadIdx.x < K) {   // the C blocks' records of candidate k, in rank order
-                        const int k = threadIdx.x;
-                        const double *o = sl + 5 * k;
-                        double r[C][5];
-#pragma unroll
-                        for (int q = 0; q < C; ++q)
-#pragma unroll
-                            for (int f = 0; f < 5; ++f) r[q][f] = ld_peer(o + f, q);
-                        double mx = 0.0, R = 0.0, Tt = 0.0, zm = (double)INFINITY, D = 0.0;
-#pragma unroll
-                        for (int q = 0; q < C; ++q)
-                            cand_merge1d<float, double>(mx, R, Tt, zm, D, r[q][0], r[q][1], r[q][2], r[q][3], r[q][4], 1);
-                        brec[k][0] = mx; brec[k][1] = R; brec[k][2] = Tt; brec[k][3] = zm; brec[k][4] = D;
-                    }
-                }
-                if (threadIdx.x < K) {
-                    const int k = threadIdx.x;
-                    const double mx = brec[k][0], R = brec[k][1], Tt = brec[k][2], D = brec[k][4];
-                    // Psi = (1/eta) ln(R_true / S_p) = (1/eta) ln(1 + T_true / S_p) (Sec. 4.1);
-                    // the transcendentals in FP32 (as the FP32 form's passes take them), the
-                    // combination in FP64
-                    const double lS = (double)logf((float)Sp);
-                    const double lq = mx + (double)logf((float)Tt) - lS;
-                    s_psi[k] = (lq < 0.0) ? (double)log1pf(expf((float)lq)) / eta : (mx + (double)logf((float)R) - lS) / eta;
-                    if (k == 0) s_dpsi = R > 0.0 ? D / R : 0.0;   // Psi' (Sec. 4.2): both sums share the shift
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {
+                    const double z = cs.z, dz = cs.dz;
                     int ok[KMAX];
                     double zmk[KMAX];
                     for (int k = 0; k < K; ++k) {
@@ -3021,49 +3143,59 @@ __device__ void bt_solve(const BatchDesc &B, int inst, DevState *st, Crew<NT, C>
                     } else {
                         search_decide(st, ok, zmk);
                     }
-                    s_go = (st->status == ST_RUNNING && st->phase != PH_DONE) ? 1 : 0;
+                    cs.go = (st->status == ST_RUNNING && st->phase != PH_DONE) ? 1 : 0;
+                    cs.phase = st->phase;
+                    cs.kpass = st->kpass;
+                    if (!cs.go) bt_step_end(cs, st);
                 }
                 __syncthreads();
-                if (!s_go) break;
+                if (!cs.go) break;
             }
-            if (st->status != ST_RUNNING || !(st->alpha_acc >= 1.0)) { status = ST_INFEASIBLE; break; }
-            // a8: x += alpha d, y += alpha dy, z += alpha dz
-            const double alpha = st->alpha_acc;
-            const float af = (float)alpha;
+            // a8: x += alpha d, y += alpha dy (z += alpha dz in bt_step_end); a search
+            // that accepted no step >= 1 (or ran out of passes) ends the probe infeasible
+            if (!cs.acc) break;
+            const float af = cs.af;
             for (int64_t e = tid; e < E; e += S) x[e] = fmaf(af, d[e], x[e]);
             for (int64_t w = tid; w < n; w += S) y[w] = fmaf(af, dy[w], y[w]);
-            z += alpha * dz;
-            ++it;
-            __syncthreads();
-            if (threadIdx.x == 0) { st->alpha_prev = alpha; st->iter = it; }
         }
-        __syncthreads();
-        evals += st->evals;
-        passes += st->total_passes;
-        iters += it;
-        ++probes;
         // certificate of the probe's x: 1^T x / max(Px), with y recomputed from x
-        double sx = 0.0;
-        for (int64_t e = tid; e < E; e += S) sx += (double)x[e];
-        sx = crew_sum(cw, sx, sm);   // (orders the last x writes before the gathers)
+        double v[1] = {0.0};   // FP32 over runs of 8 edges, folded into FP64
+        {
+            float run = 0.0f;
+            int cnt = 0;
+            for (int64_t e = tid; e < E; e += S) {
+                run += x[e];
+                if (++cnt == 8) { v[0] += (double)run; run = 0.0f; cnt = 0; }
+            }
+            v[0] += (double)run;
+        }
+        double o[1];
+        crew_sums(cw, v, o, sm);   // (orders the last x writes before the gathers)
         bt_rows(cw, vp, ei, bnd, x, y, n);
         __syncthreads();
-        double ym = 0.0;
-        for (int64_t w = tid; w < n; w += S) ym = fmax(ym, (double)y[w]);
-        ym = crew_max(cw, ym, sm);
-        const double cert = ym > 0.0 ? sx / ym : 0.0;
-        best = fmax(best, cert);
-        lo = fmax(lo, cert);
-        if (status == ST_FEASIBLE) lo = fmax(lo, M);
-        else hi = fmin(hi, M);
+        float ym = 0.0f;
+        for (int64_t w = tid; w < n; w += S) ym = fmaxf(ym, y[w]);
+        ym = crew_max(cw, ym, smf);
+        if (threadIdx.x == 0) {
+            cs.evals += st->evals;
+            cs.passes += st->total_passes;
+            cs.iters += cs.it;
+            cs.probes += 1;
+            const double cert = ym > 0.0f ? o[0] / (double)ym : 0.0;
+            cs.best = fmax(cs.best, cert);
+            cs.lo = fmax(cs.lo, cert);
+            if (cs.status == ST_FEASIBLE) cs.lo = fmax(cs.lo, cs.M);
+            else cs.hi = fmin(cs.hi, cs.M);
+        }
         __syncthreads();
     }
     if (cw.rank == 0 && threadIdx.x == 0) {
-        B.obj[inst] = best;
-        B.iters[inst] = iters;
-        B.probes[inst] = probes;
-        B.evals[inst] = evals;
-        B.passes[inst] = passes;
+        B.obj[inst] = cs.best;
+        B.iters[inst] = cs.iters;
+        B.probes[inst] = cs.probes;
+        B.evals[inst] = cs.evals;
+        B.passes[inst] = cs.passes;
+        B.t_end[inst] = (int64_t)globaltimer_ns();
     }
 }
 
@@ -3085,7 +3217,10 @@ template <int NT> __device__ void bt_alone(const BatchDesc &B, DevState *st, dou
 template <int NT, int C>
 __global__ void __launch_bounds__(NT) k_batch_solve(BatchDesc B) {
     __shared__ double slot[2 * XS];
-    DevState *st = B.st + blockIdx.x;
+    // the search state lives in shared memory: thread 0's decision rules touch
+    // it dozens of times per pass, each a dependent access
+    __shared__ DevState st_sh;
+    DevState *st = &st_sh;
     if constexpr (C > 1) {
         // the cluster's instances: rank 0 takes the next from queue[0] and
         // publishes it; all C blocks solve it together
@@ -3106,8 +3241,6 @@ __global__ void __launch_bounds__(NT) k_batch_solve(BatchDesc B) {
     }
     bt_alone<NT>(B, st, slot);
 }
-
-int batch_cluster_edges(int nt, int cl) { return cl > 1 ? 8 * nt * cl : 0x7fffffff; }
 
 template <int NT, int C> static cudaError_t batch_launch_cfg(const BatchDesc &B, int blocks, cudaStream_t s) {
     if constexpr (C == 1) {
@@ -3146,6 +3279,11 @@ template <int NT, int C> static int batch_blocks_cfg(int n_sms) {
         cfg.blockDim = dim3(NT);
         cfg.attrs = at;
         cfg.numAttrs = 1;
+        if (C > 8 && cudaFuncSetAttribute(k_batch_solve<NT, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                         cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
         int ncl = 0;
         if (cudaOccupancyMaxActiveClusters(&ncl, k_batch_solve<NT, C>, &cfg) != cudaSuccess) {
             cudaGetLastError();
@@ -3155,7 +3293,8 @@ template <int NT, int C> static int batch_blocks_cfg(int n_sms) {
     }
 }
 
-#define MWU_BATCH_CFGS(X) X(256, 1) X(512, 1) X(1024, 1) X(256, 4) X(512, 4) X(256, 8) X(512, 8)
+#define MWU_BATCH_CFGS(X) \
+    X(256, 1) X(512, 1) X(1024, 1) X(256, 4) X(512, 4) X(256, 8) X(512, 8) X(256, 16) X(512, 16)
 
 cudaError_t launch_batch_solve(const BatchDesc &Bin, int nt, int cl, int n_cluster, int blocks, cudaStream_t s) {
     BatchDesc B = Bin;

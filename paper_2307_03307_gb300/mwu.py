@@ -44,7 +44,8 @@ class mwu_options(C.Structure):
                 ("stop_rule", C.c_int32), ("grad_tol", C.c_double), ("stream", C.c_void_p),
                 ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("batch_workers", C.c_int32),
                 ("drop_covered", C.c_int32), ("spmv_tiles", C.c_int32), ("h_scatter", C.c_int32),
-                ("dv_scatter", C.c_int32), ("col_split", C.c_int32), ("batch_cluster", C.c_int32)]
+                ("dv_scatter", C.c_int32), ("col_split", C.c_int32), ("batch_cluster", C.c_int32),
+                ("batch_cluster_edges", C.c_int32)]
 
 
 class mwu_iter_stats(C.Structure):
@@ -122,6 +123,7 @@ def load(path: str = LIB_PATH):
         "mwu_solve_batch": (C.c_int, [V, P(D), P(I64), P(mwu_result)]),
         "mwu_batch_tuning": (C.c_int, [V, P(I32), P(I32), P(D)]),
         "mwu_batch_stats": (C.c_int, [V, P(I64), P(I32)]),
+        "mwu_batch_timeline": (C.c_int, [V, P(D), P(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -138,6 +140,7 @@ def exported_symbols():
             "mwu_solve",
             "mwu_get_vector", "mwu_get_scalars", "mwu_get_timing", "mwu_spmv_tiles", "mwu_potential", "mwu_check_values",
             "mwu_candidates_static", "mwu_create_batch", "mwu_solve_batch", "mwu_batch_tuning", "mwu_batch_stats",
+            "mwu_batch_timeline",
             "mwu_diag_one_minus_exp_neg"]
 
 
@@ -391,7 +394,7 @@ def mwu_solve_batch(ctx, count):
 
 
 # the autotuner's (threads per block, blocks per cluster), in mwu_batch_tuning's order
-BATCH_TUNE_CONFIGS = ((256, 1), (512, 1), (1024, 1), (256, 4), (512, 4), (256, 8), (512, 8))
+BATCH_TUNE_CONFIGS = ((256, 1), (512, 1), (1024, 1), (256, 4), (512, 4), (256, 8), (512, 8), (256, 16), (512, 16))
 
 
 def mwu_batch_tuning(ctx):
@@ -401,6 +404,14 @@ def mwu_batch_tuning(ctx):
     ms = (C.c_double * len(BATCH_TUNE_CONFIGS))()
     _check(ctx, load().mwu_batch_tuning(ctx, C.byref(nt), C.byref(cl), ms))
     return nt.value, cl.value, list(ms)
+
+
+def mwu_batch_timeline(ctx, count):
+    """Per-instance (start ms, end ms) of the last batch solve, after the earliest start."""
+    a = (C.c_double * count)()
+    b = (C.c_double * count)()
+    _check(ctx, load().mwu_batch_timeline(ctx, a, b))
+    return list(a), list(b)
 
 
 def mwu_batch_stats(ctx, count):

@@ -81,16 +81,17 @@ def test_batch_from_host_arrays_and_autotuner(M):
     assert obj == obj2 and it == it2                         # host or device inputs, same solve
 
 
-@pytest.mark.parametrize("nt,cl,step", [(256, 4, "kary"), (512, 8, "newton"), (256, 8, "kary")])
+@pytest.mark.parametrize("nt,cl,step", [(256, 4, "kary"), (512, 8, "newton"), (256, 8, "kary"), (512, 16, "newton")])
 def test_cluster_batch_equals_alone_and_exact(M, nt, cl, step):
-    """Instances of at least 8 * nt * cl edges are solved by a whole cluster
-    (sums combined across its blocks in rank order), the rest by one block;
-    either way the batch changes nothing and the objective is certified."""
+    """Instances of at least batch_cluster_edges edges are solved by a whole
+    cluster (sums combined across its blocks in a fixed tree), the rest by one
+    block; either way the batch changes nothing and the objective is certified."""
     insts = W.bmatching_batch(count=8, seed=11, lo=2e3, hi=8e4)
-    thr = 8 * nt * cl
+    thr = 16384
     assert any(w.graph.m >= thr for w in insts) and any(w.graph.m < thr for w in insts)
     st = M.STEP_NEWTON if step == "newton" else M.STEP_KARY
-    ctx = M.mwu_create_batch(_mats(insts), batch_workers=nt, batch_cluster=cl, step=st)
+    opts = dict(batch_workers=nt, batch_cluster=cl, batch_cluster_edges=thr, step=st)
+    ctx = M.mwu_create_batch(_mats(insts), **opts)
     try:
         obj_b, it_b, tot = M.mwu_solve_batch(ctx, len(insts))
         obj_2, it_2, _ = M.mwu_solve_batch(ctx, len(insts))
@@ -99,7 +100,7 @@ def test_cluster_batch_equals_alone_and_exact(M, nt, cl, step):
         M.mwu_destroy(ctx)
     assert obj_b == obj_2 and it_b == it_2 and tot["launches"] == 1
     for k, wl in enumerate(insts):
-        c1 = M.mwu_create_batch(_mats([wl]), batch_workers=nt, batch_cluster=cl, step=st)
+        c1 = M.mwu_create_batch(_mats([wl]), **opts)
         try:
             o1, i1, _ = M.mwu_solve_batch(c1, 1)
         finally:
