@@ -49,6 +49,8 @@ UNIT = "edges*iters/s"
 WORKLOADS = {
     "vcover-rmat24": ("vcover", "vertex cover, M^T x >= 1 implicit (R-MAT 24, seed 5), K = 8 candidates per pass",
                       "kary", "f32"),
+    "vcover-rmat21": ("vcover", "vertex cover, M^T x >= 1 implicit (R-MAT 21, seed 5), K = 8 candidates per pass; "
+                                "the profiling-size case of the same kernels", "kary", "f32"),
     "densest-rmat18": ("densest", "densest subgraph, Charikar dual W z >= 1, O z <= D (R-MAT 18, seed 2)",
                        "newton", "f32"),
     "domset-rmat20": ("domset", "weighted dominating set, (I + A) x >= 1 explicit CSR (R-MAT 20, seed 3)",
@@ -313,6 +315,7 @@ def roofline(ab, tim, workload):
 def make_workload(name, device):
     from graphgen import workloads as W
     return {"vcover-rmat24": lambda: W.vcover(24, seed=5, device=device),
+            "vcover-rmat21": lambda: W.vcover(21, seed=5, device=device),
             "densest-rmat18": lambda: W.densest(18, seed=2, device=device),
             "domset-rmat20": lambda: W.domset(20, seed=3, device=device),
             "bmatch-2k": lambda: W.bmatch(device=device),

@@ -150,8 +150,16 @@ typedef struct {
                                   of the loop of Alg. 1 and Alg. 2 (C <- {c_j : c_j^T x < 1}):
                                   a row with (Cx)_j >= 1 leaves smin, h, Phi and Phi'.  x
                                   never decreases, so the active rows are those with
-                                  (Cx)_j < 1.  0 (default): every row is kept, as the
-                                  paper's implementation does (Sec. 4)                     */
+                                  (Cx)_j < 1.  On the vertex-cover split view the rows are
+                                  also compacted: inside one mwu_iterate call, whenever
+                                  the unsatisfied edges are at most 70 % of the current
+                                  rows, a stable stream compaction keeps only them for the
+                                  SpMV dz = Cd, the candidate passes and the update (the
+                                  direction still reads every column); the call restores
+                                  the full rows, with z = Cx, before it returns.  2: the
+                                  same dropping without compaction (rows masked in place).
+                                  0 (default): every row is kept, as the paper's
+                                  implementation does (Sec. 4)                             */
     int32_t spmv_tiles;        /* forward SpMV of an explicit or incidence CSR side: 0
                                   (default) stages each tile of rows' input window in
                                   shared memory when the columns of 90 % of the tiles
@@ -236,6 +244,7 @@ typedef struct {
     double update_ms;          /* y, z update with the next iteration's reductions           */
     int64_t iters;             /* iterations timed                                           */
     int64_t cand_passes;       /* candidate passes that evaluated candidates                 */
+    int64_t compactions;       /* active-row compactions (drop_covered = 1, split view)      */
 } mwu_timing;
 
 typedef struct {

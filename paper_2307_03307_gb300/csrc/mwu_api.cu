@@ -48,6 +48,20 @@ struct mwu_ctx {
     const float *objective = nullptr;
     cudaGraphExec_t gexec_chunk = nullptr;   // check_every iterations
     cudaGraphExec_t gexec_one = nullptr;     // one iteration
+    // active-row compaction (drop_covered = 1 on the vertex-cover split view):
+    // inside one mwu_iterate call the covering side's rows shrink to the
+    // unsatisfied edges (two buffer sets, used in turn); the call restores
+    // the full rows before it returns
+    bool cmp_ok = false, cmp_on = false;
+    int cmp_buf = 0;
+    int32_t *cmp_pairs[2] = {nullptr, nullptr}, *cmp_orig[2] = {nullptr, nullptr};
+    void *cmp_v[2] = {nullptr, nullptr};
+    void *cmp_dv = nullptr;
+    int32_t *cmp_tile = nullptr;
+    int64_t *cmp_total = nullptr;
+    Side<float> cmp_full_f{};
+    Side<double> cmp_full_d{};
+    cudaGraphExec_t gexec_chunk_c = nullptr, gexec_one_c = nullptr;   // graphs of the compacted rows
     std::vector<cudaEvent_t> ev;             // 4 per iteration of the chunk graph (timing)
     std::vector<cudaEvent_t> ev_one;         // 4 for the one-iteration graph
     mwu_timing tim{};
@@ -487,6 +501,7 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         return fail(nullptr, MWU_ERR_INVALID, "unknown precision");
     if (o.step < MWU_STEP_KARY || o.step > MWU_STEP_NEWTON) return fail(nullptr, MWU_ERR_INVALID, "unknown step mode");
     if (o.max_newton < 0) return fail(nullptr, MWU_ERR_INVALID, "max_newton must be >= 0");
+    if (o.drop_covered < 0 || o.drop_covered > 2) return fail(nullptr, MWU_ERR_INVALID, "drop_covered must be 0, 1 or 2");
 
     mwu_ctx *c = new mwu_ctx();
     c->kind = kind;
@@ -595,7 +610,7 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
     if (cp0 || cp1) {
         int lq = 1;
         cudaError_t e = length_quantile2(c->ar, cp0, cp1, c->n, 0.75, &lq, c->stream);
-        if (e != cudaSuccess) { fail_cuda(c, e, "column length quantile"); return bail(MWU_ERR_CUDA); }
+        if (e != cudaSuccess) return bail(fail_cuda(c, e, "column length quantile"));
         G_var = c->opt.group > 0 ? c->opt.group : std::max(1, std::min(32, pow2_ceil((lq + 3) / 4)));
         const int light = std::min(16 * G_var, HEAVY_LEN);
         for (int s = 0; s < 2; ++s)
@@ -606,14 +621,14 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         const int heavy = (sb[1].cv.kind == CK_SPLIT2 && !cp0) ? SPLIT_HEAVY : HEAVY_LEN;
         e = heavy_list2(c->ar, cp0, heavy, cp1, heavy, c->n, &hv, &nhv, c->stream);
         if (e == cudaSuccess) e = range_list2(c->ar, cp0, cp1, c->n, light, std::max(light, heavy), &mv, &nmv, c->stream);
-        if (e != cudaSuccess) { fail_cuda(c, e, "variable length classes"); return bail(MWU_ERR_CUDA); }
+        if (e != cudaSuccess) return bail(fail_cuda(c, e, "variable length classes"));
         if (sb[1].cv.kind == CK_SPLIT2 && nhv > 0 && (rc = split_segments(c, sb[1].cv, hv, nhv)) != MWU_OK)
             return bail(rc);
         if (sb[1].cv.kind == CK_SPLIT2 && !cp0) {   // split view: tiny and light variable lists
             const int lt = std::min(light, SPLIT_HEAVY);
             e = range_list2(c->ar, nullptr, cp1, c->n, -1, SPLIT_TINY, &tv, &ntv, c->stream);
             if (e == cudaSuccess) e = range_list2(c->ar, nullptr, cp1, c->n, SPLIT_TINY, lt, &lv, &nlv, c->stream);
-            if (e != cudaSuccess) { fail_cuda(c, e, "variable length classes"); return bail(MWU_ERR_CUDA); }
+            if (e != cudaSuccess) return bail(fail_cuda(c, e, "variable length classes"));
         }
     }
     // device state
@@ -640,6 +655,35 @@ int mwu_create(int32_t kind, const mwu_matrix *P, const mwu_matrix *C, const flo
         c->pf.n_tiny_var = ntv; c->pf.tiny_var = tv; c->pf.n_light_var = nlv; c->pf.light_var = lv;
     }
     if (rc != MWU_OK) return bail(rc);
+    // active-row compaction: drop_covered = 1 on a covering side of edge rows
+    // in the split view (vertex cover); two buffer sets of pairs, z and row
+    // numbers, one dz, the tile offsets
+    {
+        const Side<float> &s1f = c->pf.side[1];
+        const Side<double> &s1d = c->pd.side[1];
+        const int32_t ck = c->fp64 ? s1d.cv.kind : s1f.cv.kind, rk = c->fp64 ? s1d.rv.kind : s1f.rv.kind;
+        const int64_t m1 = c->fp64 ? s1d.m : s1f.m;
+        if (o.drop_covered == 1 && ck == CK_SPLIT2 && rk == RK_FIXED2 && !o.h_scatter && m1 > 0) {
+            const size_t ts = c->fp64 ? sizeof(double) : sizeof(float);
+            bool ok = true;
+            for (int b = 0; b < 2; ++b) {
+                c->cmp_pairs[b] = c->ar.alloc<int32_t>(2 * m1);
+                c->cmp_orig[b] = c->ar.alloc<int32_t>(m1);
+                c->cmp_v[b] = c->ar.raw((size_t)m1 * ts);
+                ok = ok && c->cmp_pairs[b] && c->cmp_orig[b] && c->cmp_v[b];
+            }
+            c->cmp_dv = c->ar.raw((size_t)m1 * ts);
+            c->cmp_tile = c->ar.alloc<int32_t>(cmp_tiles(m1) + 1);
+            c->cmp_total = c->ar.alloc<int64_t>(1);
+            if (!ok || !c->cmp_dv || !c->cmp_tile || !c->cmp_total) {
+                c->err = "allocating the compaction buffers";
+                return bail(MWU_ERR_OOM);
+            }
+            c->cmp_ok = true;
+            c->cmp_full_f = s1f;
+            c->cmp_full_d = s1d;
+        }
+    }
     c->x_best = c->ar.raw((size_t)c->n * (c->fp64 ? sizeof(double) : sizeof(float)));
     if (!c->x_best) { c->err = "allocating best x"; return bail(MWU_ERR_OOM); }
     c->ar.release_tmp();
@@ -659,6 +703,8 @@ void mwu_destroy(mwu_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->gexec_chunk) cudaGraphExecDestroy(c->gexec_chunk);
     if (c->gexec_one) cudaGraphExecDestroy(c->gexec_one);
+    if (c->gexec_chunk_c) cudaGraphExecDestroy(c->gexec_chunk_c);
+    if (c->gexec_one_c) cudaGraphExecDestroy(c->gexec_one_c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_one) cudaEventDestroy(e);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -987,6 +1033,15 @@ static cudaError_t enqueue_search(mwu_ctx *c, Prob &p, bool loop) {
     return e1 != cudaSuccess ? e1 : e2;
 }
 
+// The direction kernels read the covering side through its column view, whose
+// split form streams z by the full edge order: with compacted rows they get
+// the full z (the update keeps it current for the active edges).
+template <class P> static P dir_view(const P &p) {
+    P q = p;
+    if (q.side[1].orig) q.side[1].v = q.side[1].vfull;
+    return q;
+}
+
 static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev, bool loop = false) {
     return with_prob(c, [&](auto &p0) -> cudaError_t {
         cudaError_t e;
@@ -1000,7 +1055,7 @@ static cudaError_t enqueue_iteration(mwu_ctx *c, cudaEvent_t *ev, bool loop = fa
             p.cond_on = 1;
         }
         if (ev && (e = cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = launch_dir(p, 0, c->stream)) != cudaSuccess) return e;
+        if ((e = launch_dir(dir_view(p), 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = spmv_direction(p, 0, c->stream)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
@@ -1040,9 +1095,87 @@ static int capture(mwu_ctx *c, int iters, std::vector<cudaEvent_t> &ev, cudaGrap
 
 static int ensure_graphs(mwu_ctx *c) {
     int rc;
-    if (!c->gexec_chunk && (rc = capture(c, c->opt.check_every, c->ev, &c->gexec_chunk)) != MWU_OK) return rc;
-    if (!c->gexec_one && (rc = capture(c, 1, c->ev_one, &c->gexec_one)) != MWU_OK) return rc;
+    cudaGraphExec_t &gc = c->cmp_on ? c->gexec_chunk_c : c->gexec_chunk;
+    cudaGraphExec_t &g1 = c->cmp_on ? c->gexec_one_c : c->gexec_one;
+    if (!gc && (rc = capture(c, c->opt.check_every, c->ev, &gc)) != MWU_OK) return rc;
+    if (!g1 && (rc = capture(c, 1, c->ev_one, &g1)) != MWU_OK) return rc;
     return MWU_OK;
+}
+
+// ------------------------------------------------------------ active-row compaction
+// Between graph launches (or iterations of the plain form) of one mwu_iterate
+// call: count the unsatisfied covering rows (z < act_hi) of the current rows
+// and, once they are at most CMP_KEEP of them, compact the edge pairs, z and
+// the original row numbers into the other buffer set.  x only grows within a
+// probe, so a dropped row stays satisfied.
+constexpr double CMP_KEEP = 0.7;
+
+template <class T> static int compact_rows(mwu_ctx *c, Problem<T> &p, const Side<T> &full) {
+    Side<T> &sd = p.side[1];
+    const int64_t m = sd.m;
+    if (m <= 0) return MWU_OK;
+    const double hi = c->st_host->act_hi;
+    TRY_CUDA(c, launch_cmp_count<T>(sd.v, m, hi, c->cmp_tile, c->cmp_total, c->stream));
+    int64_t total = 0;
+    TRY_CUDA(c, cudaMemcpyAsync(&total, c->cmp_total, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->launches += 2;
+    if (total <= 0 || (double)total > CMP_KEEP * (double)m) return MWU_OK;
+    const int nb = c->cmp_on ? 1 - c->cmp_buf : 0;
+    TRY_CUDA(c, launch_cmp_scatter<T>(sd.rv.idx, sd.v, sd.orig, m, hi, c->cmp_tile, c->cmp_pairs[nb],
+                                      (T *)c->cmp_v[nb], c->cmp_orig[nb], c->stream));
+    c->launches += 1;
+    sd.rv.idx = c->cmp_pairs[nb];
+    sd.rv.rows = total;
+    sd.rv.nnz = 2 * total;
+    sd.m = total;
+    sd.v = (T *)c->cmp_v[nb];
+    sd.dv = (T *)c->cmp_dv;
+    sd.orig = c->cmp_orig[nb];
+    sd.vfull = full.v;
+    c->cmp_buf = nb;
+    c->cmp_on = true;
+    c->tim.compactions += 1;
+    if (c->gexec_chunk_c) { cudaGraphExecDestroy(c->gexec_chunk_c); c->gexec_chunk_c = nullptr; }
+    if (c->gexec_one_c) { cudaGraphExecDestroy(c->gexec_one_c); c->gexec_one_c = nullptr; }
+    if (c->trace)
+        std::fprintf(stderr, "[mwu] compaction: %lld of %lld covering rows active (iteration %d)\n", (long long)total,
+                     (long long)m, c->st_host->iter);
+    return MWU_OK;
+}
+
+static int maybe_compact(mwu_ctx *c) {
+    if (!c->cmp_ok || c->st_host->status != ST_RUNNING) return MWU_OK;
+    return c->fp64 ? compact_rows(c, c->pd, c->cmp_full_d) : compact_rows(c, c->pf, c->cmp_full_f);
+}
+
+// Back to the full rows: z = x_u + x_v over every edge (the rows dropped
+// earlier hold their value at drop time), and a probe that stopped on the
+// bound act_hi for the dropped rows' minimum re-runs the stopping test on the
+// exact min z over every row.
+template <class T> static int expand_rows(mwu_ctx *c, Problem<T> &p, const Side<T> &full) {
+    p.side[1] = full;
+    c->cmp_on = false;
+    TRY_CUDA(c, launch_cmp_refresh<T>(p, c->stream));
+    c->launches += 1;
+    int rc = pull_state(c);
+    if (rc != MWU_OK) return rc;
+    DevState &h = *c->st_host;
+    if (h.reason == RS_RATIO || h.reason == RS_COVERED || h.reason == RS_PACKING) {
+        h.status = ST_RUNNING;
+        h.reason = RS_NONE;
+        TRY_CUDA(c, cudaMemcpyAsync(&c->st_dev->status, &h.status, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        TRY_CUDA(c, cudaMemcpyAsync(&c->st_dev->reason, &h.reason, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        TRY_CUDA(c, launch_rows_reduce<T>(p, c->stream));
+        c->launches += 1;
+        if ((rc = pull_state(c)) != MWU_OK) return rc;
+    }
+    return MWU_OK;
+}
+
+static int cmp_expand(mwu_ctx *c) {
+    if (!c->cmp_on) return MWU_OK;
+    return c->fp64 ? expand_rows(c, c->pd, c->cmp_full_d) : expand_rows(c, c->pf, c->cmp_full_f);
 }
 
 // add the event times of the first `real` iterations recorded in ev
@@ -1074,13 +1207,11 @@ static void fill_stats(mwu_ctx *c, mwu_iter_stats *s) {
     s->zmin = h.zmin;
 }
 
-int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
-    if (!c || n_iters < 0) return MWU_ERR_INVALID;
+static int iterate_loop(mwu_ctx *c, int32_t n_iters) {
     int rc = pull_state(c);
     if (rc != MWU_OK) return rc;
     c->have_direction = false;
     const bool graph = !c->fp64 && c->opt.use_graph;
-    if (graph && (rc = ensure_graphs(c)) != MWU_OK) return rc;
     const int kpi = kernels_per_iteration(c);
     int done = 0;
     while (done < n_iters && c->st_host->status == ST_RUNNING) {
@@ -1092,7 +1223,7 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             std::vector<cudaEvent_t> &ev = c->ev_one;
             if (c->opt.timing && (rc = make_events(c, ev, EV_PER_IT)) != MWU_OK) return rc;
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[0], c->stream));
-            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(p, 0, c->stream); }));
+            TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_dir(dir_view(p), 0, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[1], c->stream));
             TRY_CUDA(c, with_prob(c, [&](auto &p) { return spmv_direction(p, 0, c->stream); }));
             if (c->opt.timing) TRY_CUDA(c, cudaEventRecord(ev[2], c->stream));
@@ -1119,9 +1250,12 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             if (c->opt.timing && (rc = accumulate_timing(c, ev, c->st_host->iter - iter0)) != MWU_OK) return rc;
             done += 1;
         } else if (graph) {
+            if ((rc = ensure_graphs(c)) != MWU_OK) return rc;
             bool chunk = n_iters - done >= c->opt.check_every;
             int n = chunk ? c->opt.check_every : 1;
-            TRY_CUDA(c, cudaGraphLaunch(chunk ? c->gexec_chunk : c->gexec_one, c->stream));
+            cudaGraphExec_t gx = chunk ? (c->cmp_on ? c->gexec_chunk_c : c->gexec_chunk)
+                                       : (c->cmp_on ? c->gexec_one_c : c->gexec_one);
+            TRY_CUDA(c, cudaGraphLaunch(gx, c->stream));
             if ((rc = pull_state(c)) != MWU_OK) return rc;
             // direction, SpMV and update per captured iteration, plus the kernels
             // the search loops ran (counted on the device)
@@ -1138,7 +1272,17 @@ int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
             done += n;
         }
         c->tim.cand_passes += c->st_host->total_passes - passes0;
+        if ((rc = maybe_compact(c)) != MWU_OK) return rc;
     }
+    return MWU_OK;
+}
+
+int mwu_iterate(mwu_ctx *c, int32_t n_iters, mwu_iter_stats *stats) {
+    if (!c || n_iters < 0) return MWU_ERR_INVALID;
+    int rc = iterate_loop(c, n_iters);
+    const int rc2 = cmp_expand(c);   // the full rows again (exact z, the stopping test re-decided)
+    if (rc != MWU_OK) return rc;
+    if (rc2 != MWU_OK) return rc2;
     TRY_CUDA(c, with_prob(c, [&](auto &p) { return launch_flush(p, c->stream); }));
     c->launches += 1;
     if ((rc = pull_state(c)) != MWU_OK) return rc;
@@ -1726,7 +1870,7 @@ int mwu_create_batch(int32_t count, const mwu_matrix *P, const mwu_options *opt,
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             }
         }
-        if (e != cudaSuccess) { fail_cuda(c, e, "packing a batch instance"); return bail(MWU_ERR_CUDA); }
+        if (e != cudaSuccess) return bail(fail_cuda(c, e, "packing a batch instance"));
         c->ar.release_tmp();
     }
     if (validate_positive(bound, Nt, 7, d_err, s) != cudaSuccess) { c->err = "validating bounds"; return bail(MWU_ERR_CUDA); }

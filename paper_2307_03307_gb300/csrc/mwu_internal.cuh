@@ -121,6 +121,13 @@ struct Side {
     T *v;            // y or z (nullptr for DENSE1)
     T *dv;           // dy or dz
     T *seg_part;     // per-segment partial sums of long CSR rows
+    // compacted covering side (drop_covered on the vertex-cover split view):
+    // rows j < m are the active edges, orig[j] their row in the full edge
+    // list, vfull the full z that the direction's split view reads (the update
+    // writes vfull[orig[j]] = v[j]; the rows dropped earlier keep their last
+    // value, >= 1).  nullptr when the side is not compacted.
+    const int32_t *orig = nullptr;
+    T *vfull = nullptr;
 };
 
 // Probe status values stored on the device.
@@ -295,4 +302,19 @@ template <class T> int spmv_blocks_per_sm();
 template <class T> int newton_blocks_per_sm();
 template <class T> int tiled_blocks_per_sm();
 
+// Stream compaction of the active covering rows (v < hi) of an edge-row side:
+// per tile of CMP_TILE rows a count, one exclusive scan, then a stable
+// scatter of the edge pairs, values and original row numbers (orig == nullptr:
+// the rows are the full list, row j is its own original).  *total (device)
+// receives the number of active rows.
+constexpr int CMP_TILE = BLOCK * 8;
+__host__ __device__ inline int64_t cmp_tiles(int64_t m) { return (m + CMP_TILE - 1) / CMP_TILE; }
+template <class T>
+cudaError_t launch_cmp_count(const T *v, int64_t m, double hi, int32_t *tile_off, int64_t *total, cudaStream_t s);
+template <class T>
+cudaError_t launch_cmp_scatter(const int32_t *pairs, const T *v, const int32_t *orig, int64_t m, double hi,
+                               const int32_t *tile_off, int32_t *pairs_o, T *v_o, int32_t *orig_o, cudaStream_t s);
+// z_e = (x_u + x_v) scale_1 over every row of the full edge-row side (the
+// arithmetic of the update's rebuild)
+template <class T> cudaError_t launch_cmp_refresh(const Problem<T> &p, cudaStream_t s);
 }  // namespace mwu

@@ -581,6 +581,10 @@ __device__ void finalize_reductions(Problem<T> &p, int gP, int nb_row, int nb_va
         // min z over every row: with dropped rows the shift of the sums is the
         // minimum over the active rows only
         st->zmin = (drop && p.side[1].rv.kind != RK_DENSE1) ? sh_fin[1][2] : st->s[1];
+        // compacted rows: the dropped ones (z >= act_hi) are no longer read, so
+        // act_hi bounds their minimum; exact while an active row is below it,
+        // and the end of the call re-decides a probe that stopped on the bound
+        if (p.side[1].orig) st->zmin = fmin(st->zmin, st->act_hi);
         if (bad) {
             st->status = ST_NUMERIC;
             st->numeric_bad = 1;
@@ -2146,11 +2150,16 @@ __global__ void __launch_bounds__(BLOCK) k_update(Problem<T> p, int gP) {
 #pragma unroll
                     for (int r = 0; r < 4; ++r) sd.v[j0 + r] = vv[r];
                 }
+                if (sd.orig) {   // compacted rows: the full z the direction reads
+                    const int4 o = *reinterpret_cast<const int4 *>(sd.orig + j0);
+                    sd.vfull[o.x] = vv[0]; sd.vfull[o.y] = vv[1]; sd.vfull[o.z] = vv[2]; sd.vfull[o.w] = vv[3];
+                }
             } else {
                 for (int r = 0; r < nr; ++r) {
                     const int2 e = ed[j0 + r];
                     vv[r] = (p.x[e.x] + p.x[e.y]) * scale;
                     sd.v[j0 + r] = vv[r];
+                    if (sd.orig) sd.vfull[sd.orig[j0 + r]] = vv[r];
                 }
             }
 #pragma unroll
@@ -3316,6 +3325,153 @@ int batch_blocks(int nt, int cl, int n_sms) {
     return 0;
 }
 
+// ============================================================ active-row compaction
+// (drop_covered on the vertex-cover split view) a stable stream compaction of
+// the covering rows with v < hi: per tile of CMP_TILE rows (eight consecutive
+// rows per thread) a count, one exclusive scan over the tiles, then a scatter
+// at each tile's offset plus the in-tile prefix.  Fixed order, no atomics.
+__device__ __forceinline__ int block_excl_scan_int(int v, int *sm_w, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += o;
+    }
+    if (lane == 31) sm_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < BLOCK / 32 ? sm_w[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += o;
+        }
+        if (lane < BLOCK / 32) sm_w[lane] = t;   // inclusive over the warps
+    }
+    __syncthreads();
+    total = sm_w[BLOCK / 32 - 1];
+    const int before = w > 0 ? sm_w[w - 1] : 0;
+    __syncthreads();
+    return before + inc - v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_cmp_count(const T *v, int64_t m, T hi, int32_t *tile_cnt) {
+    __shared__ int sm_w[32];
+    const int64_t tiles = cmp_tiles(m);
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t base = t * CMP_TILE + (int64_t)threadIdx.x * 8;
+        int c = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) c += (base + r < m && v[base + r] < hi) ? 1 : 0;
+        int tot;
+        block_excl_scan_int(c, sm_w, tot);
+        if (threadIdx.x == 0) tile_cnt[t] = tot;
+    }
+}
+
+// exclusive scan of the tile counts in place (one block), the total to *total
+__global__ void __launch_bounds__(BLOCK) k_cmp_scan(int32_t *tile_cnt, int64_t tiles, int64_t *total) {
+    __shared__ long long sm_l[32];
+    const int64_t chunk = (tiles + BLOCK - 1) / BLOCK;
+    const int64_t b = (int64_t)threadIdx.x * chunk, e = min(tiles, b + chunk);
+    long long sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += tile_cnt[i];
+    // exclusive scan of the thread sums (64-bit)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long o = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += o;
+    }
+    if (lane == 31) sm_l[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long t = lane < BLOCK / 32 ? sm_l[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long o = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += o;
+        }
+        if (lane < BLOCK / 32) sm_l[lane] = t;
+    }
+    __syncthreads();
+    long long off = (w > 0 ? sm_l[w - 1] : 0) + inc - sum;
+    for (int64_t i = b; i < e; ++i) {
+        const int32_t c = tile_cnt[i];
+        tile_cnt[i] = (int32_t)off;
+        off += c;
+    }
+    if (threadIdx.x == 0) *total = sm_l[BLOCK / 32 - 1];
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_cmp_scatter(const int2 *pairs, const T *v, const int32_t *orig, int64_t m,
+                                                       T hi, const int32_t *tile_off, int2 *pairs_o, T *v_o,
+                                                       int32_t *orig_o) {
+    __shared__ int sm_w[32];
+    const int64_t tiles = cmp_tiles(m);
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t base = t * CMP_TILE + (int64_t)threadIdx.x * 8;
+        T vv[8];
+        int c = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            vv[r] = base + r < m ? v[base + r] : hi;
+            c += vv[r] < hi ? 1 : 0;
+        }
+        int tot;
+        int64_t pos = (int64_t)tile_off[t] + block_excl_scan_int(c, sm_w, tot);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            if (vv[r] < hi) {
+                const int64_t j = base + r;
+                pairs_o[pos] = pairs[j];
+                v_o[pos] = vv[r];
+                orig_o[pos] = orig ? orig[j] : (int32_t)j;
+                ++pos;
+            }
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_cmp_refresh(Problem<T> p) {
+    const Side<T> &sd = p.side[1];
+    const int2 *ed = reinterpret_cast<const int2 *>(sd.rv.idx);
+    const T scale = (T)p.st->scale[1];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < sd.m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = ed[j];
+        sd.v[j] = (p.x[e.x] + p.x[e.y]) * scale;
+    }
+}
+
+static int cmp_grid(int64_t tiles) { return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * 16)); }
+
+template <class T>
+cudaError_t launch_cmp_count(const T *v, int64_t m, double hi, int32_t *tile_off, int64_t *total, cudaStream_t s) {
+    const int64_t tiles = cmp_tiles(m);
+    if (tiles == 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), s);
+    k_cmp_count<T><<<cmp_grid(tiles), BLOCK, 0, s>>>(v, m, (T)hi, tile_off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_cmp_scan<<<1, BLOCK, 0, s>>>(tile_off, tiles, total);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_cmp_scatter(const int32_t *pairs, const T *v, const int32_t *orig, int64_t m, double hi,
+                               const int32_t *tile_off, int32_t *pairs_o, T *v_o, int32_t *orig_o, cudaStream_t s) {
+    const int64_t tiles = cmp_tiles(m);
+    if (tiles == 0) return cudaSuccess;
+    k_cmp_scatter<T><<<cmp_grid(tiles), BLOCK, 0, s>>>(reinterpret_cast<const int2 *>(pairs), v, orig, m, (T)hi,
+                                                       tile_off, reinterpret_cast<int2 *>(pairs_o), v_o, orig_o);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_cmp_refresh(const Problem<T> &p, cudaStream_t s) {
+    k_cmp_refresh<T><<<grid_for(p.side[1].m, p.grid_upd), BLOCK, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 #define MWU_INSTANTIATE(T)                                                                                     \
     template cudaError_t launch_x_init<T>(const Problem<T> &, cudaStream_t);                                   \
     template cudaError_t launch_x_set<T>(const Problem<T> &, const void *, int, cudaStream_t);                 \
@@ -3335,7 +3491,11 @@ int batch_blocks(int nt, int cl, int n_sms) {
     template cudaError_t launch_copy_vec<T>(const T *, void *, int64_t, int, cudaStream_t);                    \
     template int sweep_blocks_per_sm<T>(int *, int *, int *);                                                  \
     template int spmv_blocks_per_sm<T>();                                                                      \
-    template int tiled_blocks_per_sm<T>();
+    template int tiled_blocks_per_sm<T>();                                                                     \
+    template cudaError_t launch_cmp_count<T>(const T *, int64_t, double, int32_t *, int64_t *, cudaStream_t);     \
+    template cudaError_t launch_cmp_scatter<T>(const int32_t *, const T *, const int32_t *, int64_t, double,       \
+                                               const int32_t *, int32_t *, T *, int32_t *, cudaStream_t);          \
+    template cudaError_t launch_cmp_refresh<T>(const Problem<T> &, cudaStream_t);
 
 MWU_INSTANTIATE(float)
 MWU_INSTANTIATE(double)

@@ -62,7 +62,8 @@ class mwu_result(C.Structure):
 
 class mwu_timing(C.Structure):
     _fields_ = [("dir_ms", C.c_double), ("spmv_ms", C.c_double), ("cand_ms", C.c_double),
-                ("update_ms", C.c_double), ("iters", C.c_int64), ("cand_passes", C.c_int64)]
+                ("update_ms", C.c_double), ("iters", C.c_int64), ("cand_passes", C.c_int64),
+                ("compactions", C.c_int64)]
 
 
 class mwu_scalars(C.Structure):

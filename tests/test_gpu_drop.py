@@ -188,3 +188,66 @@ def test_drop_potential_takes_every_row(M, wls):
     S_all = om.lse_shift_sum(ch.z, ch.eta, -1)[1]
     S_act = om.lse_shift_sum(ch.za, ch.eta, -1)[1]
     assert S_all > 1.1 * S_act            # the two sums differ: the check above is not vacuous
+
+
+@pytest.mark.parametrize("step", ["kary", "newton"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_compacted_probe_restores_the_rows(M, prec, step):
+    """drop_covered = 1 on the vertex-cover split view compacts the unsatisfied
+    edges inside mwu_iterate (the last step of Alg. 1/2 as a stream
+    compaction).  On return every z equals x_u + x_v in the form's precision,
+    the rows dropped earlier included, zmin is the minimum over every row, and
+    the probe ends as the masked form (drop_covered = 2) ends it."""
+    from graphgen import workloads as W
+    wl = W.vcover(12, seed=21)
+    g = wl.graph
+    u, v = g.u.numpy().astype(np.int64), g.v.numpy().astype(np.int64)
+    T = 1.03 * exact_opt(wl)        # feasible, near the optimum: a long probe in which most edges are met
+    out = {}
+    for drop in (1, 2):
+        ctx = make_ctx(M, wl, prec, drop_covered=drop, step=M.STEP_NEWTON if step == "newton" else M.STEP_KARY)
+        try:
+            M.mwu_set_target(ctx, T)
+            rc, st = M.mwu_iterate(ctx, 5000)
+            x = vec(M, ctx, M.VEC_X, g.n)
+            z = vec(M, ctx, M.VEC_Z, g.m)
+            out[drop] = (rc, st, x, z, M.mwu_get_scalars(ctx), M.mwu_get_timing(ctx))
+        finally:
+            M.mwu_destroy(ctx)
+    rc, st, x, z, sc, tim = out[1]
+    assert tim["compactions"] >= 1 and out[2][5]["compactions"] == 0
+    dt = np.float32 if prec == "f32" else np.float64
+    xs = x.astype(dt)
+    zx = (xs[u] + xs[v]).astype(np.float64)
+    assert np.array_equal(np.sort(z), np.sort(zx))           # the context's row order is its own
+    assert sc["zmin"] == float(zx.min())
+    assert rc == out[2][0] == M.FEASIBLE
+    if sc["zmin"] >= 1.0:                                   # the stopping test on the exact rows
+        assert sc["ymax"] <= (1 + wl.eps) * sc["zmin"]
+    it1, it2 = st["iters"], out[2][1]["iters"]
+    assert abs(it1 - it2) <= 0.1 * max(it1, it2) + 2, (it1, it2)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_compacted_solve_matches_oracle_and_exact(M, prec):
+    from graphgen import workloads as W
+    wl = W.vcover(12, seed=21)
+    ctx = make_ctx(M, wl, prec, drop_covered=1)
+    try:
+        res = M.mwu_solve(ctx)
+        x = vec(M, ctx, M.VEC_X, H.n_vars(wl))
+        assert M.mwu_get_timing(ctx)["compactions"] >= 1
+    finally:
+        M.mwu_destroy(ctx)
+    cert = certificate_from_x(wl, x)
+    assert cert == pytest.approx(res["objective"], rel=1e-4)
+    opt = exact_opt(wl)
+    assert opt * (1 - 1e-9) <= cert <= opt * (1 + wl.eps) ** 2
+    ores = H.oracle_solve(wl, drop_covered=True)
+    assert 1 / (1 + wl.eps) <= cert / ores.objective <= 1 + wl.eps, (cert, ores.objective)
+
+
+def test_drop_covered_rejects_other_values(M, wls):
+    with pytest.raises(M.MWUError) as e:
+        make_ctx(M, wls["vcover"], "f32", drop_covered=3)
+    assert e.value.code == M.ERR_INVALID
