@@ -353,13 +353,17 @@ static int build_side(mwu_ctx *c, const mwu_matrix *A, int32_t sign, SideBuild &
             sb.rv.n_seg = ns;
         }
         // staged SpMV for banded matrices: tiles of 4 row steps of a block; taken
-        // when at least 90 % of the tiles' input windows fit in shared memory
+        // when the input windows of at least 90 % of the tiles, holding at least
+        // 90 % of the entries, fit in shared memory (a tile that does not fit runs
+        // on one block from global memory: a few long rows there, like the item
+        // rows of a users x items graph, would leave that block as the tail)
         if (c->opt.spmv_tiles >= 0 && sb.rv.rows > 0) {
             const int tr = 4 * (BLOCK / sb.rv.G);
             const int wmax = c->fp64 ? tile_wmax<double>() : tile_wmax<float>();
             int32_t *tlo = nullptr, *tlen = nullptr, nt = 0, fit = 0;
-            TRY_CUDA(c, build_tiles(c->ar, sb.rv.ptr, sb.rv.idx, sb.rv.rows, tr, wmax, &tlo, &tlen, &nt, &fit, s));
-            if (nt > 0 && (double)fit >= 0.9 * (double)nt) {
+            int64_t fit_nnz = 0;
+            TRY_CUDA(c, build_tiles(c->ar, sb.rv.ptr, sb.rv.idx, sb.rv.rows, tr, wmax, &tlo, &tlen, &nt, &fit, &fit_nnz, s));
+            if (nt > 0 && (double)fit >= 0.9 * (double)nt && (double)fit_nnz >= 0.9 * (double)sb.rv.nnz) {
                 sb.rv.n_tiles = nt;
                 sb.rv.tile_rows = tr;
                 sb.rv.tile_lo = tlo;

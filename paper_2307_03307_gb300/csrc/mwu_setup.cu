@@ -366,9 +366,10 @@ cudaError_t bin_list(Arena &ar, const int32_t *ptr, int64_t rows, int lo, int hi
     return select_flagged(ar, flag, rows, list, count, s);
 }
 
-// one block per tile: min and max column over the tile's entries
+// one block per tile: min and max column over the tile's entries; fit[0]
+// counts the tiles whose window fits, fit[1] the entries those tiles hold
 __global__ void k_tile_windows(const int32_t *ptr, const int32_t *idx, int64_t rows, int tile_rows, int wmax,
-                               int32_t *lo, int32_t *len, int *fit) {
+                               int32_t *lo, int32_t *len, unsigned long long *fit) {
     __shared__ int s_lo[8], s_hi[8];
     const int64_t t = blockIdx.x;
     const int64_t r0 = t * tile_rows, r1 = r0 + tile_rows < rows ? r0 + tile_rows : rows;
@@ -391,26 +392,34 @@ __global__ void k_tile_windows(const int32_t *ptr, const int32_t *idx, int64_t r
         const int span = mx >= mn ? mx - mn + 1 : 0;
         lo[t] = span > 0 ? mn : 0;
         len[t] = span;
-        if (span <= wmax) atomicAdd(fit, 1);
+        if (span <= wmax) {
+            atomicAdd(fit, 1ull);
+            atomicAdd(fit + 1, (unsigned long long)(ptr[r1] - ptr[r0]));
+        }
     }
 }
 
 cudaError_t build_tiles(Arena &ar, const int32_t *ptr, const int32_t *idx, int64_t rows, int tile_rows, int wmax,
-                        int32_t **lo, int32_t **len, int32_t *n_tiles, int32_t *fit, cudaStream_t s) {
+                        int32_t **lo, int32_t **len, int32_t *n_tiles, int32_t *fit, int64_t *fit_nnz, cudaStream_t s) {
     const int64_t nt = (rows + tile_rows - 1) / tile_rows;
     *n_tiles = (int32_t)nt;
     *fit = 0;
+    *fit_nnz = 0;
     if (nt <= 0) return cudaSuccess;
     *lo = ar.alloc<int32_t>(nt);
     *len = ar.alloc<int32_t>(nt);
-    int *d_fit = ar.alloc_tmp<int>(1);
+    unsigned long long *d_fit = ar.alloc_tmp<unsigned long long>(2);
     if (!*lo || !*len || !d_fit) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaMemsetAsync(d_fit, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(d_fit, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     k_tile_windows<<<(unsigned)nt, 256, 0, s>>>(ptr, idx, rows, tile_rows, wmax, *lo, *len, d_fit);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(fit, d_fit, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-    return cudaStreamSynchronize(s);
+    unsigned long long h[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(h, d_fit, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *fit = (int32_t)h[0];
+    *fit_nnz = (int64_t)h[1];
+    return cudaSuccess;
 }
 
 cudaError_t range_list2(Arena &ar, const int32_t *p1, const int32_t *p2, int64_t rows, int lo, int hi,

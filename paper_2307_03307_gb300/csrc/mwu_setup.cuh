@@ -107,9 +107,11 @@ cudaError_t length_quantile2(Arena &ar, const int32_t *p1, const int32_t *p2, in
                              cudaStream_t s);
 // Tile plan of a CSR row view for the staged SpMV: tiles of tile_rows
 // consecutive rows; per tile the first column and the column span of its
-// entries (0 for an empty tile).  *fit = tiles whose span is at most wmax.
+// entries (0 for an empty tile).  *fit = tiles whose span is at most wmax,
+// *fit_nnz = the entries of those tiles.
 cudaError_t build_tiles(Arena &ar, const int32_t *ptr, const int32_t *idx, int64_t rows, int tile_rows, int wmax,
-                        int32_t **lo, int32_t **len, int32_t *n_tiles, int32_t *fit, cudaStream_t s);
+                        int32_t **lo, int32_t **len, int32_t *n_tiles, int32_t *fit, int64_t *fit_nnz,
+                        cudaStream_t s);
 cudaError_t bracket_stats(Arena &ar, const ColView &cv, int64_t n, const float *c, double *sum_inv_min,
                           double *sum_inv_max, double *deg_max, cudaStream_t s);
 cudaError_t bracket_rowratio(Arena &ar, const RowView &rv, int64_t rows, const float *c, double *out,
