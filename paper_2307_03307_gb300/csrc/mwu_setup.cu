@@ -470,6 +470,10 @@ __global__ void k_colstats(ColView cv, int64_t n, const float *c, double *part) 
         auto put = [&](double a) { mn = fmin(mn, a); mx = fmax(mx, a); };
         switch (cv.kind) {
         case CK_CSR:
+            if (!cv.val && !cv.rdiv) {   // unit entries: one value, no division per entry
+                if (cv.ptr[i + 1] > cv.ptr[i]) put(1.0);
+                break;
+            }
             for (int k = cv.ptr[i]; k < cv.ptr[i + 1]; ++k)
                 put((cv.val ? (double)cv.val[k] : 1.0) / (cv.rdiv ? (double)cv.rdiv[cv.idx[k]] : 1.0));
             break;
@@ -515,6 +519,22 @@ __global__ void k_rowratio(RowView rv, int64_t rows, const float *c, double *par
         double mn = INFINITY;
         switch (rv.kind) {
         case RK_CSR:
+            if (!rv.val) {
+                // every entry of the row is coef: a correctly rounded division by a
+                // positive constant is monotone, so min_k (c_k / coef) is
+                // (min_k c_k) / coef exactly, with one FP64 division per row
+                // (the minimum itself in FP32: float -> double is exact and monotone)
+                if (coef > 0.0 && rv.ptr[j + 1] > rv.ptr[j]) {
+                    float cm = INFINITY;
+                    if (c) {
+                        for (int k = rv.ptr[j]; k < rv.ptr[j + 1]; ++k) cm = fminf(cm, c[rv.idx[k]]);
+                    } else {
+                        cm = 1.0f;
+                    }
+                    mn = (double)cm / coef;
+                }
+                break;
+            }
             for (int k = rv.ptr[j]; k < rv.ptr[j + 1]; ++k) {
                 double a = (rv.val ? (double)rv.val[k] : 1.0) * coef;
                 if (a > 0.0) mn = fmin(mn, (c ? (double)c[rv.idx[k]] : 1.0) / a);

@@ -251,3 +251,28 @@ def test_drop_covered_rejects_other_values(M, wls):
     with pytest.raises(M.MWUError) as e:
         make_ctx(M, wls["vcover"], "f32", drop_covered=3)
     assert e.value.code == M.ERR_INVALID
+
+
+def test_compacted_probe_eager_launches(M):
+    """The compaction between host-launched iterations (use_graph = 0) follows
+    the captured-graph form: the same iterates, status and restored rows."""
+    from graphgen import workloads as W
+    wl = W.vcover(12, seed=21)
+    g = wl.graph
+    u, v = g.u.numpy().astype(np.int64), g.v.numpy().astype(np.int64)
+    T = 1.03 * exact_opt(wl)
+    out = {}
+    for graph in (0, 1):
+        ctx = make_ctx(M, wl, "f32", drop_covered=1, use_graph=graph)
+        try:
+            M.mwu_set_target(ctx, T)
+            rc, st = M.mwu_iterate(ctx, 5000)
+            out[graph] = (rc, st["iters"], vec(M, ctx, M.VEC_X, g.n), vec(M, ctx, M.VEC_Z, g.m),
+                          M.mwu_get_timing(ctx)["compactions"])
+        finally:
+            M.mwu_destroy(ctx)
+    rc, it, x, z, nc = out[0]
+    assert nc >= 1 and rc == out[1][0] and it == out[1][1]
+    assert np.array_equal(x, out[1][2])
+    xs = x.astype(np.float32)
+    assert np.array_equal(np.sort(z), np.sort((xs[u] + xs[v]).astype(np.float64)))
