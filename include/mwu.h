@@ -490,8 +490,10 @@ int mwu_batch_stats(mwu_ctx *ctx, int64_t *passes, int32_t *probes);
 
 /* Per-instance start and end of its solve in the last mwu_solve_batch, in
  * milliseconds after the earliest start (the device's global timer): shows
- * which instance ends last and sets the batch time.  Host arrays of `count`
- * entries, either NULL.  MWU_ERR_STATE before a solve. */
+ * which instance ends last and sets the batch time.  A diagnostic of this
+ * library with no counterpart in the paper.  Host arrays of `count` entries,
+ * either NULL.  MWU_ERR_INVALID for a context that is not a batch,
+ * MWU_ERR_STATE before a solve. */
 int mwu_batch_timeline(mwu_ctx *ctx, double *start_ms, double *end_ms);
 
 /* ------------------------------------------------------------ diagnostics */
